@@ -1,0 +1,369 @@
+"""Benchmark of the per-macroparticle QED Monte Carlo step on GB300.
+
+Workload (one step = one qed_step_fused pass over all species): 2^26 = 64M
+electrons with chi log-uniform in [1e-3, 1e2] and gamma log-uniform in
+[1e2, 1e4], per-particle fields (B perpendicular to p, |B| = chi a_S/|p|,
+E = 0), Dt = 0.01 / omega0, table sampler, FP32 state.  Photons (and the
+pairs they create) accumulate across steps and are advanced in the steps
+after their birth.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  `value` = particle-steps per second over all ranks
+(device-resident inputs); `e2e` = the same metric with the state on the host,
+copied in and out around every step; `roofline` = the lepton kernel's
+algorithmic bytes per launch over its CUDA-event time against the measured
+HBM copy bandwidth; `cpu_baseline` = the FP64 oracle on the host's cores on
+a bounded sample.  `--impl reference` times that oracle alone.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QED particle-steps/s at 64M particles (table vs MLP) and % HBM roofline"
+UNIT = "particle-steps/s"
+N_PART = 1 << 26
+DT = 0.01
+LEPTON_BYTES = 84       # R x,y,z,px,py,pz,w (28) + id (8) + E,B (24); W x,y,z,px,py,pz (24)
+PHOTON_APPEND_BYTES = 61  # x,y,z,px,py,pz,w (28) + id (8) + alive (1) + inherited E,B (24)
+PHOTON_BYTES = 85       # photon step: R 28+8+1+24, W x,y,z (12) [+ alive on pair]
+
+
+def workload_desc(n):
+    return {"workload": f"chi-target ensemble: {n} electrons (chi log-uniform [1e-3,1e2], gamma "
+                        "log-uniform [1e2,1e4], per-particle B perp p, E=0), fused step "
+                        "(gather+Boris+chi+rate+Method I+xi+recoil+append; photon push+pairs), "
+                        "table sampler, photons/pairs accumulate",
+            "particles": n, "dt": DT, "precision": "fp32 state, fp64 chi where it cancels",
+            "sampler": "table", "l2": "inputs larger than L2 (>= 5.4 GB read per step)"}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+                for nm, v in zip(names, r[4:8]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def host_workload(n, seed, chunk=1 << 22):
+    """Generate the chi-target ensemble in chunks (float32 host arrays)."""
+    from paper_1608_06356_gb300 import workloads as W
+    out = {k: np.empty(n, dtype=np.float32) for k in
+           ("x", "y", "z", "px", "py", "pz", "w", "ex", "ey", "ez", "bx", "by", "bz")}
+    out["id"] = np.empty(n, dtype=np.uint64)
+    for c0 in range(0, n, chunk):
+        m = min(chunk, n - c0)
+        st, _, _ = W.chi_target(m, seed=seed * 100003 + c0 // chunk, id0=c0)
+        for k, v in st.items():
+            out[k][c0:c0 + m] = v
+    return out
+
+
+def cpu_baseline(sample_n=12288, steps=2, seed=0):
+    """The FP64 oracle as it stands on a bounded sample of the same workload."""
+    import oracle as O
+    from paper_1608_06356_gb300 import workloads as W
+    st, _, _ = W.chi_target(sample_n, seed=seed)
+    st = {k: (v.astype(np.float32).astype(np.float64) if v.dtype.kind == "f" else v)
+          for k, v in st.items()}
+    cfg = O.make_config(dt=DT, seed=1)
+    e = O.Species(sample_n * 2, -1.0, per_particle_fields=True).load(**st)
+    p = O.Species(sample_n, 1.0, per_particle_fields=True)
+    g = O.Species(sample_n * 4 * (steps + 1), 0.0, per_particle_fields=True, with_alive=True)
+    f = O.per_particle_fields()
+    t0 = time.perf_counter()
+    ps = 0
+    for s in range(steps):
+        ps += e.n + p.n + g.n
+        O.step(cfg, f, e, p, g, s)
+    dt = time.perf_counter() - t0
+    return {"value": ps / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{sample_n} electrons of the same ensemble x {steps} step(s) "
+                      f"({ps} particle-steps in {dt:.1f} s), FP64 quadrature rates"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    O.build()
+    from paper_1608_06356_gb300 import workloads as W
+    n = args.ref_particles
+    st, _, _ = W.chi_target(n, seed=0)
+    st = {k: (v.astype(np.float32).astype(np.float64) if v.dtype.kind == "f" else v)
+          for k, v in st.items()}
+    cfg = O.make_config(dt=DT, seed=1)
+    total = args.warmup + args.steps
+    e = O.Species(n * 2, -1.0, per_particle_fields=True).load(**st)
+    p = O.Species(n, 1.0, per_particle_fields=True)
+    g = O.Species(n * 2 * (total + 1), 0.0, per_particle_fields=True, with_alive=True)
+    f = O.per_particle_fields()
+    for s in range(args.warmup):
+        O.step(cfg, f, e, p, g, s)
+    ps = 0
+    t0 = time.perf_counter()
+    for s in range(args.warmup, total):
+        ps += e.n + p.n + g.n
+        O.step(cfg, f, e, p, g, s)
+    dt = time.perf_counter() - t0
+    v = ps / dt
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": workload_desc(N_PART),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                             "sample": f"{n} electrons of the same ensemble per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--particles", type=int, default=N_PART)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--ref-particles", type=int, default=1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1608_06356_gb300 import api
+
+    n = args.particles
+    total_steps = args.warmup + args.steps + args.e2e_steps
+    # photon/pair capacity: ~0.25 emissions per electron per step at Dt = 0.01 at the start,
+    # falling as the ensemble cools; dead photons are compacted every step
+    cap_g = int(n * 0.3 * (total_steps + 1)) + 4096
+    cap_e = 2 * n
+    cap_p = n
+    ctx = api.qed_init_tables(api.config(dt=DT, seed=1 + rank, max_particles=max(cap_g, cap_e)))
+    host = host_workload(n, seed=rank)
+    host["id"] += np.uint64(rank) << np.uint64(40)
+    e = api.Species.empty(cap_e, -1, fields=True).load(**host)
+    p = api.Species.empty(cap_p, +1, fields=True)
+    g = api.Species.empty(cap_g, 0, fields=True)
+    F = api.Fields.per_particle()
+    counts = torch.zeros((args.steps, 3), dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def one_step(k, s):
+        counts[k, 0].copy_(e.n[0] + p.n[0])
+        counts[k, 1].copy_(g.n[0])
+        api.qed_step_fused(ctx, e, p, g, F, s)
+        api.qed_compact(ctx, g)
+
+    # warm-up runs the exact loop body, so every kernel (ours and torch's) is loaded
+    for s in range(args.warmup):
+        one_step(0, s)
+    torch.cuda.synchronize()
+    api.qed_reset_counters(ctx)
+    c_before = api.qed_read_counters(ctx)
+    api.qed_profile_begin(ctx, args.steps)
+    launches0 = ctx.launches
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(args.steps):
+        one_step(k, args.warmup + k)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = clk.stop()
+    launches = ctx.launches - launches0
+    ms = t0.elapsed_time(t1)
+    lep_ms, pho_ms, nprof = api.qed_profile_end(ctx)
+    c_after = api.qed_read_counters(ctx)
+    cnt = counts.cpu().numpy()
+    ps_local = float(cnt[:, 0].sum() + cnt[:, 1].sum())
+    t_max = ms
+    ps_total = ps_local
+    if world > 1:
+        tt = torch.tensor([ms, ps_local], dtype=torch.float64, device="cuda")
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        t_max, ps_total = float(mx[0]), float(tt[1])
+    value = ps_total / (t_max * 1e-3)
+
+    # roofline of the dominant (lepton) kernel: algorithmic bytes / event time
+    emitted = c_after["emit_events"] - c_before["emit_events"]
+    lep_bytes = (LEPTON_BYTES * cnt[:, 0].sum() + PHOTON_APPEND_BYTES * emitted) / max(nprof, 1)
+    lep_t = lep_ms / max(nprof, 1) * 1e-3
+    peak, peak_kind = peaks()
+    achieved = lep_bytes / lep_t / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_lepton (fused gather/push/emission)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": f"{peak_kind} HBM copy", "traffic": None,
+                "bytes_per_launch": lep_bytes, "ms_per_launch": lep_t * 1e3,
+                "lepton_share_of_step": lep_ms / max(ms, 1e-9),
+                "photon_kernel_ms_per_launch": pho_ms / max(nprof, 1)}
+
+    # e2e: the same steps with the state on the host (pinned), copied in and out
+    e2e = None
+    if args.e2e_steps > 0:
+        names_l = ("x", "y", "z", "px", "py", "pz", "w", "id", "ex", "ey", "ez", "bx", "by", "bz")
+        names_g = names_l + ("alive",)
+        torch.cuda.synchronize()
+        sizes = {"e": e.count(), "p": p.count(), "g": g.count()}
+        pin = {}
+        grow = int(0.25 * n * args.e2e_steps) + 4096  # appends these steps may add
+        for sp_name, sp, names in (("e", e, names_l), ("p", p, names_l), ("g", g, names_g)):
+            room = min(sp.capacity, sizes[sp_name] + grow)
+            for k in names:
+                t = getattr(sp, k)
+                pin[(sp_name, k)] = torch.empty(room, dtype=t.dtype, pin_memory=True)
+                m = sizes[sp_name]
+                pin[(sp_name, k)][:m].copy_(t[:m])
+        n_host = torch.zeros(3, dtype=torch.int64, pin_memory=True)
+        torch.cuda.synchronize()
+        h2d = d2h = 0
+        ps_e2e = 0
+        w0 = time.perf_counter()
+        for k in range(args.e2e_steps):
+            for sp_name, sp, names in (("e", e, names_l), ("p", p, names_l), ("g", g, names_g)):
+                m = sizes[sp_name]
+                for nm in names:
+                    t = getattr(sp, nm)
+                    t[:m].copy_(pin[(sp_name, nm)][:m], non_blocking=True)
+                    h2d += m * t.element_size()
+                sp.n.fill_(m)
+            ps_e2e += sizes["e"] + sizes["p"] + sizes["g"]
+            api.qed_step_fused(ctx, e, p, g, F, args.warmup + args.steps + k)
+            api.qed_compact(ctx, g)
+            n_host[0].copy_(e.n[0], non_blocking=True)
+            n_host[1].copy_(p.n[0], non_blocking=True)
+            n_host[2].copy_(g.n[0], non_blocking=True)
+            stream.synchronize()
+            d2h += 24
+            sizes = {"e": int(n_host[0]), "p": int(n_host[1]), "g": int(n_host[2])}
+            for nm_, sp_ in (("e", e), ("p", p), ("g", g)):
+                sizes[nm_] = min(sizes[nm_], pin[(nm_, "x")].numel())
+            for sp_name, sp, names in (("e", e, names_l), ("p", p, names_l), ("g", g, names_g)):
+                m = sizes[sp_name]
+                for nm in names:
+                    t = getattr(sp, nm)
+                    pin[(sp_name, nm)][:m].copy_(t[:m], non_blocking=True)
+                    d2h += m * t.element_size()
+            stream.synchronize()
+        wall = time.perf_counter() - w0
+        e2e = {"value": ps_e2e / wall, "unit": UNIT,
+               "h2d_bytes_per_step": h2d // args.e2e_steps, "d2h_bytes_per_step": d2h // args.e2e_steps,
+               "steps": args.e2e_steps,
+               "note": "state on pinned host memory; every step copies all species in, runs "
+                       "qed_step_fused, reads the counts and copies all species back"}
+
+    status = c_after["status"]
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_desc(n), "roofline": roofline, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clocks,
+            "counters": {"emit_events": emitted,
+                         "pair_events": c_after["pair_events"] - c_before["pair_events"],
+                         "substeps": c_after["substeps"] - c_before["substeps"],
+                         "dropped": c_after["dropped"], "domain": c_after["domain"],
+                         "status": status,
+                         "particles_at_end": {"leptons": int(cnt[-1, 0]), "photons": int(cnt[-1, 1])}}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

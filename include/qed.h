@@ -1,0 +1,227 @@
+/*
+ * qed.h -- C ABI of libqed, a GB300 (sm_103a) implementation of the
+ * per-macroparticle QED Monte Carlo step of Wang, Sheng, Gibbon & Li,
+ * "Modeling of photon and pair production due to QED effects in
+ * particle-in-cell simulation" (arXiv:1608.06356).
+ *
+ * Physics (paper equation numbers):
+ *   chi_e  -- Eq. (2);  chi_ph -- Eq. (3)
+ *   photon emission spectrum, formula I -- Eq. (1), adopted by the paper for
+ *     the simulation (text after Fig. 1)
+ *   pair (Breit-Wheeler) spectrum -- Eq. (6)
+ *   event generator: Method I (text before Eq. 7): emit iff W*Dt > r1; photon
+ *     energy fraction from the inverse CDF, Eq. (7), with the infrared cut
+ *     xi_min * eps_e = 2 m c^2
+ *   adjustable time step (paragraph after Fig. 4): if W*Dt > 0.2 the generator
+ *     runs N sub-steps with W*Dt/N <= 0.2
+ *
+ * Units: time 1/omega0, length c/omega0, momentum m_e c, fields m_e c omega0/e,
+ * energies m_e c^2.  a_S is the Schwinger field E_S in field units.
+ *
+ * Conventions for every call:
+ *   - Returns QED_OK (0) or a negative QED_ERR_* code; qed_strerror() names it.
+ *   - Particle and field pointers are CALLER-OWNED DEVICE memory.  The library
+ *     owns only what qed_init_tables allocates (tables, scan state, counters)
+ *     and frees it in qed_destroy.  No call other than qed_init_tables
+ *     allocates device memory.
+ *   - Work is enqueued asynchronously on the given stream (NULL = legacy
+ *     default stream).  Particle counts live on the device (qed_species.d_n),
+ *     so no call reads them on the host and launches never depend on them.
+ *   - Errors found on the device (capacity overflow, chi outside the table
+ *     range, non-finite values, a bounded wait that ran out) never trap: they
+ *     set bits in a device status word, read with qed_read_counters().
+ *   - Calls that share a qed_ctx must be issued to one stream, or ordered.
+ */
+#ifndef QED_H
+#define QED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *qed_stream_t; /* a cudaStream_t */
+typedef struct qed_ctx qed_ctx;
+
+/* ---- status codes ---------------------------------------------------- */
+enum {
+  QED_OK = 0,
+  QED_ERR_ARG = -1,      /* invalid argument (NULL pointer, bad size, bad mode) */
+  QED_ERR_CUDA = -2,     /* a CUDA runtime call failed */
+  QED_ERR_CAPACITY = -3, /* a size exceeds what the context was built for */
+  QED_ERR_DOMAIN = -4,   /* table range invalid */
+  QED_ERR_TIMEOUT = -5,  /* a bounded device wait ran out (see status bits) */
+  QED_ERR_NOCONV = -6,   /* table build did not converge */
+  QED_ERR_NOMEM = -7,    /* device allocation failed (qed_init_tables only) */
+  QED_ERR_UNSUPPORTED = -8
+};
+
+/* ---- device status bits (qed_counters.status) ----------------------- */
+enum {
+  QED_STATUS_CAPACITY = 1u, /* appends beyond a species' capacity were dropped */
+  QED_STATUS_DOMAIN = 2u,   /* chi (or delta_min) outside the table range: clamped */
+  QED_STATUS_NONFINITE = 4u,/* non-finite momentum or field met (particle skipped) */
+  QED_STATUS_TIMEOUT = 8u,  /* a look-back wait hit its iteration limit */
+  QED_STATUS_SUBSTEPS = 16u /* sub-step count was capped at qed_config.max_substeps */
+};
+
+enum { QED_FP32 = 0, QED_FP64 = 1 };
+enum { QED_FIELDS_UNIFORM = 0, QED_FIELDS_PER_PARTICLE = 1, QED_FIELDS_GRID = 2 };
+
+/* ---- configuration ---------------------------------------------------- */
+typedef struct {
+  double a_S;           /* E_S / (m_e c omega0 / e); 412148.45 at lambda = 1 um */
+  double alpha;         /* fine-structure constant, 1/137.035999 ("~1/137", Eq. 1) */
+  double dt;            /* PIC step Dt in 1/omega0 */
+  double wdt_max;       /* sub-step threshold: W*Dt/N <= wdt_max (0.2, after Fig. 4) */
+  double xi_min_energy; /* infrared cut xi_min * eps_e = xi_min_energy (2 m c^2, Eq. 7) */
+  int pair_sign;        /* sign of int K_{1/3} in Eq. (6): +1 (standard, default) or -1 (as printed) */
+  int precision;        /* QED_FP32 (FP32 state/tables, FP64 chi where it cancels) or QED_FP64 */
+  double chi_min, chi_max;           /* photon-emission table range in chi_e */
+  double chi_pair_min, chi_pair_max; /* pair table range in chi_ph; below chi_pair_min W_pair = 0 */
+  double fwd_per_unit;  /* forward-table nodes per unit of ln chi and ln delta (0 = default) */
+  double inv_per_unit;  /* inverse-table nodes per unit of kappa (0 = default) */
+  uint64_t seed;        /* Philox4x32-10 key */
+  double spec_lo, spec_hi; /* photon-energy histogram: 64 log bins over [spec_lo, spec_hi) m c^2 */
+  int64_t max_particles;   /* largest per-species capacity any call will use (sizes scan state) */
+  int64_t max_substeps;    /* cap on N per particle per step (status bit when hit) */
+} qed_config;
+
+/* Fill *cfg with the paper-derived defaults (FP32, dt = 0.01, seed 0). */
+void qed_config_default(qed_config *cfg);
+
+/* ---- particle species (structure of arrays) ----------------------------
+ * Element type of x..w and ex..bz is float in QED_FP32 contexts and double in
+ * QED_FP64 contexts.  id: 64-bit particle ids (key of the Philox stream).
+ * alive: photons only (1 alive, 0 dead); may be NULL for leptons.
+ * ex..bz: per-particle fields (QED_FIELDS_PER_PARTICLE); children inherit
+ * their parent's fields; NULL otherwise.
+ * d_n: device int64 holding the current count; appends beyond `capacity` are
+ * dropped and counted.  q: -1 electron, +1 positron, 0 photon.              */
+typedef struct {
+  void *x, *y, *z, *px, *py, *pz, *w;
+  uint64_t *id;
+  uint8_t *alive;
+  void *ex, *ey, *ez, *bx, *by, *bz;
+  int64_t *d_n;
+  int64_t capacity;
+  int q;
+  int pad_;
+} qed_species;
+
+/* ---- fields -------------------------------------------------------------
+ * UNIFORM: e[3], b[3] everywhere.  PER_PARTICLE: the species' ex..bz arrays.
+ * GRID: CIC (trilinear) gather from a periodic collocated node grid
+ * grid[nz][ny][nx][8] (float; Ex Ey Ez Bx By Bz, 2 pad floats; node (i,j,k)
+ * at (x0 + i dx, y0 + j dy, z0 + k dz)).                                     */
+typedef struct {
+  int mode, nx, ny, nz;
+  double e[3], b[3];
+  const float *grid;
+  double dx, dy, dz, x0, y0, z0;
+} qed_fields;
+
+/* ---- counters (device-resident, accumulated until reset) --------------- */
+typedef struct {
+  int64_t emit_events;  /* photons emitted (Method I events of leptons) */
+  int64_t pair_events;  /* pairs created */
+  int64_t substeps;     /* generator sub-steps executed (leptons + photons) */
+  int64_t dropped;      /* appends lost to capacity */
+  int64_t domain;       /* evaluations clamped to the table range */
+  uint32_t status;      /* QED_STATUS_* bits */
+  uint32_t pad_;
+  int64_t hist[64];     /* emitted-photon energies, 64 log bins over [spec_lo, spec_hi) */
+} qed_counters;
+
+const char *qed_strerror(int code);
+
+/* Build the rate and inverse-CDF tables (FP64 on the device by Bessel
+ * quadrature of Eqs. (1) and (6); FP32 copies for QED_FP32) and allocate the
+ * context.  Blocks until the tables are built.  *out is set only on success. */
+int qed_init_tables(const qed_config *cfg, qed_ctx **out, qed_stream_t stream);
+
+/* Free everything the context owns (after synchronising its device work). */
+void qed_destroy(qed_ctx *ctx);
+
+/* Field gather + Boris push for all leptons of s (q = -1 or +1; photons
+ * are pushed by qed_pair).  Positions advance by v*dt with the new momentum. */
+int qed_gather_push(qed_ctx *ctx, const qed_species *s, const qed_fields *f, int64_t step,
+                    qed_stream_t stream);
+
+/* Method I photon emission (Eqs. 1, 2, 7) for every lepton of `lepton`
+ * with fields gathered at its current position: chi_e, W_rad, N sub-steps,
+ * events, xi draw, recoil, stable append of photons to `photons`. */
+int qed_emit(qed_ctx *ctx, const qed_species *lepton, const qed_species *photons,
+             const qed_fields *f, int64_t step, qed_stream_t stream);
+
+/* Ballistic push + Method I Breit-Wheeler pair creation (Eqs. 3, 6) for every
+ * alive photon present when the call starts; pairs appended in photon order,
+ * the photon is marked dead. */
+int qed_pair(qed_ctx *ctx, const qed_species *photons, const qed_species *electrons,
+             const qed_species *positrons, const qed_fields *f, int64_t step,
+             qed_stream_t stream);
+
+/* Stable in-place removal of dead particles (alive == 0). */
+int qed_compact(qed_ctx *ctx, const qed_species *s, qed_stream_t stream);
+
+/* One fused QED-PIC step: electrons then positrons (gather at the old
+ * position, Boris push, emission with the same fields), then the photons that
+ * existed when the step began (push, pair creation).  Particles created in
+ * this step are first advanced in the next one.  Any of e, p may have
+ * capacity 0; g is required when e or p has particles. */
+int qed_step_fused(qed_ctx *ctx, const qed_species *e, const qed_species *p,
+                   const qed_species *g, const qed_fields *f, int64_t step,
+                   qed_stream_t stream);
+
+/* Isolated photon-energy sampler: xi[i] from Eq. (7) at (chi[i], gamma[i]),
+ * r2 from Philox(seed; id = i, step, sub 0, stream 0) word 1 (float arrays,
+ * device memory, QED_FP32 contexts). */
+int qed_sample_xi(qed_ctx *ctx, const float *chi, const float *gamma, float *xi, int64_t n,
+                  int64_t step, qed_stream_t stream);
+
+/* Rates from the tables, for parity checks.  which = 0: W_rad(chi, gamma)
+ * (photon emission with the xi_min cut); which = 1: W_pair(chi, gamma_ph).
+ * Device double arrays; evaluated in the context's precision. */
+int qed_rates(qed_ctx *ctx, int which, const double *chi, const double *gamma, double *W,
+              int64_t n, qed_stream_t stream);
+
+/* Inverse CDF from the tables, for parity checks.  which = 0: photon xi at
+ * (chi, gamma) for the uniform word w (u = (w + 1/2) 2^-32); which = 1: pair
+ * xi at chi.  Device arrays; evaluated in the context's precision. */
+int qed_sample_table(qed_ctx *ctx, int which, const double *chi, const double *gamma,
+                     const uint32_t *word, double *xi, int64_t n, qed_stream_t stream);
+
+/* Analytic standing wave (two counter-propagating circularly polarised waves
+ * of amplitude a0 each) sampled at the nodes of a grid as qed_fields.GRID. */
+int qed_fill_standing_wave(qed_ctx *ctx, float *grid, int nx, int ny, int nz, double x0,
+                           double dx, double a0, double t, qed_stream_t stream);
+
+/* Copy the FP64 master table `which` to host memory.  which: 0 photon
+ * ln-rate R(l), 1 photon forward kappa(l, y), 2 photon inverse ln delta(l,
+ * kappa), 3 pair ln-rate P(l), 4 pair inverse eta(l, kappa).  dims[0..5] gets
+ * (n0, n1, x0_0, h_0, x0_1, h_1) as doubles; n may be 0 to query dims only.
+ * Synchronous. */
+int qed_table_get(qed_ctx *ctx, int which, double *host_out, size_t n, double *dims);
+
+/* Counters: copy to host (synchronises `stream`) / zero them (async). */
+int qed_read_counters(qed_ctx *ctx, qed_counters *out, qed_stream_t stream);
+int qed_reset_counters(qed_ctx *ctx, qed_stream_t stream);
+
+/* Measurement hooks.  qed_profile_begin creates CUDA events (call it outside
+ * any timed or captured region) so that each of the next max_steps calls of
+ * qed_step_fused records events on its stream around its lepton kernel and
+ * its photon kernel.  qed_profile_end synchronises, returns the summed
+ * milliseconds of each kernel and the number of steps recorded, and releases
+ * the events. */
+int qed_profile_begin(qed_ctx *ctx, int max_steps);
+int qed_profile_end(qed_ctx *ctx, double *lepton_ms, double *photon_ms, int64_t *steps);
+
+/* Number of kernel launches this context has issued (for accounting). */
+int64_t qed_launch_count(const qed_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QED_H */

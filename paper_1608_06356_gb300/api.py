@@ -1,0 +1,295 @@
+"""Python face of libqed: the C-ABI calls under the same names, with torch
+tensors as the caller-owned device buffers.
+
+    ctx = qed_init_tables(config(dt=0.01))
+    e = Species.empty(capacity, q=-1, device="cuda")
+    qed_step_fused(ctx, e, p, g, Fields.uniform(E, B), step)
+
+Only marshalling happens here; all particle work is done by the kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _binding as B
+
+STATE = ("x", "y", "z", "px", "py", "pz", "w")
+FIELD_NAMES = ("ex", "ey", "ez", "bx", "by", "bz")
+
+
+def config(**kw) -> B.qed_config:
+    """qed_config with the library defaults, overridden by keyword."""
+    c = B.qed_config()
+    B.lib().qed_config_default(C.byref(c))
+    for k, v in kw.items():
+        if not hasattr(c, k):
+            raise KeyError(k)
+        setattr(c, k, v)
+    return c
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+class Context:
+    """Owns a qed_ctx (tables, scan state, counters)."""
+
+    def __init__(self, cfg: B.qed_config, stream=None):
+        self.cfg = cfg
+        self.handle = C.c_void_p()
+        B.check(B.lib().qed_init_tables(C.byref(cfg), C.byref(self.handle), _stream(stream)),
+                "qed_init_tables")
+        self.dtype = torch.float64 if cfg.precision == B.QED_FP64 else torch.float32
+
+    def close(self):
+        if self.handle:
+            B.lib().qed_destroy(self.handle)
+            self.handle = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def launches(self) -> int:
+        return B.lib().qed_launch_count(self.handle)
+
+
+def qed_init_tables(cfg: B.qed_config | None = None, stream=None) -> Context:
+    return Context(cfg if cfg is not None else config(), stream)
+
+
+def qed_destroy(ctx: Context) -> None:
+    ctx.close()
+
+
+@dataclass
+class Species:
+    """Structure-of-arrays particle buffers (torch device tensors)."""
+    x: torch.Tensor
+    y: torch.Tensor
+    z: torch.Tensor
+    px: torch.Tensor
+    py: torch.Tensor
+    pz: torch.Tensor
+    w: torch.Tensor
+    id: torch.Tensor          # int64 storage of the uint64 ids
+    n: torch.Tensor           # int64[1] device count
+    q: int
+    alive: torch.Tensor | None = None
+    ex: torch.Tensor | None = None
+    ey: torch.Tensor | None = None
+    ez: torch.Tensor | None = None
+    bx: torch.Tensor | None = None
+    by: torch.Tensor | None = None
+    bz: torch.Tensor | None = None
+
+    @property
+    def capacity(self) -> int:
+        return int(self.x.numel())
+
+    @staticmethod
+    def empty(capacity: int, q: int, dtype=torch.float32, device="cuda", fields=False,
+              alive=None) -> "Species":
+        cap = max(int(capacity), 0)
+        mk = lambda: torch.zeros(cap, dtype=dtype, device=device)
+        kw = {k: mk() for k in STATE}
+        if fields:
+            kw.update({k: mk() for k in FIELD_NAMES})
+        if alive is None:
+            alive = q == 0
+        return Species(id=torch.zeros(cap, dtype=torch.int64, device=device),
+                       n=torch.zeros(1, dtype=torch.int64, device=device), q=q,
+                       alive=torch.zeros(cap, dtype=torch.uint8, device=device) if alive else None,
+                       **kw)
+
+    def load(self, **arrays) -> "Species":
+        """Copy host/device arrays into the first n slots and set n."""
+        n = None
+        for k, v in arrays.items():
+            t = torch.as_tensor(np.ascontiguousarray(v)) if isinstance(v, np.ndarray) else v
+            if k == "id":
+                t = t.to(torch.int64) if t.dtype != torch.uint64 else t.view(torch.int64)
+            n = t.numel() if n is None else n
+            getattr(self, k)[:n].copy_(t.reshape(-1))
+        if self.alive is not None and "alive" not in arrays and n:
+            self.alive[:n] = 1
+        self.n.fill_(n or 0)
+        return self
+
+    def count(self) -> int:
+        return int(self.n.item())
+
+    def host(self, names=None) -> dict:
+        n = self.count()
+        names = names or [k for k in STATE + ("id", "alive") + FIELD_NAMES
+                          if getattr(self, k) is not None]
+        out = {}
+        for k in names:
+            t = getattr(self, k)
+            if t is None:
+                continue
+            a = t[:n].cpu().numpy()
+            out[k] = a.view(np.uint64) if k == "id" else a
+        return out
+
+    def struct(self) -> B.qed_species:
+        s = B.qed_species()
+        for k in STATE + FIELD_NAMES + ("id", "alive"):
+            t = getattr(self, k)
+            setattr(s, k, t.data_ptr() if t is not None and t.numel() else None)
+        s.d_n = self.n.data_ptr()
+        s.capacity = self.capacity
+        s.q = self.q
+        return s
+
+
+class Fields:
+    @staticmethod
+    def uniform(E, Bf) -> B.qed_fields:
+        f = B.qed_fields()
+        f.mode = B.QED_FIELDS_UNIFORM
+        for c in range(3):
+            f.e[c] = float(E[c])
+            f.b[c] = float(Bf[c])
+        return f
+
+    @staticmethod
+    def per_particle() -> B.qed_fields:
+        f = B.qed_fields()
+        f.mode = B.QED_FIELDS_PER_PARTICLE
+        return f
+
+    @staticmethod
+    def grid(grid: torch.Tensor, dx, dy, dz, x0=0.0, y0=0.0, z0=0.0) -> B.qed_fields:
+        assert grid.dtype == torch.float32 and grid.is_contiguous() and grid.shape[-1] == 8
+        nz, ny, nx = grid.shape[:3]
+        f = B.qed_fields()
+        f.mode = B.QED_FIELDS_GRID
+        f.nx, f.ny, f.nz = nx, ny, nz
+        f.grid = grid.data_ptr()
+        f.dx, f.dy, f.dz, f.x0, f.y0, f.z0 = dx, dy, dz, x0, y0, z0
+        f._keep = grid
+        return f
+
+
+def _sp(s: Species | None) -> B.qed_species:
+    if s is None:  # an empty species with a zero count
+        z = torch.zeros(1, dtype=torch.int64, device="cuda")
+        st = B.qed_species()
+        st.d_n = z.data_ptr()
+        st.capacity = 0
+        st._keep = z
+        return st
+    return s.struct()
+
+
+def qed_gather_push(ctx: Context, s: Species, f, step: int, stream=None) -> None:
+    B.check(B.lib().qed_gather_push(ctx.handle, C.byref(s.struct()), C.byref(f), int(step),
+                                    _stream(stream)), "qed_gather_push")
+
+
+def qed_emit(ctx: Context, lepton: Species, photons: Species, f, step: int, stream=None) -> None:
+    B.check(B.lib().qed_emit(ctx.handle, C.byref(lepton.struct()), C.byref(photons.struct()),
+                             C.byref(f), int(step), _stream(stream)), "qed_emit")
+
+
+def qed_pair(ctx: Context, photons: Species, electrons: Species, positrons: Species, f, step: int,
+             stream=None) -> None:
+    B.check(B.lib().qed_pair(ctx.handle, C.byref(photons.struct()), C.byref(electrons.struct()),
+                             C.byref(positrons.struct()), C.byref(f), int(step), _stream(stream)),
+            "qed_pair")
+
+
+def qed_compact(ctx: Context, s: Species, stream=None) -> None:
+    B.check(B.lib().qed_compact(ctx.handle, C.byref(s.struct()), _stream(stream)), "qed_compact")
+
+
+def qed_step_fused(ctx: Context, e: Species | None, p: Species | None, g: Species, f, step: int,
+                   stream=None) -> None:
+    se, sp_, sg = _sp(e), _sp(p), _sp(g)
+    B.check(B.lib().qed_step_fused(ctx.handle, C.byref(se), C.byref(sp_), C.byref(sg), C.byref(f),
+                                   int(step), _stream(stream)), "qed_step_fused")
+
+
+def qed_sample_xi(ctx: Context, chi: torch.Tensor, gamma: torch.Tensor, xi: torch.Tensor, step: int,
+                  stream=None) -> None:
+    n = chi.numel()
+    B.check(B.lib().qed_sample_xi(ctx.handle, chi.data_ptr(), gamma.data_ptr(), xi.data_ptr(), n,
+                                  int(step), _stream(stream)), "qed_sample_xi")
+
+
+def qed_rates(ctx: Context, which: int, chi: torch.Tensor, gamma: torch.Tensor,
+              stream=None) -> torch.Tensor:
+    chi = chi.to(torch.float64).contiguous()
+    gamma = gamma.to(torch.float64).contiguous()
+    out = torch.empty_like(chi)
+    B.check(B.lib().qed_rates(ctx.handle, int(which), chi.data_ptr(), gamma.data_ptr(),
+                              out.data_ptr(), chi.numel(), _stream(stream)), "qed_rates")
+    return out
+
+
+def qed_sample_table(ctx: Context, which: int, chi: torch.Tensor, gamma: torch.Tensor | None,
+                     word: torch.Tensor, stream=None) -> torch.Tensor:
+    chi = chi.to(torch.float64).contiguous()
+    g = gamma.to(torch.float64).contiguous() if gamma is not None else chi
+    word = word.to(torch.int32).contiguous()
+    out = torch.empty_like(chi)
+    B.check(B.lib().qed_sample_table(ctx.handle, int(which), chi.data_ptr(), g.data_ptr(),
+                                     word.data_ptr(), out.data_ptr(), chi.numel(), _stream(stream)),
+            "qed_sample_table")
+    return out
+
+
+def qed_fill_standing_wave(ctx: Context, grid: torch.Tensor, x0: float, dx: float, a0: float,
+                           t: float, stream=None) -> None:
+    nz, ny, nx = grid.shape[:3]
+    B.check(B.lib().qed_fill_standing_wave(ctx.handle, grid.data_ptr(), nx, ny, nz, float(x0),
+                                           float(dx), float(a0), float(t), _stream(stream)),
+            "qed_fill_standing_wave")
+
+
+def qed_table_get(ctx: Context, which: int):
+    """Returns (table as 2-D float64 array, grid info dict)."""
+    dims = (C.c_double * 6)()
+    B.check(B.lib().qed_table_get(ctx.handle, int(which), None, 0, dims), "qed_table_get")
+    n0, n1 = int(dims[0]), int(dims[1])
+    out = np.zeros(n0 * n1, dtype=np.float64)
+    B.check(B.lib().qed_table_get(ctx.handle, int(which), out.ctypes.data, out.size, dims),
+            "qed_table_get")
+    return out.reshape(n0, n1), {"n0": n0, "n1": n1, "x0_0": dims[2], "h_0": dims[3],
+                                 "x0_1": dims[4], "h_1": dims[5]}
+
+
+def qed_read_counters(ctx: Context, stream=None) -> dict:
+    c = B.qed_counters()
+    code = B.lib().qed_read_counters(ctx.handle, C.byref(c), _stream(stream))
+    if code not in (B.QED_OK, -5):
+        B.check(code, "qed_read_counters")
+    return c.as_dict()
+
+
+def qed_reset_counters(ctx: Context, stream=None) -> None:
+    B.check(B.lib().qed_reset_counters(ctx.handle, _stream(stream)), "qed_reset_counters")
+
+
+def qed_profile_begin(ctx: Context, max_steps: int) -> None:
+    B.check(B.lib().qed_profile_begin(ctx.handle, int(max_steps)), "qed_profile_begin")
+
+
+def qed_profile_end(ctx: Context) -> tuple[float, float, int]:
+    """(lepton kernel ms, photon kernel ms, steps recorded)."""
+    a, b, n = C.c_double(), C.c_double(), C.c_int64()
+    B.check(B.lib().qed_profile_end(ctx.handle, C.byref(a), C.byref(b), C.byref(n)), "qed_profile_end")
+    return a.value, b.value, n.value

@@ -1,0 +1,1054 @@
+// qed_step.cu -- the per-macroparticle QED Monte Carlo step on sm_103a.
+//
+// Every step kernel is persistent: a grid of (SM count x resident blocks)
+// CTAs takes 256-particle tiles from a device counter in increasing order.
+// Each thread owns one particle of the tile:
+//   leptons: field gather (uniform / per-particle / CIC) -> Boris push ->
+//            chi_e (Eq. 2) -> W_rad from the tables (Eq. 1 with the xi_min
+//            cut) -> N = max(1, ceil(W Dt / 0.2)) sub-steps -> Method I events
+//            with Philox draws -> xi from Eq. (7) -> recoil; photons appended.
+//   photons: ballistic push -> chi_ph (Eq. 3) -> W_pair (Eq. 6) -> Method I ->
+//            pair split xi (Eq. 6) -> e-/e+ appended, photon marked dead.
+// Appends keep particle order (and sub-step order within a particle): the
+// per-thread counts are scanned within the block and across tiles by a
+// single-pass decoupled look-back, so slot = count at launch + global prefix.
+// Particle state is structure-of-arrays; loads and stores of a tile are
+// coalesced 4-byte (FP32) or 8-byte (FP64) accesses.
+#include <cstdio>
+
+#include "qed_internal.h"
+
+namespace qed {
+
+template <class Real> struct Sp {
+  Real *x, *y, *z, *px, *py, *pz, *w;
+  uint64_t *id;
+  uint8_t *alive;
+  Real *ex, *ey, *ez, *bx, *by, *bz;
+  int64_t *d_n;
+  int64_t cap;
+  Real q;
+};
+
+template <class Real> struct Fld {
+  Real e[3], b[3];
+  const float *grid;
+  int nx, ny, nz;
+  Real idx, idy, idz, x0, y0, z0;
+};
+
+enum { FM_UNIFORM = 0, FM_PER_PARTICLE = 1, FM_GRID = 2 };
+enum { MODE_PUSH = 0, MODE_EMIT = 1, MODE_FUSED = 2 };
+
+struct Out {
+  qed_counters *cnt;
+  ScanState scan;
+};
+
+// CIC gather from grid[nz][ny][nx][8] (periodic).
+template <class Real>
+__device__ __forceinline__ void cic_gather(const Fld<Real> &f, Real x, Real y, Real z, Real E[3],
+                                           Real B[3]) {
+  Real fx = (x - f.x0) * f.idx, fy = (y - f.y0) * f.idy, fz = (z - f.z0) * f.idz;
+  Real ix = m_floor(fx), iy = m_floor(fy), iz = m_floor(fz);
+  Real wx = fx - ix, wy = fy - iy, wz = fz - iz;
+  long long i0 = (long long)ix, j0 = (long long)iy, k0 = (long long)iz;
+  i0 %= f.nx; if (i0 < 0) i0 += f.nx;
+  j0 %= f.ny; if (j0 < 0) j0 += f.ny;
+  k0 %= f.nz; if (k0 < 0) k0 += f.nz;
+  long long i1 = i0 + 1 == f.nx ? 0 : i0 + 1;
+  long long j1 = j0 + 1 == f.ny ? 0 : j0 + 1;
+  long long k1 = k0 + 1 == f.nz ? 0 : k0 + 1;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) { E[c] = (Real)0; B[c] = (Real)0; }
+#pragma unroll
+  for (int dk = 0; dk < 2; ++dk)
+#pragma unroll
+    for (int dj = 0; dj < 2; ++dj)
+#pragma unroll
+      for (int di = 0; di < 2; ++di) {
+        Real w = (di ? wx : (Real)1 - wx) * (dj ? wy : (Real)1 - wy) * (dk ? wz : (Real)1 - wz);
+        long long node = ((dk ? k1 : k0) * f.ny + (dj ? j1 : j0)) * f.nx + (di ? i1 : i0);
+        const float4 *pn = reinterpret_cast<const float4 *>(f.grid + 8 * node);
+        float4 a = __ldg(pn), b = __ldg(pn + 1);
+        E[0] += w * (Real)a.x; E[1] += w * (Real)a.y; E[2] += w * (Real)a.z;
+        B[0] += w * (Real)a.w; B[1] += w * (Real)b.x; B[2] += w * (Real)b.y;
+      }
+}
+
+// Relativistic Boris push; returns gamma after the push.
+template <class Real>
+__device__ __forceinline__ Real boris(Real &px, Real &py, Real &pz, const Real E[3],
+                                      const Real B[3], Real q, Real dt) {
+  Real h = (Real)0.5 * q * dt;
+  Real ux = px + h * E[0], uy = py + h * E[1], uz = pz + h * E[2];
+  Real gm = m_sqrt((Real)1 + ux * ux + uy * uy + uz * uz);
+  Real ig = h / gm;
+  Real tx = B[0] * ig, ty = B[1] * ig, tz = B[2] * ig;
+  Real t2 = tx * tx + ty * ty + tz * tz;
+  Real s = (Real)2 / ((Real)1 + t2);
+  Real sx = tx * s, sy = ty * s, sz = tz * s;
+  Real vx = ux + (uy * tz - uz * ty), vy = uy + (uz * tx - ux * tz), vz = uz + (ux * ty - uy * tx);
+  ux += vy * sz - vz * sy;
+  uy += vz * sx - vx * sz;
+  uz += vx * sy - vy * sx;
+  px = ux + h * E[0];
+  py = uy + h * E[1];
+  pz = uz + h * E[2];
+  return m_sqrt((Real)1 + px * px + py * py + pz * pz);
+}
+
+// ---------------------------------------------------------------------------
+// block-level tallies
+// ---------------------------------------------------------------------------
+struct BlockTally {
+  unsigned long long events, substeps, dropped, domain;
+  unsigned int status;
+  unsigned long long hist[64];
+};
+
+__device__ __forceinline__ void tally_flush(BlockTally *bt, const Tally &tl) {
+  // warp reduce then one shared atomic per warp
+  long long e = tl.events, s = tl.substeps, d = tl.dropped, m = tl.domain;
+  unsigned st = tl.status;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    e += __shfl_xor_sync(0xFFFFFFFFu, e, o);
+    s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    d += __shfl_xor_sync(0xFFFFFFFFu, d, o);
+    m += __shfl_xor_sync(0xFFFFFFFFu, m, o);
+    st |= __shfl_xor_sync(0xFFFFFFFFu, st, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (e) atomicAdd(&bt->events, (unsigned long long)e);
+    if (s) atomicAdd(&bt->substeps, (unsigned long long)s);
+    if (d) atomicAdd(&bt->dropped, (unsigned long long)d);
+    if (m) atomicAdd(&bt->domain, (unsigned long long)m);
+    if (st) atomicOr(&bt->status, st);
+  }
+}
+
+__device__ __forceinline__ void block_tally_init(BlockTally *bt) {
+  if (threadIdx.x == 0) {
+    bt->events = bt->substeps = bt->dropped = bt->domain = 0;
+    bt->status = 0;
+  }
+  for (int b = threadIdx.x; b < 64; b += blockDim.x) bt->hist[b] = 0;
+}
+
+// which: 0 -> emit_events, 1 -> pair_events
+__device__ __forceinline__ void block_tally_commit(BlockTally *bt, qed_counters *g, int which) {
+  if (threadIdx.x == 0) {
+    unsigned long long *ev = reinterpret_cast<unsigned long long *>(which ? &g->pair_events
+                                                                          : &g->emit_events);
+    if (bt->events) atomicAdd(ev, bt->events);
+    if (bt->substeps) atomicAdd(reinterpret_cast<unsigned long long *>(&g->substeps), bt->substeps);
+    if (bt->dropped) atomicAdd(reinterpret_cast<unsigned long long *>(&g->dropped), bt->dropped);
+    if (bt->domain) atomicAdd(reinterpret_cast<unsigned long long *>(&g->domain), bt->domain);
+    if (bt->status) atomicOr(&g->status, bt->status);
+  }
+  for (int b = threadIdx.x; b < 64; b += blockDim.x)
+    if (bt->hist[b]) atomicAdd(reinterpret_cast<unsigned long long *>(&g->hist[b]), bt->hist[b]);
+}
+
+// End of a persistent launch: the last CTA to finish resets the tile counter
+// and advances the epoch for the next launch.
+__device__ __forceinline__ void launch_epilogue(const ScanState &S, uint32_t epoch) {
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned int prev = atomicAdd(&S.sync[1], 1u);
+    if (prev == gridDim.x - 1) {
+      S.sync[0] = 0u;
+      S.sync[1] = 0u;
+      S.sync[2] = epoch + 1u;
+      __threadfence();
+    }
+  }
+}
+
+template <class Real>
+__device__ __forceinline__ void load_tables_smem(Real *dst, const Real *src, int n) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
+}
+
+// ---------------------------------------------------------------------------
+// Lepton kernel (electrons and positrons in one launch)
+// ---------------------------------------------------------------------------
+template <class Real> struct LeptonArgs {
+  Sp<Real> sp[2];
+  int nsp;
+  Sp<Real> ph;
+  Fld<Real> f;
+  Consts C;
+  Tables<Real> T;  // R, F staged to shared memory; Y read through L1/L2
+  Out o;
+  int64_t step;
+  uint8_t *heavy_flags;     // [main-pass slots] 1 = deferred to the heavy pass
+  const int *heavy_list;    // ordered main-pass slots of the deferred particles
+  const int64_t *heavy_n;   // length of heavy_list
+};
+
+template <class Real, int FM>
+__device__ __forceinline__ void get_fields(const Sp<Real> &s, const Fld<Real> &f, int64_t i,
+                                           Real x, Real y, Real z, Real E[3], Real B[3]) {
+  if (FM == FM_UNIFORM) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { E[c] = f.e[c]; B[c] = f.b[c]; }
+  } else if (FM == FM_PER_PARTICLE) {
+    E[0] = s.ex[i]; E[1] = s.ey[i]; E[2] = s.ez[i];
+    B[0] = s.bx[i]; B[1] = s.by[i]; B[2] = s.bz[i];
+  } else {
+    cic_gather(f, x, y, z, E, B);
+  }
+}
+
+template <class Real>
+__device__ __forceinline__ int spec_bin(const Consts &C, Real eps) {
+  if (!(eps >= (Real)C.spec_lo)) return -1;
+  Real b = m_floor((Real)C.spec_scale * m_log(eps / (Real)C.spec_lo));
+  if (b < (Real)0 || b >= (Real)64) return -1;
+  return (int)b;
+}
+
+template <class Real>
+__device__ __forceinline__ void write_child(const Sp<Real> &d, int64_t slot, Real x, Real y, Real z,
+                                            Real px, Real py, Real pz, Real w, uint64_t id,
+                                            const Real E[3], const Real B[3]) {
+  d.x[slot] = x; d.y[slot] = y; d.z[slot] = z;
+  d.px[slot] = px; d.py[slot] = py; d.pz[slot] = pz;
+  d.w[slot] = w;
+  d.id[slot] = id;
+  if (d.alive) d.alive[slot] = 1;
+  if (d.ex) {
+    d.ex[slot] = E[0]; d.ey[slot] = E[1]; d.ez[slot] = E[2];
+    d.bx[slot] = B[0]; d.by[slot] = B[1]; d.bz[slot] = B[2];
+  }
+}
+
+// Particles whose step needs more than HEAVY_SUBSTEPS generator sub-steps
+// are deferred by the main pass (no state is written for them) and processed
+// by a second pass over a compacted, ordered list of them.  Mixing them with
+// light particles would make every warp, and through the look-back every
+// tile in flight, wait for the slowest lane.
+constexpr int64_t HEAVY_SUBSTEPS = 8;
+enum { PASS_MAIN = 0, PASS_HEAVY = 1 };
+
+template <class Real, int FM, int MODE, int PASS>
+__global__ void __launch_bounds__(TILE) k_lepton(LeptonArgs<Real> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // FP32 tables are staged in shared memory; the finer FP64 tables are read
+  // through L1/L2 (the FP64 path serves small, launch-bound ensembles).
+  constexpr bool kSmem = sizeof(Real) == 4;
+  Real *sR = kSmem ? reinterpret_cast<Real *>(smem_raw) : const_cast<Real *>(A.T.R);
+  Real *sF = kSmem ? sR + A.T.gl.n : const_cast<Real *>(A.T.F);
+  __shared__ uint32_t scan_sm[33];
+  __shared__ long long s_meta[8];  // tile id, prefix, counts
+  __shared__ BlockTally bt;
+  constexpr bool emit = MODE != MODE_PUSH;
+  constexpr bool defer = emit && PASS == PASS_MAIN;
+  if (emit && kSmem) {
+    load_tables_smem(sR, A.T.R, A.T.gl.n);
+    load_tables_smem(sF, A.T.F, A.T.gl.n * A.T.gy.n);
+  }
+  block_tally_init(&bt);
+  if (threadIdx.x == 0) {
+    s_meta[2] = *(volatile int64_t *)A.sp[0].d_n;
+    s_meta[3] = A.nsp > 1 ? *(volatile int64_t *)A.sp[1].d_n : 0;
+    s_meta[4] = emit ? *(volatile int64_t *)A.ph.d_n : 0;
+    s_meta[5] = (long long)A.o.scan.sync[2];
+    s_meta[6] = PASS == PASS_HEAVY ? *(volatile int64_t *)A.heavy_n : 0;
+  }
+  __syncthreads();
+  const int64_t n0 = s_meta[2], n1 = s_meta[3], nph = s_meta[4];
+  const uint32_t epoch = (uint32_t)s_meta[5];
+  const int64_t T0 = (n0 + TILE - 1) / TILE, T1 = (n1 + TILE - 1) / TILE;
+  const int64_t nheavy = s_meta[6];
+  const int64_t ntiles = PASS == PASS_HEAVY ? (nheavy + TILE - 1) / TILE : T0 + T1;
+  const double inv_aS = 1.0 / A.C.a_S;
+  const Real dt = (Real)A.C.dt;
+  Tally tl;
+  tl.clear();
+
+  for (;;) {
+    if (threadIdx.x == 0) s_meta[0] = (long long)atomicAdd(&A.o.scan.sync[0], 1u);
+    __syncthreads();
+    const int64_t t = s_meta[0];
+    __syncthreads();
+    if (t >= ntiles) break;
+    // this lane's particle: species si, index i (main-pass slot g = tile * TILE + lane)
+    int64_t g_slot;
+    bool active;
+    if (PASS == PASS_HEAVY) {
+      const int64_t h = t * TILE + threadIdx.x;
+      active = h < nheavy;
+      g_slot = active ? (int64_t)A.heavy_list[h] : 0;
+    } else {
+      g_slot = t * TILE + threadIdx.x;
+      active = true;
+    }
+    const int64_t tile_main = g_slot / TILE;
+    const int si = tile_main < T0 ? 0 : 1;
+    const Sp<Real> &S = A.sp[si];
+    const int64_t i = (tile_main - (si ? T0 : 0)) * TILE + (g_slot % TILE);
+    active = active && i < (si ? n1 : n0);
+
+    Real x = 0, y = 0, z = 0, px = 0, py = 0, pz = 0, wt = 0, g = 1;
+    Real E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
+    uint64_t pid = 0;
+    uint32_t cnt = 0;
+    uint8_t heavy = 0;
+    Real nx = 0, ny = 0, nz = 0;
+    Real eph0 = 0, eph1 = 0;
+    int64_t k0 = 0, k1 = 0;
+    // state at the start of the emission loop (for a replay when cnt > 2)
+    Real g_init = 1, chi_init = 0;
+    RateOut<Real> ro_init{0, 0, 0};
+    int64_t N = 1;
+    if (active) {
+      x = S.x[i]; y = S.y[i]; z = S.z[i];
+      px = S.px[i]; py = S.py[i]; pz = S.pz[i];
+      get_fields<Real, FM>(S, A.f, i, x, y, z, E, B);
+      if (emit) { wt = S.w[i]; pid = S.id[i]; }
+      if (MODE != MODE_EMIT) {
+        g = boris(px, py, pz, E, B, S.q, dt);
+        Real ig = dt / g;
+        x += px * ig; y += py * ig; z += pz * ig;
+      } else {
+        g = m_sqrt((Real)1 + px * px + py * py + pz * pz);
+      }
+      if (!(g < (Real)1e30)) { tl.status |= QED_STATUS_NONFINITE; }
+      else if (emit) {
+        Real chi = chi_lepton(px, py, pz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
+        Tally t0;
+        t0.clear();
+        RateOut<Real> ro = photon_rate(sR, sF, A.T, A.C, chi, g, t0);
+        Real wdt = ro.W * dt;
+        if (wdt > (Real)A.C.wdt_max) {
+          double nn = ceil((double)wdt / A.C.wdt_max);
+          if (nn > (double)A.C.max_substeps) {
+            nn = (double)A.C.max_substeps;
+            t0.status |= QED_STATUS_SUBSTEPS;
+          }
+          N = (int64_t)nn;
+        }
+        if (defer && N > HEAVY_SUBSTEPS) {
+          heavy = 1;  // the heavy pass redoes this particle from its stored state
+        } else {
+          tl.status |= t0.status;
+          tl.domain += t0.domain;
+          const Real dts = dt / (Real)N;
+          tl.substeps += N;
+          Real pm = m_sqrt(px * px + py * py + pz * pz);
+          if (pm > (Real)0) { Real ip = (Real)1 / pm; nx = px * ip; ny = py * ip; nz = pz * ip; }
+          g_init = g; chi_init = chi; ro_init = ro;
+          for (int64_t k = 0; k < N; ++k) {
+            U4 r = draw(A.C.seed, pid, A.step, k, STREAM_EMIT);
+            if (!(ro.W * dts > unif<Real>(r.x))) continue;
+            XiOut<Real> xo = photon_xi(A.T.Y, A.T, ro.l, chi, ro.kmin, unif<Real>(r.y),
+                                       unif<Real>(~r.y), tl);
+            // eps_ph = xi gamma directly (gamma - gamma(1-xi) cancels for soft photons)
+            Real g2 = g * xo.omxi, eph = g * xo.xi;
+            if (g2 < (Real)1) { g2 = (Real)1; eph = g - (Real)1; }
+            if (cnt == 0) { eph0 = eph; k0 = k; }
+            else if (cnt == 1) { eph1 = eph; k1 = k; }
+            ++cnt;
+            Real pm2 = m_sqrt((g2 - (Real)1) * (g2 + (Real)1));
+            px = pm2 * nx; py = pm2 * ny; pz = pm2 * nz;
+            g = g2;
+            chi = chi_lepton(px, py, pz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
+            ro = photon_rate(sR, sF, A.T, A.C, chi, g, tl);
+          }
+          tl.events += cnt;
+        }
+      }
+      if (!heavy) {
+        if (MODE != MODE_EMIT) { S.x[i] = x; S.y[i] = y; S.z[i] = z; }
+        if (MODE != MODE_EMIT || cnt) { S.px[i] = px; S.py[i] = py; S.pz[i] = pz; }
+      }
+    }
+    if (defer) A.heavy_flags[t * TILE + threadIdx.x] = heavy;
+    if (!emit) continue;
+
+    // ---- stable append: block scan + decoupled look-back
+    uint32_t excl = block_excl_scan(cnt, scan_sm);
+    uint32_t agg = scan_sm[32];
+    if (threadIdx.x < 32) {
+      uint32_t st = 0;
+      uint32_t pre = lookback_warp(A.o.scan, t, epoch, agg, st);
+      if (threadIdx.x == 0) {
+        s_meta[1] = pre;
+        if (st) tl.status |= st;
+        if (t == ntiles - 1) {  // last tile: publish the new photon count
+          int64_t nn = nph + (int64_t)pre + agg;
+          *A.ph.d_n = nn < A.ph.cap ? nn : A.ph.cap;
+        }
+      }
+    }
+    __syncthreads();
+    const int64_t base = nph + s_meta[1] + excl;
+    if (cnt) {
+      const Real Ec[3] = {E[0], E[1], E[2]}, Bc[3] = {B[0], B[1], B[2]};
+      if (cnt <= 2) {
+        for (uint32_t j = 0; j < cnt; ++j) {
+          Real eph = j == 0 ? eph0 : eph1;
+          int64_t kk = j == 0 ? k0 : k1;
+          int b = spec_bin(A.C, eph);
+          if (b >= 0) atomicAdd(&bt.hist[b], 1ull);
+          int64_t slot = base + j;
+          if (slot >= A.ph.cap) { tl.dropped += 1; tl.status |= QED_STATUS_CAPACITY; continue; }
+          U4 cid = draw(A.C.seed, pid, A.step, kk, STREAM_PHOTON_ID);
+          write_child(A.ph, slot, x, y, z, eph * nx, eph * ny, eph * nz, wt,
+                      (uint64_t)cid.x | ((uint64_t)cid.y << 32), Ec, Bc);
+        }
+      } else {
+        // replay the emission loop (deterministic: same draws, same tables)
+        Tally dummy;
+        dummy.clear();
+        Real gg = g_init, chi = chi_init;
+        RateOut<Real> ro = ro_init;
+        const Real dts = dt / (Real)N;
+        uint32_t j = 0;
+        for (int64_t k = 0; k < N && j < cnt; ++k) {
+          U4 r = draw(A.C.seed, pid, A.step, k, STREAM_EMIT);
+          if (!(ro.W * dts > unif<Real>(r.x))) continue;
+          XiOut<Real> xo = photon_xi(A.T.Y, A.T, ro.l, chi, ro.kmin, unif<Real>(r.y),
+                                     unif<Real>(~r.y), dummy);
+          Real g2 = gg * xo.omxi, eph = gg * xo.xi;
+          if (g2 < (Real)1) { g2 = (Real)1; eph = gg - (Real)1; }
+          int b = spec_bin(A.C, eph);
+          if (b >= 0) atomicAdd(&bt.hist[b], 1ull);
+          int64_t slot = base + j;
+          ++j;
+          if (slot >= A.ph.cap) {
+            tl.dropped += 1;
+            tl.status |= QED_STATUS_CAPACITY;
+          } else {
+            U4 cid = draw(A.C.seed, pid, A.step, k, STREAM_PHOTON_ID);
+            write_child(A.ph, slot, x, y, z, eph * nx, eph * ny, eph * nz, wt,
+                        (uint64_t)cid.x | ((uint64_t)cid.y << 32), Ec, Bc);
+          }
+          Real pm2 = m_sqrt((g2 - (Real)1) * (g2 + (Real)1));
+          gg = g2;
+          chi = chi_lepton(pm2 * nx, pm2 * ny, pm2 * nz, gg, E[0], E[1], E[2], B[0], B[1], B[2],
+                           inv_aS);
+          ro = photon_rate(sR, sF, A.T, A.C, chi, gg, dummy);
+        }
+      }
+    }
+  }
+  tally_flush(&bt, tl);
+  __syncthreads();
+  block_tally_commit(&bt, A.o.cnt, 0);
+  launch_epilogue(A.o.scan, epoch);
+}
+
+// ---------------------------------------------------------------------------
+// Ordered list of the deferred (heavy) particles: stable compaction of the
+// main pass's flags, one flag per main-pass slot (tile * TILE + lane).
+// ---------------------------------------------------------------------------
+struct HeavyListArgs {
+  const uint8_t *flags;
+  int *list;
+  int64_t *count;
+  const int64_t *n0, *n1;  // species counts (sizes the main pass's slot range)
+  Out o;
+};
+
+__global__ void __launch_bounds__(TILE) k_heavy_list(HeavyListArgs A) {
+  __shared__ uint32_t scan_sm[33];
+  __shared__ long long s_meta[8];
+  if (threadIdx.x == 0) {
+    int64_t n0 = *(volatile const int64_t *)A.n0;
+    int64_t n1 = A.n1 ? *(volatile const int64_t *)A.n1 : 0;
+    s_meta[2] = ((n0 + TILE - 1) / TILE + (n1 + TILE - 1) / TILE);
+    s_meta[5] = (long long)A.o.scan.sync[2];
+  }
+  __syncthreads();
+  const int64_t ntiles = s_meta[2];
+  const uint32_t epoch = (uint32_t)s_meta[5];
+  uint32_t status = 0;
+  if (ntiles == 0 && blockIdx.x == 0 && threadIdx.x == 0) *A.count = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_meta[0] = (long long)atomicAdd(&A.o.scan.sync[0], 1u);
+    __syncthreads();
+    const int64_t t = s_meta[0];
+    __syncthreads();
+    if (t >= ntiles) break;
+    const int64_t slot = t * TILE + threadIdx.x;
+    uint32_t f = A.flags[slot] ? 1u : 0u;
+    uint32_t excl = block_excl_scan(f, scan_sm);
+    uint32_t agg = scan_sm[32];
+    if (threadIdx.x < 32) {
+      uint32_t pre = lookback_warp(A.o.scan, t, epoch, agg, status);
+      if (threadIdx.x == 0) {
+        s_meta[1] = pre;
+        if (t == ntiles - 1) *A.count = (int64_t)pre + agg;
+      }
+    }
+    __syncthreads();
+    if (f) A.list[s_meta[1] + excl] = (int)slot;
+  }
+  if (threadIdx.x == 0 && status) atomicOr(&A.o.cnt->status, status);
+  launch_epilogue(A.o.scan, epoch);
+}
+
+// ---------------------------------------------------------------------------
+// Photon kernel: push + Breit-Wheeler pairs
+// ---------------------------------------------------------------------------
+template <class Real> struct PhotonArgs {
+  Sp<Real> ph, el, po;
+  const int64_t *n_active;  // photons [0, *n_active) are processed
+  Fld<Real> f;
+  Consts C;
+  Tables<Real> T;
+  Out o;
+  int64_t step;
+};
+
+template <class Real, int FM>
+__global__ void __launch_bounds__(TILE) k_photon(PhotonArgs<Real> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real *sP = reinterpret_cast<Real *>(smem_raw);
+  __shared__ uint32_t scan_sm[33];
+  __shared__ long long s_meta[8];
+  __shared__ BlockTally bt;
+  load_tables_smem(sP, A.T.P, A.T.glp.n);
+  block_tally_init(&bt);
+  if (threadIdx.x == 0) {
+    s_meta[2] = *(volatile const int64_t *)A.n_active;
+    s_meta[3] = *(volatile int64_t *)A.el.d_n;
+    s_meta[4] = *(volatile int64_t *)A.po.d_n;
+    s_meta[5] = (long long)A.o.scan.sync[2];
+  }
+  __syncthreads();
+  const int64_t n = s_meta[2], ne = s_meta[3], np = s_meta[4];
+  const uint32_t epoch = (uint32_t)s_meta[5];
+  const int64_t ntiles = (n + TILE - 1) / TILE;
+  const double inv_aS = 1.0 / A.C.a_S;
+  const Real dt = (Real)A.C.dt;
+  Tally tl;
+  tl.clear();
+  for (;;) {
+    if (threadIdx.x == 0) s_meta[0] = (long long)atomicAdd(&A.o.scan.sync[0], 1u);
+    __syncthreads();
+    const int64_t t = s_meta[0];
+    __syncthreads();
+    if (t >= ntiles) break;
+    const int64_t i = t * TILE + threadIdx.x;
+    bool active = i < n;
+    if (active && A.ph.alive) active = A.ph.alive[i] != 0;
+    Real x = 0, y = 0, z = 0, px = 0, py = 0, pz = 0, wt = 0, k = 0;
+    Real E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
+    uint64_t pid = 0;
+    uint32_t cnt = 0;
+    Real ge = 0, gp = 0;
+    int64_t ks = 0;
+    if (active) {
+      x = A.ph.x[i]; y = A.ph.y[i]; z = A.ph.z[i];
+      px = A.ph.px[i]; py = A.ph.py[i]; pz = A.ph.pz[i];
+      wt = A.ph.w[i]; pid = A.ph.id[i];
+      get_fields<Real, FM>(A.ph, A.f, i, x, y, z, E, B);
+      k = m_sqrt(px * px + py * py + pz * pz);
+      if (k > (Real)0) {
+        Real ik = dt / k;
+        x += px * ik; y += py * ik; z += pz * ik;
+        A.ph.x[i] = x; A.ph.y[i] = y; A.ph.z[i] = z;
+      }
+      Real chi = chi_photon(px, py, pz, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
+      RateOut<Real> ro = pair_rate(sP, A.T, A.C, chi, k, tl);
+      int64_t N = 1;
+      Real wdt = ro.W * dt;
+      if (wdt > (Real)A.C.wdt_max) {
+        double nn = ceil((double)wdt / A.C.wdt_max);
+        if (nn > (double)A.C.max_substeps) { nn = (double)A.C.max_substeps; tl.status |= QED_STATUS_SUBSTEPS; }
+        N = (int64_t)nn;
+      }
+      const Real dts = dt / (Real)N;
+      tl.substeps += N;
+      for (int64_t s = 0; s < N; ++s) {
+        U4 r = draw(A.C.seed, pid, A.step, s, STREAM_PAIR);
+        if (!(ro.W * dts > unif<Real>(r.x))) continue;
+        XiOut<Real> xo = pair_xi(A.T.Yp, A.T, ro.l, unif<Real>(r.y), unif<Real>(~r.y));
+        ge = xo.xi * k;
+        gp = xo.omxi * k;
+        if (ge < (Real)1) { ge = (Real)1; gp = k - (Real)1; }
+        if (gp < (Real)1) { gp = (Real)1; ge = k - (Real)1; }
+        ks = s;
+        cnt = 1;
+        A.ph.alive[i] = 0;
+        break;
+      }
+      tl.events += cnt;
+    }
+    uint32_t excl = block_excl_scan(cnt, scan_sm);
+    uint32_t agg = scan_sm[32];
+    if (threadIdx.x < 32) {
+      uint32_t st = 0;
+      uint32_t pre = lookback_warp(A.o.scan, t, epoch, agg, st);
+      if (threadIdx.x == 0) {
+        s_meta[1] = pre;
+        if (st) tl.status |= st;
+        if (t == ntiles - 1) {
+          int64_t tot = (int64_t)pre + agg;
+          *A.el.d_n = ne + tot < A.el.cap ? ne + tot : A.el.cap;
+          *A.po.d_n = np + tot < A.po.cap ? np + tot : A.po.cap;
+        }
+      }
+    }
+    __syncthreads();
+    if (cnt) {
+      const int64_t off = s_meta[1] + excl;
+      Real ik = (Real)1 / k;
+      Real nx = px * ik, ny = py * ik, nz = pz * ik;
+      U4 cid = draw(A.C.seed, pid, A.step, ks, STREAM_PAIR_ID);
+      Real pe = m_sqrt((ge - (Real)1) * (ge + (Real)1));
+      Real pp = m_sqrt((gp - (Real)1) * (gp + (Real)1));
+      if (ne + off < A.el.cap)
+        write_child(A.el, ne + off, x, y, z, pe * nx, pe * ny, pe * nz, wt,
+                    (uint64_t)cid.x | ((uint64_t)cid.y << 32), E, B);
+      else { tl.dropped += 1; tl.status |= QED_STATUS_CAPACITY; }
+      if (np + off < A.po.cap)
+        write_child(A.po, np + off, x, y, z, pp * nx, pp * ny, pp * nz, wt,
+                    (uint64_t)cid.z | ((uint64_t)cid.w << 32), E, B);
+      else { tl.dropped += 1; tl.status |= QED_STATUS_CAPACITY; }
+    }
+  }
+  tally_flush(&bt, tl);
+  __syncthreads();
+  block_tally_commit(&bt, A.o.cnt, 1);
+  launch_epilogue(A.o.scan, epoch);
+}
+
+// ---------------------------------------------------------------------------
+// Stable in-place compaction of dead particles (alive == 0).  Every tile loads
+// its particles into registers before it publishes its count, and a tile
+// writes only below the end of its own range, after every earlier tile has
+// published -- so no data is overwritten before it has been read.
+// ---------------------------------------------------------------------------
+template <class Real> struct CompactArgs {
+  Sp<Real> s;
+  Out o;
+};
+
+template <class Real>
+__global__ void __launch_bounds__(TILE) k_compact(CompactArgs<Real> A) {
+  __shared__ uint32_t scan_sm[33];
+  __shared__ long long s_meta[8];
+  if (threadIdx.x == 0) {
+    s_meta[2] = *(volatile int64_t *)A.s.d_n;
+    s_meta[5] = (long long)A.o.scan.sync[2];
+  }
+  __syncthreads();
+  const int64_t n = s_meta[2];
+  const uint32_t epoch = (uint32_t)s_meta[5];
+  const int64_t ntiles = (n + TILE - 1) / TILE;
+  const bool fields = A.s.ex != nullptr;
+  uint32_t status = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_meta[0] = (long long)atomicAdd(&A.o.scan.sync[0], 1u);
+    __syncthreads();
+    const int64_t t = s_meta[0];
+    __syncthreads();
+    if (t >= ntiles) break;
+    const int64_t i = t * TILE + threadIdx.x;
+    uint32_t keep = 0;
+    Real v[13];
+    uint64_t id = 0;
+    if (i < n && A.s.alive[i]) {
+      keep = 1;
+      v[0] = A.s.x[i]; v[1] = A.s.y[i]; v[2] = A.s.z[i];
+      v[3] = A.s.px[i]; v[4] = A.s.py[i]; v[5] = A.s.pz[i]; v[6] = A.s.w[i];
+      id = A.s.id[i];
+      if (fields) {
+        v[7] = A.s.ex[i]; v[8] = A.s.ey[i]; v[9] = A.s.ez[i];
+        v[10] = A.s.bx[i]; v[11] = A.s.by[i]; v[12] = A.s.bz[i];
+      }
+    }
+    uint32_t excl = block_excl_scan(keep, scan_sm);
+    uint32_t agg = scan_sm[32];
+    if (threadIdx.x < 32) {
+      uint32_t pre = lookback_warp(A.o.scan, t, epoch, agg, status);
+      if (threadIdx.x == 0) {
+        s_meta[1] = pre;
+        if (t == ntiles - 1) *A.s.d_n = (int64_t)pre + agg;
+      }
+    }
+    __syncthreads();
+    if (keep) {
+      int64_t d = s_meta[1] + excl;
+      A.s.x[d] = v[0]; A.s.y[d] = v[1]; A.s.z[d] = v[2];
+      A.s.px[d] = v[3]; A.s.py[d] = v[4]; A.s.pz[d] = v[5]; A.s.w[d] = v[6];
+      A.s.id[d] = id;
+      A.s.alive[d] = 1;
+      if (fields) {
+        A.s.ex[d] = v[7]; A.s.ey[d] = v[8]; A.s.ez[d] = v[9];
+        A.s.bx[d] = v[10]; A.s.by[d] = v[11]; A.s.bz[d] = v[12];
+      }
+    }
+  }
+  if (threadIdx.x == 0 && status) atomicOr(&A.o.cnt->status, status);
+  launch_epilogue(A.o.scan, epoch);
+}
+
+// ---------------------------------------------------------------------------
+// Snapshot of the photon count at the start of a fused step.
+// ---------------------------------------------------------------------------
+__global__ void k_snapshot(const int64_t *src, int64_t *dst) { *dst = *src; }
+
+// ---------------------------------------------------------------------------
+// Isolated sampler (xi at given chi, gamma; r2 from Philox(i, step)).
+// ---------------------------------------------------------------------------
+struct SampleArgs {
+  const float *chi, *gamma;
+  float *xi;
+  int64_t n, step;
+  Consts C;
+  Tables<float> T;
+  Out o;
+};
+
+__global__ void __launch_bounds__(TILE) k_sample_xi(SampleArgs A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float *sR = reinterpret_cast<float *>(smem_raw);
+  float *sF = sR + A.T.gl.n;
+  load_tables_smem(sR, A.T.R, A.T.gl.n);
+  load_tables_smem(sF, A.T.F, A.T.gl.n * A.T.gy.n);
+  __syncthreads();
+  Tally tl;
+  tl.clear();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += stride) {
+    float chi = __ldcs(A.chi + i), g = __ldcs(A.gamma + i);
+    RateOut<float> ro = photon_rate(sR, sF, A.T, A.C, chi, g, tl);
+    U4 r = draw(A.C.seed, (uint64_t)i, A.step, 0, STREAM_EMIT);
+    float xi = 0.f;
+    if (ro.W > 0.f) {
+      XiOut<float> xo = photon_xi(A.T.Y, A.T, ro.l, chi, ro.kmin, unif<float>(r.y),
+                                  unif<float>(~r.y), tl);
+      xi = xo.xi;
+    }
+    __stcs(A.xi + i, xi);
+  }
+  if (tl.status) atomicOr(&A.o.cnt->status, tl.status);
+}
+
+// ---------------------------------------------------------------------------
+// Parity helpers: rates and inverse CDF at given inputs (tables in global).
+// ---------------------------------------------------------------------------
+template <class Real> struct EvalArgs {
+  int which;
+  const double *chi, *gamma;
+  const uint32_t *word;
+  double *out;
+  int64_t n;
+  Consts C;
+  Tables<Real> T;
+};
+
+template <class Real> __global__ void k_eval_rates(EvalArgs<Real> A) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  Tally tl;
+  tl.clear();
+  Real chi = (Real)A.chi[i], g = (Real)A.gamma[i];
+  if (A.which == 0)
+    A.out[i] = (double)photon_rate(A.T.R, A.T.F, A.T, A.C, chi, g, tl).W;
+  else
+    A.out[i] = (double)pair_rate(A.T.P, A.T, A.C, chi, g, tl).W;
+}
+
+template <class Real> __global__ void k_eval_xi(EvalArgs<Real> A) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= A.n) return;
+  Tally tl;
+  tl.clear();
+  Real chi = (Real)A.chi[i];
+  uint32_t w = A.word[i];
+  if (A.which == 0) {
+    Real g = (Real)A.gamma[i];
+    RateOut<Real> ro = photon_rate(A.T.R, A.T.F, A.T, A.C, chi, g, tl);
+    XiOut<Real> xo = photon_xi(A.T.Y, A.T, ro.l, chi, ro.kmin, unif<Real>(w), unif<Real>(~w), tl);
+    A.out[i] = (double)xo.xi;
+  } else {
+    RateOut<Real> ro = pair_rate(A.T.P, A.T, A.C, chi, (Real)1e6, tl);
+    Real l = ro.l;
+    if (!(chi >= (Real)A.C.chi_pair_min)) l = A.T.glp.lo;
+    XiOut<Real> xo = pair_xi(A.T.Yp, A.T, l, unif<Real>(w), unif<Real>(~w));
+    A.out[i] = (double)xo.xi;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Standing wave E = 2 a0 cos x (0, cos t, sin t), B = 2 a0 sin x (0, cos t,
+// sin t) on grid[nz][ny][nx][8].  Each block computes the nx node values of
+// one x-row once (FP64 cos/sin) and streams them over its (y, z) rows.
+// ---------------------------------------------------------------------------
+__global__ void k_fill_standing_wave(float *grid, int nx, int ny, int nz, double x0, double dx,
+                                     double a0, double t) {
+  extern __shared__ __align__(16) float4 srow[];  // [nx][2]
+  const double ct = cos(t), st = sin(t);
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    double x = x0 + (double)i * dx;
+    double cx = 2.0 * a0 * cos(x), sx = 2.0 * a0 * sin(x);
+    srow[2 * i] = make_float4(0.f, (float)(cx * ct), (float)(cx * st), 0.f);
+    srow[2 * i + 1] = make_float4((float)(sx * ct), (float)(sx * st), 0.f, 0.f);
+  }
+  __syncthreads();
+  const int64_t rows = (int64_t)ny * nz;
+  const int64_t total = rows * nx * 2;  // float4 units
+  float4 *g4 = reinterpret_cast<float4 *>(grid);
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    int64_t within = q % (2 * (int64_t)nx);
+    __stcs(g4 + q, srow[within]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launch helpers
+// ---------------------------------------------------------------------------
+template <class Real> Sp<Real> to_sp(const qed_species *s) {
+  Sp<Real> d{};
+  if (!s) return d;
+  d.x = (Real *)s->x; d.y = (Real *)s->y; d.z = (Real *)s->z;
+  d.px = (Real *)s->px; d.py = (Real *)s->py; d.pz = (Real *)s->pz; d.w = (Real *)s->w;
+  d.id = s->id; d.alive = s->alive;
+  d.ex = (Real *)s->ex; d.ey = (Real *)s->ey; d.ez = (Real *)s->ez;
+  d.bx = (Real *)s->bx; d.by = (Real *)s->by; d.bz = (Real *)s->bz;
+  d.d_n = s->d_n; d.cap = s->capacity; d.q = (Real)s->q;
+  return d;
+}
+
+template <class Real> Fld<Real> to_fld(const qed_fields *f) {
+  Fld<Real> d{};
+  for (int c = 0; c < 3; ++c) { d.e[c] = (Real)f->e[c]; d.b[c] = (Real)f->b[c]; }
+  d.grid = f->grid;
+  d.nx = f->nx; d.ny = f->ny; d.nz = f->nz;
+  if (f->mode == QED_FIELDS_GRID) {
+    d.idx = (Real)(1.0 / f->dx); d.idy = (Real)(1.0 / f->dy); d.idz = (Real)(1.0 / f->dz);
+  }
+  d.x0 = (Real)f->x0; d.y0 = (Real)f->y0; d.z0 = (Real)f->z0;
+  return d;
+}
+
+template <class Real> Tables<Real> tables_of(const qed_ctx *c);
+template <> Tables<float> tables_of<float>(const qed_ctx *c) {
+  return Tables<float>{c->R32, c->F32, c->Y32, c->P32, c->Yp32, to_r<float>(c->gl),
+                       to_r<float>(c->gy), to_r<float>(c->gk), to_r<float>(c->glp),
+                       to_r<float>(c->gkp)};
+}
+template <> Tables<double> tables_of<double>(const qed_ctx *c) {
+  return Tables<double>{c->R64, c->F64, c->Y64, c->P64, c->Yp64, to_r<double>(c->gl),
+                        to_r<double>(c->gy), to_r<double>(c->gk), to_r<double>(c->glp),
+                        to_r<double>(c->gkp)};
+}
+
+Consts consts_of(const qed_ctx *c) {
+  Consts k{};
+  k.a_S = c->cfg.a_S;
+  k.alpha = c->cfg.alpha;
+  k.dt = c->cfg.dt;
+  k.wdt_max = c->cfg.wdt_max;
+  k.xi_min_energy = c->cfg.xi_min_energy;
+  k.chi_pair_min = c->cfg.chi_pair_min;
+  k.spec_lo = c->cfg.spec_lo;
+  k.spec_scale = 64.0 / log(c->cfg.spec_hi / c->cfg.spec_lo);
+  k.seed = c->cfg.seed;
+  k.max_substeps = c->cfg.max_substeps;
+  k.pair_sign = c->cfg.pair_sign;
+  return k;
+}
+
+Out out_of(const qed_ctx *c) {
+  return Out{c->d_counters, ScanState{c->tile_state, c->sync, c->max_tiles}};
+}
+
+template <class Real> size_t lepton_smem(const qed_ctx *c) {
+  return sizeof(Real) * ((size_t)c->gl.n + (size_t)c->gl.n * c->gy.n);
+}
+
+template <class Real, int FM, int MODE, int PASS>
+static cudaError_t launch_lepton_pass(qed_ctx *c, const LeptonArgs<Real> &a, cudaStream_t st) {
+  size_t sm = (MODE == MODE_PUSH || sizeof(Real) == 8) ? 0 : lepton_smem<Real>(c);
+  auto kern = k_lepton<Real, FM, MODE, PASS>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE, sm);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  kern<<<c->num_sms * per_sm, TILE, sm, st>>>(a);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+// Main pass, then (for emission) the ordered list of deferred particles and
+// the heavy pass over it.
+template <class Real, int FM, int MODE>
+static cudaError_t launch_lepton_t(qed_ctx *c, const LeptonArgs<Real> &a, cudaStream_t st) {
+  cudaError_t e = launch_lepton_pass<Real, FM, MODE, PASS_MAIN>(c, a, st);
+  if (e != cudaSuccess || MODE == MODE_PUSH) return e;
+  HeavyListArgs h{};
+  h.flags = a.heavy_flags;
+  h.list = c->heavy_list;
+  h.count = c->heavy_n;
+  h.n0 = a.sp[0].d_n;
+  h.n1 = a.nsp > 1 ? a.sp[1].d_n : nullptr;
+  h.o = a.o;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_heavy_list, TILE, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  k_heavy_list<<<c->num_sms * per_sm, TILE, 0, st>>>(h);
+  c->launches += 1;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_lepton_pass<Real, FM, MODE, PASS_HEAVY>(c, a, st);
+}
+
+template <class Real, int MODE>
+static cudaError_t launch_lepton_m(qed_ctx *c, const LeptonArgs<Real> &a, int fm, cudaStream_t st) {
+  if (fm == QED_FIELDS_UNIFORM) return launch_lepton_t<Real, FM_UNIFORM, MODE>(c, a, st);
+  if (fm == QED_FIELDS_PER_PARTICLE) return launch_lepton_t<Real, FM_PER_PARTICLE, MODE>(c, a, st);
+  return launch_lepton_t<Real, FM_GRID, MODE>(c, a, st);
+}
+
+template <class Real>
+cudaError_t launch_lepton(qed_ctx *c, const qed_species *s0, const qed_species *s1,
+                          const qed_species *ph, const qed_fields *f, int64_t step, int mode,
+                          cudaStream_t st) {
+  LeptonArgs<Real> a{};
+  a.sp[0] = to_sp<Real>(s0);
+  a.nsp = s1 ? 2 : 1;
+  if (s1) a.sp[1] = to_sp<Real>(s1);
+  a.ph = to_sp<Real>(ph);
+  a.f = to_fld<Real>(f);
+  a.C = consts_of(c);
+  a.T = tables_of<Real>(c);
+  a.o = out_of(c);
+  a.step = step;
+  a.heavy_flags = c->heavy_flags;
+  a.heavy_list = c->heavy_list;
+  a.heavy_n = c->heavy_n;
+  if (mode == MODE_PUSH) return launch_lepton_m<Real, MODE_PUSH>(c, a, f->mode, st);
+  if (mode == MODE_EMIT) return launch_lepton_m<Real, MODE_EMIT>(c, a, f->mode, st);
+  return launch_lepton_m<Real, MODE_FUSED>(c, a, f->mode, st);
+}
+
+template <class Real, int FM>
+static cudaError_t launch_photon_t(qed_ctx *c, const PhotonArgs<Real> &a, cudaStream_t st) {
+  size_t sm = sizeof(Real) * (size_t)c->glp.n;
+  auto kern = k_photon<Real, FM>;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE, sm);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  kern<<<c->num_sms * per_sm, TILE, sm, st>>>(a);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+template <class Real>
+cudaError_t launch_photon(qed_ctx *c, const qed_species *g, const qed_species *e,
+                          const qed_species *p, const int64_t *n_active, const qed_fields *f,
+                          int64_t step, cudaStream_t st) {
+  PhotonArgs<Real> a{};
+  a.ph = to_sp<Real>(g);
+  a.el = to_sp<Real>(e);
+  a.po = to_sp<Real>(p);
+  a.n_active = n_active;
+  a.f = to_fld<Real>(f);
+  a.C = consts_of(c);
+  a.T = tables_of<Real>(c);
+  a.o = out_of(c);
+  a.step = step;
+  if (f->mode == QED_FIELDS_UNIFORM) return launch_photon_t<Real, FM_UNIFORM>(c, a, st);
+  if (f->mode == QED_FIELDS_PER_PARTICLE) return launch_photon_t<Real, FM_PER_PARTICLE>(c, a, st);
+  return launch_photon_t<Real, FM_GRID>(c, a, st);
+}
+
+template <class Real>
+cudaError_t launch_compact(qed_ctx *c, const qed_species *s, cudaStream_t st) {
+  CompactArgs<Real> a{};
+  a.s = to_sp<Real>(s);
+  a.o = out_of(c);
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_compact<Real>, TILE, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  k_compact<Real><<<c->num_sms * per_sm, TILE, 0, st>>>(a);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_snapshot(qed_ctx *c, const int64_t *src, int64_t *dst, cudaStream_t st) {
+  k_snapshot<<<1, 1, 0, st>>>(src, dst);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sample_xi(qed_ctx *c, const float *chi, const float *gamma, float *xi,
+                             int64_t n, int64_t step, cudaStream_t st) {
+  SampleArgs a{};
+  a.chi = chi; a.gamma = gamma; a.xi = xi; a.n = n; a.step = step;
+  a.C = consts_of(c);
+  a.T = tables_of<float>(c);
+  a.o = out_of(c);
+  size_t sm = lepton_smem<float>(c);
+  cudaError_t e = cudaFuncSetAttribute(k_sample_xi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample_xi, TILE, sm);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  k_sample_xi<<<c->num_sms * per_sm, TILE, sm, st>>>(a);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+template <class Real>
+cudaError_t launch_eval(qed_ctx *c, int kind, int which, const double *chi, const double *gamma,
+                        const uint32_t *word, double *out, int64_t n, cudaStream_t st) {
+  EvalArgs<Real> a{};
+  a.which = which; a.chi = chi; a.gamma = gamma; a.word = word; a.out = out; a.n = n;
+  a.C = consts_of(c);
+  a.T = tables_of<Real>(c);
+  unsigned blocks = (unsigned)((n + 255) / 256);
+  if (blocks == 0) return cudaSuccess;
+  if (kind == 0) k_eval_rates<Real><<<blocks, 256, 0, st>>>(a);
+  else k_eval_xi<Real><<<blocks, 256, 0, st>>>(a);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill(qed_ctx *c, float *grid, int nx, int ny, int nz, double x0, double dx,
+                        double a0, double t, cudaStream_t st) {
+  size_t sm = sizeof(float4) * 2 * (size_t)nx;
+  cudaError_t e = cudaFuncSetAttribute(k_fill_standing_wave,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_fill_standing_wave<<<c->num_sms * 4, 256, sm, st>>>(grid, nx, ny, nz, x0, dx, a0, t);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_lepton<float>(qed_ctx *, const qed_species *, const qed_species *,
+                                          const qed_species *, const qed_fields *, int64_t, int,
+                                          cudaStream_t);
+template cudaError_t launch_lepton<double>(qed_ctx *, const qed_species *, const qed_species *,
+                                           const qed_species *, const qed_fields *, int64_t, int,
+                                           cudaStream_t);
+template cudaError_t launch_photon<float>(qed_ctx *, const qed_species *, const qed_species *,
+                                          const qed_species *, const int64_t *, const qed_fields *,
+                                          int64_t, cudaStream_t);
+template cudaError_t launch_photon<double>(qed_ctx *, const qed_species *, const qed_species *,
+                                           const qed_species *, const int64_t *, const qed_fields *,
+                                           int64_t, cudaStream_t);
+template cudaError_t launch_compact<float>(qed_ctx *, const qed_species *, cudaStream_t);
+template cudaError_t launch_compact<double>(qed_ctx *, const qed_species *, cudaStream_t);
+template cudaError_t launch_eval<float>(qed_ctx *, int, int, const double *, const double *,
+                                        const uint32_t *, double *, int64_t, cudaStream_t);
+template cudaError_t launch_eval<double>(qed_ctx *, int, int, const double *, const double *,
+                                         const uint32_t *, double *, int64_t, cudaStream_t);
+
+}  // namespace qed

@@ -1,0 +1,99 @@
+"""Host-side checks of the C-ABI boundary (no GPU needed): the shared library
+loads, it exports every function include/qed.h declares, the Python binding
+covers each of them, and the ctypes struct layouts match the C compiler's."""
+import ctypes as C
+import os
+import re
+import subprocess
+import textwrap
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "qed.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qed_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def qlib():
+    from paper_1608_06356_gb300 import build, _binding
+    build()
+    return _binding
+
+
+def test_library_exports_every_declared_symbol(qlib):
+    names = _declared_functions()
+    assert "qed_init_tables" in names and "qed_step_fused" in names
+    lib = C.CDLL(qlib.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(qlib.SIGNATURES), set(names) ^ set(qlib.SIGNATURES)
+
+
+def test_struct_layouts_match_c(qlib, tmp_path):
+    src = tmp_path / "sz.c"
+    src.write_text(textwrap.dedent("""
+        #include <stdio.h>
+        #include <stddef.h>
+        #include "qed.h"
+        int main(void) {
+          printf("%zu %zu %zu %zu\\n", sizeof(qed_config), sizeof(qed_species),
+                 sizeof(qed_fields), sizeof(qed_counters));
+          printf("%zu %zu %zu %zu\\n", offsetof(qed_config, seed), offsetof(qed_species, d_n),
+                 offsetof(qed_fields, grid), offsetof(qed_counters, hist));
+          return 0;
+        }"""))
+    exe = tmp_path / "sz"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = subprocess.check_output([str(exe)], text=True).split()
+    B = qlib
+    assert [int(v) for v in out[:4]] == [C.sizeof(B.qed_config), C.sizeof(B.qed_species),
+                                         C.sizeof(B.qed_fields), C.sizeof(B.qed_counters)]
+    assert [int(v) for v in out[4:]] == [B.qed_config.seed.offset, B.qed_species.d_n.offset,
+                                         B.qed_fields.grid.offset, B.qed_counters.hist.offset]
+
+
+def test_config_defaults_and_strerror(qlib):
+    lib = qlib.lib()
+    c = qlib.qed_config()
+    lib.qed_config_default(C.byref(c))
+    assert c.wdt_max == 0.2 and c.xi_min_energy == 2.0 and c.pair_sign == 1
+    assert abs(c.alpha - 1 / 137.035999) < 1e-15 and c.a_S == 412148.45
+    assert lib.qed_strerror(-1) == b"invalid argument"
+    assert lib.qed_strerror(0) == b"ok"
+
+
+def test_invalid_arguments_rejected_without_gpu(qlib):
+    # argument checks run on the host before any CUDA call
+    lib = qlib.lib()
+    c = qlib.qed_config()
+    lib.qed_config_default(C.byref(c))
+    c.dt = -1.0
+    h = C.c_void_p()
+    assert lib.qed_init_tables(C.byref(c), C.byref(h), None) == -1
+    assert lib.qed_step_fused(None, None, None, None, None, 0, None) == -1
+    assert lib.qed_sample_xi(None, None, None, None, 4, 0, None) == -1
+    assert lib.qed_table_get(None, 1, None, 0, None) == -1
+
+
+def test_workload_generators_are_seeded():
+    from paper_1608_06356_gb300 import workloads as W
+    a, _, _ = W.chi_target(1000, seed=3)
+    b, chi, g = W.chi_target(1000, seed=3)
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k])
+    # B is perpendicular to p and sized for the target chi
+    p = np.stack([a["px"], a["py"], a["pz"]])
+    Bv = np.stack([a["bx"], a["by"], a["bz"]])
+    assert np.max(np.abs((p * Bv).sum(0)) / (np.linalg.norm(p, axis=0) * np.linalg.norm(Bv, axis=0))) < 1e-12
+    np.testing.assert_allclose(np.linalg.norm(p, axis=0) * np.linalg.norm(Bv, axis=0) / W.A_S_1UM, chi,
+                               rtol=1e-12)
+    e = W.ensemble(500, seed=1)
+    gam = np.sqrt(1 + e["px"] ** 2 + e["py"] ** 2 + e["pz"] ** 2)
+    assert gam.min() >= 100 * (1 - 1e-12) and gam.max() <= 1e4 * (1 + 1e-12)
