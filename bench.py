@@ -220,8 +220,9 @@ def main():
     # photon/pair capacity: ~0.25 emissions per electron per step at Dt = 0.01 at the start,
     # falling as the ensemble cools; dead photons are compacted every step
     cap_g = int(n * 0.3 * (total_steps + 1)) + 4096
-    cap_e = 2 * n
-    cap_p = n
+    # the photons of the hottest electrons create pairs (a cascade): room for the leptons it adds
+    cap_e = 3 * n
+    cap_p = 2 * n
     ctx = api.qed_init_tables(api.config(dt=DT, seed=1 + rank, max_particles=max(cap_g, cap_e)))
     host = host_workload(n, seed=rank)
     host["id"] += np.uint64(rank) << np.uint64(40)

@@ -191,7 +191,7 @@ extern "C" int qed_init_tables(const qed_config *cfg, qed_ctx **out, qed_stream_
       cudaMalloc(&c->sync, sizeof(unsigned int) * 4) != cudaSuccess ||
       cudaMalloc(&c->snap, sizeof(int64_t) * 4) != cudaSuccess ||
       cudaMalloc(&c->d_counters, sizeof(qed_counters)) != cudaSuccess ||
-      cudaMalloc(&c->heavy_flags, (size_t)c->max_tiles * TILE) != cudaSuccess ||
+      cudaMalloc(&c->heavy_flags, (size_t)c->max_tiles * TILE + 4096) != cudaSuccess ||
       cudaMalloc(&c->heavy_list, sizeof(int) * (size_t)c->max_tiles * TILE) != cudaSuccess ||
       cudaMalloc(&c->heavy_n, sizeof(int64_t)) != cudaSuccess) {
     free_ctx(c);

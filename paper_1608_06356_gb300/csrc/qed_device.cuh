@@ -141,7 +141,18 @@ struct Consts {
   uint64_t seed;
   int64_t max_substeps;
   int pair_sign;
+  double inv_aS, alpha_aS;  // 1/a_S and alpha a_S
+  // the same constants in single precision, so that the FP32 path does no FP64 work
+  float f_dt, f_wdt_max, f_xi_min_energy, f_chi_pair_min, f_spec_lo, f_spec_scale, f_inv_aS,
+      f_alpha_aS;
 };
+
+// Constant in the working precision.
+template <class Real> __device__ __forceinline__ Real sel(double d, float f);
+template <> __device__ __forceinline__ float sel<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double sel<double>(double d, float) { return d; }
+__device__ __forceinline__ float m_ceil(float x) { return ceilf(x); }
+__device__ __forceinline__ double m_ceil(double x) { return ceil(x); }
 
 // Status/counter accumulation per thread, reduced per block.
 struct Tally {
@@ -174,12 +185,12 @@ __device__ __forceinline__ double chi_lepton_d(double px, double py, double pz, 
 
 template <class Real>
 __device__ __forceinline__ Real chi_lepton(Real px, Real py, Real pz, Real g, Real ex, Real ey,
-                                           Real ez, Real bx, Real by, Real bz, double inv_aS) {
+                                           Real ez, Real bx, Real by, Real bz, Real inv_aS) {
   if (sizeof(Real) == 8) {
-    return (Real)chi_lepton_d(px, py, pz, ex, ey, ez, bx, by, bz, inv_aS);
+    return (Real)chi_lepton_d(px, py, pz, ex, ey, ez, bx, by, bz, (double)inv_aS);
   }
   Real p2 = px * px + py * py + pz * pz;
-  if (!(p2 > (Real)0)) return m_sqrt(ex * ex + ey * ey + ez * ez) * (Real)inv_aS;
+  if (!(p2 > (Real)0)) return m_sqrt(ex * ex + ey * ey + ez * ez) * inv_aS;
   Real ip = (Real)1 / m_sqrt(p2);
   Real nx = px * ip, ny = py * ip, nz = pz * ip;
   Real epar = nx * ex + ny * ey + nz * ez;
@@ -198,14 +209,14 @@ __device__ __forceinline__ Real chi_lepton(Real px, Real py, Real pz, Real g, Re
     double qx = g64 * ax + ((double)py * bz - (double)pz * by);
     double qy = g64 * ay + ((double)pz * bx - (double)px * bz);
     double qz = g64 * az + ((double)px * by - (double)py * bx);
-    return (Real)(sqrt(ep * ep + qx * qx + qy * qy + qz * qz) * inv_aS);
+    return (Real)(sqrt(ep * ep + qx * qx + qy * qy + qz * qz) * (double)inv_aS);
   }
-  return m_sqrt(epar * epar + d2) * (Real)inv_aS;
+  return m_sqrt(epar * epar + d2) * inv_aS;
 }
 
 template <class Real>
 __device__ __forceinline__ Real chi_photon(Real px, Real py, Real pz, Real ex, Real ey, Real ez,
-                                           Real bx, Real by, Real bz, double inv_aS) {
+                                           Real bx, Real by, Real bz, Real inv_aS) {
   if (sizeof(Real) == 8) {
     double k = sqrt((double)px * px + (double)py * py + (double)pz * pz);
     if (!(k > 0.0)) return (Real)0;
@@ -213,7 +224,7 @@ __device__ __forceinline__ Real chi_photon(Real px, Real py, Real pz, Real ex, R
     double fx = ex + ny * bz - nz * by, fy = ey + nz * bx - nx * bz, fz = ez + nx * by - ny * bx;
     double ne = nx * ex + ny * ey + nz * ez;
     double s = fx * fx + fy * fy + fz * fz - ne * ne;
-    return (Real)(s > 0.0 ? k * sqrt(s) * inv_aS : 0.0);
+    return (Real)(s > 0.0 ? k * sqrt(s) * (double)inv_aS : 0.0);
   }
   Real k2 = px * px + py * py + pz * pz;
   if (!(k2 > (Real)0)) return (Real)0;
@@ -232,9 +243,9 @@ __device__ __forceinline__ Real chi_photon(Real px, Real py, Real pz, Real ex, R
     double qx = ((double)ex - ep * n6x) + (n6y * bz - n6z * by);
     double qy = ((double)ey - ep * n6y) + (n6z * bx - n6x * bz);
     double qz = ((double)ez - ep * n6z) + (n6x * by - n6y * bx);
-    return (Real)(k6 * sqrt(qx * qx + qy * qy + qz * qz) * inv_aS);
+    return (Real)(k6 * sqrt(qx * qx + qy * qy + qz * qz) * (double)inv_aS);
   }
-  return k * m_sqrt(d2) * (Real)inv_aS;
+  return k * m_sqrt(d2) * inv_aS;
 }
 
 // ---------------------------------------------------------------------------
@@ -249,7 +260,7 @@ __device__ __forceinline__ RateOut<Real> photon_rate(const Real *R, const Real *
                                                      Real chi, Real gamma, Tally &tl) {
   RateOut<Real> o{(Real)0, (Real)-1e30, (Real)0};
   if (!(chi > (Real)0)) return o;
-  Real xi_min = (Real)C.xi_min_energy / gamma;
+  Real xi_min = sel<Real>(C.xi_min_energy, C.f_xi_min_energy) / gamma;
   if (!(xi_min < (Real)1)) return o;
   Real l = m_log(chi);
   Real shift = (Real)0;  // ln-rate extrapolation below chi_min: int dW ~ chi
@@ -283,7 +294,7 @@ __device__ __forceinline__ RateOut<Real> photon_rate(const Real *R, const Real *
     o.kmin = kmin;
     wmin = m_exp(kmin);
   }
-  o.W = (Real)(C.alpha * C.a_S) / gamma * m_exp(lnG - wmin);
+  o.W = sel<Real>(C.alpha_aS, C.f_alpha_aS) / gamma * m_exp(lnG - wmin);
   return o;
 }
 
@@ -320,7 +331,7 @@ __device__ __forceinline__ RateOut<Real> pair_rate(const Real *P, const Tables<R
                                                    const Consts &C, Real chi, Real gamma,
                                                    Tally &tl) {
   RateOut<Real> o{(Real)0, (Real)0, (Real)0};
-  if (!(gamma >= (Real)2) || !(chi >= (Real)C.chi_pair_min)) return o;
+  if (!(gamma >= (Real)2) || !(chi >= sel<Real>(C.chi_pair_min, C.f_chi_pair_min))) return o;
   Real l = m_log(chi);
   if (l > T.glp.hi) {
     l = T.glp.hi;
@@ -329,7 +340,7 @@ __device__ __forceinline__ RateOut<Real> pair_rate(const Real *P, const Tables<R
   }
   o.l = l;
   Real lnH = interp1(P, T.glp, l) - (Real)(8.0 / 3.0) * m_exp(-l);
-  o.W = (Real)(C.alpha * C.a_S) / gamma * m_exp(lnH);
+  o.W = sel<Real>(C.alpha_aS, C.f_alpha_aS) / gamma * m_exp(lnH);
   return o;
 }
 

@@ -204,8 +204,9 @@ __device__ __forceinline__ void get_fields(const Sp<Real> &s, const Fld<Real> &f
 
 template <class Real>
 __device__ __forceinline__ int spec_bin(const Consts &C, Real eps) {
-  if (!(eps >= (Real)C.spec_lo)) return -1;
-  Real b = m_floor((Real)C.spec_scale * m_log(eps / (Real)C.spec_lo));
+  const Real lo = sel<Real>(C.spec_lo, C.f_spec_lo);
+  if (!(eps >= lo)) return -1;
+  Real b = m_floor(sel<Real>(C.spec_scale, C.f_spec_scale) * m_log(eps / lo));
   if (b < (Real)0 || b >= (Real)64) return -1;
   return (int)b;
 }
@@ -234,7 +235,7 @@ constexpr int64_t HEAVY_SUBSTEPS = 8;
 enum { PASS_MAIN = 0, PASS_HEAVY = 1 };
 
 template <class Real, int FM, int MODE, int PASS>
-__global__ void __launch_bounds__(TILE) k_lepton(LeptonArgs<Real> A) {
+__global__ void __launch_bounds__(TILE, 3) k_lepton(LeptonArgs<Real> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // FP32 tables are staged in shared memory; the finer FP64 tables are read
   // through L1/L2 (the FP64 path serves small, launch-bound ensembles).
@@ -264,8 +265,8 @@ __global__ void __launch_bounds__(TILE) k_lepton(LeptonArgs<Real> A) {
   const int64_t T0 = (n0 + TILE - 1) / TILE, T1 = (n1 + TILE - 1) / TILE;
   const int64_t nheavy = s_meta[6];
   const int64_t ntiles = PASS == PASS_HEAVY ? (nheavy + TILE - 1) / TILE : T0 + T1;
-  const double inv_aS = 1.0 / A.C.a_S;
-  const Real dt = (Real)A.C.dt;
+  const Real inv_aS = sel<Real>(A.C.inv_aS, A.C.f_inv_aS);
+  const Real dt = sel<Real>(A.C.dt, A.C.f_dt);
   Tally tl;
   tl.clear();
 
@@ -323,10 +324,11 @@ __global__ void __launch_bounds__(TILE) k_lepton(LeptonArgs<Real> A) {
         t0.clear();
         RateOut<Real> ro = photon_rate(sR, sF, A.T, A.C, chi, g, t0);
         Real wdt = ro.W * dt;
-        if (wdt > (Real)A.C.wdt_max) {
-          double nn = ceil((double)wdt / A.C.wdt_max);
-          if (nn > (double)A.C.max_substeps) {
-            nn = (double)A.C.max_substeps;
+        const Real wdt_max = sel<Real>(A.C.wdt_max, A.C.f_wdt_max);
+        if (wdt > wdt_max) {
+          Real nn = m_ceil(wdt / wdt_max);
+          if (nn > (Real)A.C.max_substeps) {
+            nn = (Real)A.C.max_substeps;
             t0.status |= QED_STATUS_SUBSTEPS;
           }
           N = (int64_t)nn;
@@ -443,16 +445,108 @@ __global__ void __launch_bounds__(TILE) k_lepton(LeptonArgs<Real> A) {
 }
 
 // ---------------------------------------------------------------------------
+// Streaming pass over all leptons: gather, push, chi, rate and the first
+// Method I draw, with no block-wide synchronisation.  A particle that needs
+// one sub-step and draws no event is finished here (its new position and
+// momentum are written); the rest are only flagged -- 1: one sub-step with an
+// event, 2: more than one sub-step -- and are redone, from their unchanged
+// stored state, by the ordered passes that append photons.
+// ---------------------------------------------------------------------------
+template <class Real, int FM, int MODE>
+__global__ void __launch_bounds__(TILE) k_lepton_stream(LeptonArgs<Real> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr bool kSmem = sizeof(Real) == 4;
+  Real *sR = kSmem ? reinterpret_cast<Real *>(smem_raw) : const_cast<Real *>(A.T.R);
+  Real *sF = kSmem ? sR + A.T.gl.n : const_cast<Real *>(A.T.F);
+  __shared__ long long s_meta[4];
+  __shared__ BlockTally bt;
+  if (kSmem) {
+    load_tables_smem(sR, A.T.R, A.T.gl.n);
+    load_tables_smem(sF, A.T.F, A.T.gl.n * A.T.gy.n);
+  }
+  block_tally_init(&bt);
+  if (threadIdx.x == 0) {
+    s_meta[0] = *(volatile int64_t *)A.sp[0].d_n;
+    s_meta[1] = A.nsp > 1 ? *(volatile int64_t *)A.sp[1].d_n : 0;
+  }
+  __syncthreads();
+  const int64_t n0 = s_meta[0], n1 = s_meta[1];
+  const int64_t T0 = (n0 + TILE - 1) / TILE, T1 = (n1 + TILE - 1) / TILE;
+  const int64_t nslots = (T0 + T1) * TILE;
+  const Real inv_aS = sel<Real>(A.C.inv_aS, A.C.f_inv_aS);
+  const Real dt = sel<Real>(A.C.dt, A.C.f_dt), wdt_max = sel<Real>(A.C.wdt_max, A.C.f_wdt_max);
+  Tally tl;
+  tl.clear();
+  for (int64_t slot = blockIdx.x * (int64_t)TILE + threadIdx.x; slot < nslots;
+       slot += (int64_t)gridDim.x * TILE) {
+    const int64_t tile = slot / TILE;
+    const int si = tile < T0 ? 0 : 1;
+    const Sp<Real> &S = A.sp[si];
+    const int64_t i = (tile - (si ? T0 : 0)) * TILE + (slot % TILE);
+    uint8_t flag = 0;
+    if (i < (si ? n1 : n0)) {
+      Real x = S.x[i], y = S.y[i], z = S.z[i];
+      Real px = S.px[i], py = S.py[i], pz = S.pz[i];
+      Real E[3], B[3];
+      get_fields<Real, FM>(S, A.f, i, x, y, z, E, B);
+      const uint64_t pid = S.id[i];
+      Real g;
+      if (MODE != MODE_EMIT) {
+        g = boris(px, py, pz, E, B, S.q, dt);
+        Real ig = dt / g;
+        x += px * ig; y += py * ig; z += pz * ig;
+      } else {
+        g = m_sqrt((Real)1 + px * px + py * py + pz * pz);
+      }
+      if (!(g < (Real)1e30)) {
+        tl.status |= QED_STATUS_NONFINITE;
+      } else {
+        Real chi = chi_lepton(px, py, pz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
+        Tally t0;
+        t0.clear();
+        RateOut<Real> ro = photon_rate(sR, sF, A.T, A.C, chi, g, t0);
+        Real wdt = ro.W * dt;
+        if (wdt > wdt_max) {
+          // classes by sub-step count N = ceil(W Dt / wdt_max): 2: N <= 3, 3: N <= 7,
+          // 4: N <= 15, 5: N >= 16 (lanes of a warp then do similar amounts of work)
+          const Real q = wdt / wdt_max;
+          flag = q <= (Real)3 ? 2 : (q <= (Real)7 ? 3 : (q <= (Real)15 ? 4 : 5));
+        } else {
+          U4 r = draw(A.C.seed, pid, A.step, 0, STREAM_EMIT);
+          if (wdt > unif<Real>(r.x)) flag = 1;
+        }
+        if (flag == 0) {
+          tl.status |= t0.status;
+          tl.domain += t0.domain;
+          tl.substeps += 1;
+          if (MODE != MODE_EMIT) {
+            S.x[i] = x; S.y[i] = y; S.z[i] = z;
+            S.px[i] = px; S.py[i] = py; S.pz[i] = pz;
+          }
+        }
+      }
+    }
+    A.heavy_flags[slot] = flag;
+  }
+  tally_flush(&bt, tl);
+  __syncthreads();
+  block_tally_commit(&bt, A.o.cnt, 0);
+}
+
+// ---------------------------------------------------------------------------
 // Ordered list of the deferred (heavy) particles: stable compaction of the
 // main pass's flags, one flag per main-pass slot (tile * TILE + lane).
 // ---------------------------------------------------------------------------
 struct HeavyListArgs {
   const uint8_t *flags;
+  uint8_t want;  // flag value to collect
   int *list;
   int64_t *count;
   const int64_t *n0, *n1;  // species counts (sizes the main pass's slot range)
   Out o;
 };
+
+constexpr int LIST_ITEMS = 16;  // flags per thread (one 16-byte load)
 
 __global__ void __launch_bounds__(TILE) k_heavy_list(HeavyListArgs A) {
   __shared__ uint32_t scan_sm[33];
@@ -460,11 +554,13 @@ __global__ void __launch_bounds__(TILE) k_heavy_list(HeavyListArgs A) {
   if (threadIdx.x == 0) {
     int64_t n0 = *(volatile const int64_t *)A.n0;
     int64_t n1 = A.n1 ? *(volatile const int64_t *)A.n1 : 0;
-    s_meta[2] = ((n0 + TILE - 1) / TILE + (n1 + TILE - 1) / TILE);
+    s_meta[2] = ((n0 + TILE - 1) / TILE + (n1 + TILE - 1) / TILE) * TILE;  // flag slots
     s_meta[5] = (long long)A.o.scan.sync[2];
   }
   __syncthreads();
-  const int64_t ntiles = s_meta[2];
+  const int64_t nslots = s_meta[2];
+  const int64_t per_tile = (int64_t)TILE * LIST_ITEMS;
+  const int64_t ntiles = (nslots + per_tile - 1) / per_tile;
   const uint32_t epoch = (uint32_t)s_meta[5];
   uint32_t status = 0;
   if (ntiles == 0 && blockIdx.x == 0 && threadIdx.x == 0) *A.count = 0;
@@ -474,9 +570,16 @@ __global__ void __launch_bounds__(TILE) k_heavy_list(HeavyListArgs A) {
     const int64_t t = s_meta[0];
     __syncthreads();
     if (t >= ntiles) break;
-    const int64_t slot = t * TILE + threadIdx.x;
-    uint32_t f = A.flags[slot] ? 1u : 0u;
-    uint32_t excl = block_excl_scan(f, scan_sm);
+    const int64_t first = t * per_tile + (int64_t)threadIdx.x * LIST_ITEMS;
+    uint4 raw = make_uint4(0, 0, 0, 0);
+    if (first < nslots) raw = *reinterpret_cast<const uint4 *>(A.flags + first);
+    const uint8_t *fl = reinterpret_cast<const uint8_t *>(&raw);
+    uint32_t mask = 0;
+#pragma unroll
+    for (int j = 0; j < LIST_ITEMS; ++j)
+      if (fl[j] == A.want && first + j < nslots) mask |= 1u << j;
+    uint32_t cnt = __popc(mask);
+    uint32_t excl = block_excl_scan(cnt, scan_sm);
     uint32_t agg = scan_sm[32];
     if (threadIdx.x < 32) {
       uint32_t pre = lookback_warp(A.o.scan, t, epoch, agg, status);
@@ -486,10 +589,114 @@ __global__ void __launch_bounds__(TILE) k_heavy_list(HeavyListArgs A) {
       }
     }
     __syncthreads();
-    if (f) A.list[s_meta[1] + excl] = (int)slot;
+    int64_t out = s_meta[1] + excl;
+    while (mask) {
+      int j = __ffs(mask) - 1;
+      mask &= mask - 1;
+      A.list[out++] = (int)(first + j);
+    }
   }
   if (threadIdx.x == 0 && status) atomicOr(&A.o.cnt->status, status);
   launch_epilogue(A.o.scan, epoch);
+}
+
+// ---------------------------------------------------------------------------
+// Single-event pass: particles whose one sub-step drew an event (class 1 of
+// the streaming pass) each emit exactly one photon, so the photon of list
+// entry h goes to slot (count at launch) + h -- no scan is needed.  The
+// particle is redone from its stored state; the streaming pass's decision is
+// taken as given.  The last CTA to finish publishes the new photon count.
+// ---------------------------------------------------------------------------
+template <class Real, int FM, int MODE>
+__global__ void __launch_bounds__(TILE) k_lepton_emit1(LeptonArgs<Real> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr bool kSmem = sizeof(Real) == 4;
+  Real *sR = kSmem ? reinterpret_cast<Real *>(smem_raw) : const_cast<Real *>(A.T.R);
+  Real *sF = kSmem ? sR + A.T.gl.n : const_cast<Real *>(A.T.F);
+  __shared__ long long s_meta[8];
+  __shared__ BlockTally bt;
+  if (kSmem) {
+    load_tables_smem(sR, A.T.R, A.T.gl.n);
+    load_tables_smem(sF, A.T.F, A.T.gl.n * A.T.gy.n);
+  }
+  block_tally_init(&bt);
+  if (threadIdx.x == 0) {
+    s_meta[0] = *(volatile int64_t *)A.sp[0].d_n;
+    s_meta[1] = *(volatile const int64_t *)A.heavy_n;
+    s_meta[2] = *(volatile int64_t *)A.ph.d_n;
+    s_meta[3] = (long long)A.o.scan.sync[2];
+  }
+  __syncthreads();
+  const int64_t n0 = s_meta[0], nl = s_meta[1], base = s_meta[2];
+  const uint32_t epoch = (uint32_t)s_meta[3];
+  const int64_t T0 = (n0 + TILE - 1) / TILE;
+  const Real inv_aS = sel<Real>(A.C.inv_aS, A.C.f_inv_aS);
+  const Real dt = sel<Real>(A.C.dt, A.C.f_dt);
+  Tally tl;
+  tl.clear();
+  for (int64_t h = blockIdx.x * (int64_t)TILE + threadIdx.x; h < nl;
+       h += (int64_t)gridDim.x * TILE) {
+    const int64_t slot = A.heavy_list[h];
+    const int64_t tile = slot / TILE;
+    const int si = tile < T0 ? 0 : 1;
+    const Sp<Real> &S = A.sp[si];
+    const int64_t i = (tile - (si ? T0 : 0)) * TILE + (slot % TILE);
+    Real x = S.x[i], y = S.y[i], z = S.z[i];
+    Real px = S.px[i], py = S.py[i], pz = S.pz[i];
+    Real E[3], B[3];
+    get_fields<Real, FM>(S, A.f, i, x, y, z, E, B);
+    const uint64_t pid = S.id[i];
+    const Real wt = S.w[i];
+    Real g;
+    if (MODE != MODE_EMIT) {
+      g = boris(px, py, pz, E, B, S.q, dt);
+      Real ig = dt / g;
+      x += px * ig; y += py * ig; z += pz * ig;
+    } else {
+      g = m_sqrt((Real)1 + px * px + py * py + pz * pz);
+    }
+    Real chi = chi_lepton(px, py, pz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
+    RateOut<Real> ro = photon_rate(sR, sF, A.T, A.C, chi, g, tl);
+    U4 r = draw(A.C.seed, pid, A.step, 0, STREAM_EMIT);
+    XiOut<Real> xo = photon_xi(A.T.Y, A.T, ro.l, chi, ro.kmin, unif<Real>(r.y), unif<Real>(~r.y), tl);
+    Real g2 = g * xo.omxi, eph = g * xo.xi;
+    if (g2 < (Real)1) { g2 = (Real)1; eph = g - (Real)1; }
+    Real pm = m_sqrt(px * px + py * py + pz * pz);
+    Real ip = pm > (Real)0 ? (Real)1 / pm : (Real)0;
+    Real nx = px * ip, ny = py * ip, nz = pz * ip;
+    Real pm2 = m_sqrt((g2 - (Real)1) * (g2 + (Real)1));
+    if (MODE != MODE_EMIT) { S.x[i] = x; S.y[i] = y; S.z[i] = z; }
+    S.px[i] = pm2 * nx; S.py[i] = pm2 * ny; S.pz[i] = pm2 * nz;
+    tl.events += 1;
+    tl.substeps += 1;
+    int b = spec_bin(A.C, eph);
+    if (b >= 0) atomicAdd(&bt.hist[b], 1ull);
+    const int64_t out = base + h;
+    if (out < A.ph.cap) {
+      U4 cid = draw(A.C.seed, pid, A.step, 0, STREAM_PHOTON_ID);
+      write_child(A.ph, out, x, y, z, eph * nx, eph * ny, eph * nz, wt,
+                  (uint64_t)cid.x | ((uint64_t)cid.y << 32), E, B);
+    } else {
+      tl.dropped += 1;
+      tl.status |= QED_STATUS_CAPACITY;
+    }
+  }
+  tally_flush(&bt, tl);
+  __syncthreads();
+  block_tally_commit(&bt, A.o.cnt, 0);
+  // the last CTA to finish publishes the photon count (all CTAs have read it)
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned int prev = atomicAdd(&A.o.scan.sync[1], 1u);
+    if (prev == gridDim.x - 1) {
+      int64_t nn = base + nl;
+      *A.ph.d_n = nn < A.ph.cap ? nn : A.ph.cap;
+      A.o.scan.sync[0] = 0u;
+      A.o.scan.sync[1] = 0u;
+      A.o.scan.sync[2] = epoch + 1u;
+      __threadfence();
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -503,9 +710,71 @@ template <class Real> struct PhotonArgs {
   Tables<Real> T;
   Out o;
   int64_t step;
+  uint8_t *flags;       // streaming pass: 1 = redo in the ordered pass
+  const int *list;      // ordered pass: photon indices to process
+  const int64_t *list_n;
 };
 
+// ---------------------------------------------------------------------------
+// Streaming photon pass: ballistic push, chi_ph, pair rate and the first
+// Method I draw, with no block-wide synchronisation.  Photons with one
+// sub-step and no event are finished here; the rest are flagged and redone
+// from their stored state by the ordered pass (k_photon over the list).
+// ---------------------------------------------------------------------------
 template <class Real, int FM>
+__global__ void __launch_bounds__(TILE) k_photon_stream(PhotonArgs<Real> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real *sP = reinterpret_cast<Real *>(smem_raw);
+  __shared__ long long s_meta[2];
+  __shared__ BlockTally bt;
+  load_tables_smem(sP, A.T.P, A.T.glp.n);
+  block_tally_init(&bt);
+  if (threadIdx.x == 0) s_meta[0] = *(volatile const int64_t *)A.n_active;
+  __syncthreads();
+  const int64_t n = s_meta[0];
+  const int64_t nslots = (n + TILE - 1) / TILE * TILE;
+  const Real inv_aS = sel<Real>(A.C.inv_aS, A.C.f_inv_aS);
+  const Real dt = sel<Real>(A.C.dt, A.C.f_dt), wdt_max = sel<Real>(A.C.wdt_max, A.C.f_wdt_max);
+  Tally tl;
+  tl.clear();
+  for (int64_t i = blockIdx.x * (int64_t)TILE + threadIdx.x; i < nslots;
+       i += (int64_t)gridDim.x * TILE) {
+    uint8_t flag = 0;
+    if (i < n && A.ph.alive[i]) {
+      Real x = A.ph.x[i], y = A.ph.y[i], z = A.ph.z[i];
+      Real px = A.ph.px[i], py = A.ph.py[i], pz = A.ph.pz[i];
+      Real E[3], B[3];
+      get_fields<Real, FM>(A.ph, A.f, i, x, y, z, E, B);
+      Real k = m_sqrt(px * px + py * py + pz * pz);
+      Real chi = chi_photon(px, py, pz, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
+      Tally t0;
+      t0.clear();
+      RateOut<Real> ro = pair_rate(sP, A.T, A.C, chi, k, t0);
+      Real wdt = ro.W * dt;
+      if (wdt > wdt_max) {
+        flag = 1;
+      } else if (ro.W > (Real)0) {
+        U4 r = draw(A.C.seed, A.ph.id[i], A.step, 0, STREAM_PAIR);
+        if (wdt > unif<Real>(r.x)) flag = 1;
+      }
+      if (!flag) {
+        tl.substeps += 1;
+        tl.status |= t0.status;
+        tl.domain += t0.domain;
+        if (k > (Real)0) {
+          Real ik = dt / k;
+          A.ph.x[i] = x + px * ik; A.ph.y[i] = y + py * ik; A.ph.z[i] = z + pz * ik;
+        }
+      }
+    }
+    A.flags[i] = flag;
+  }
+  tally_flush(&bt, tl);
+  __syncthreads();
+  block_tally_commit(&bt, A.o.cnt, 1);
+}
+
+template <class Real, int FM, int LIST>
 __global__ void __launch_bounds__(TILE) k_photon(PhotonArgs<Real> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real *sP = reinterpret_cast<Real *>(smem_raw);
@@ -515,7 +784,7 @@ __global__ void __launch_bounds__(TILE) k_photon(PhotonArgs<Real> A) {
   load_tables_smem(sP, A.T.P, A.T.glp.n);
   block_tally_init(&bt);
   if (threadIdx.x == 0) {
-    s_meta[2] = *(volatile const int64_t *)A.n_active;
+    s_meta[2] = LIST ? *(volatile const int64_t *)A.list_n : *(volatile const int64_t *)A.n_active;
     s_meta[3] = *(volatile int64_t *)A.el.d_n;
     s_meta[4] = *(volatile int64_t *)A.po.d_n;
     s_meta[5] = (long long)A.o.scan.sync[2];
@@ -524,8 +793,8 @@ __global__ void __launch_bounds__(TILE) k_photon(PhotonArgs<Real> A) {
   const int64_t n = s_meta[2], ne = s_meta[3], np = s_meta[4];
   const uint32_t epoch = (uint32_t)s_meta[5];
   const int64_t ntiles = (n + TILE - 1) / TILE;
-  const double inv_aS = 1.0 / A.C.a_S;
-  const Real dt = (Real)A.C.dt;
+  const Real inv_aS = sel<Real>(A.C.inv_aS, A.C.f_inv_aS);
+  const Real dt = sel<Real>(A.C.dt, A.C.f_dt);
   Tally tl;
   tl.clear();
   for (;;) {
@@ -534,8 +803,9 @@ __global__ void __launch_bounds__(TILE) k_photon(PhotonArgs<Real> A) {
     const int64_t t = s_meta[0];
     __syncthreads();
     if (t >= ntiles) break;
-    const int64_t i = t * TILE + threadIdx.x;
-    bool active = i < n;
+    const int64_t h = t * TILE + threadIdx.x;
+    bool active = h < n;
+    const int64_t i = LIST ? (active ? (int64_t)A.list[h] : 0) : h;
     if (active && A.ph.alive) active = A.ph.alive[i] != 0;
     Real x = 0, y = 0, z = 0, px = 0, py = 0, pz = 0, wt = 0, k = 0;
     Real E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
@@ -558,9 +828,10 @@ __global__ void __launch_bounds__(TILE) k_photon(PhotonArgs<Real> A) {
       RateOut<Real> ro = pair_rate(sP, A.T, A.C, chi, k, tl);
       int64_t N = 1;
       Real wdt = ro.W * dt;
-      if (wdt > (Real)A.C.wdt_max) {
-        double nn = ceil((double)wdt / A.C.wdt_max);
-        if (nn > (double)A.C.max_substeps) { nn = (double)A.C.max_substeps; tl.status |= QED_STATUS_SUBSTEPS; }
+      const Real wdt_max = sel<Real>(A.C.wdt_max, A.C.f_wdt_max);
+      if (wdt > wdt_max) {
+        Real nn = m_ceil(wdt / wdt_max);
+        if (nn > (Real)A.C.max_substeps) { nn = (Real)A.C.max_substeps; tl.status |= QED_STATUS_SUBSTEPS; }
         N = (int64_t)nn;
       }
       const Real dts = dt / (Real)N;
@@ -772,7 +1043,7 @@ template <class Real> __global__ void k_eval_xi(EvalArgs<Real> A) {
   } else {
     RateOut<Real> ro = pair_rate(A.T.P, A.T, A.C, chi, (Real)1e6, tl);
     Real l = ro.l;
-    if (!(chi >= (Real)A.C.chi_pair_min)) l = A.T.glp.lo;
+    if (!(chi >= sel<Real>(A.C.chi_pair_min, A.C.f_chi_pair_min))) l = A.T.glp.lo;
     XiOut<Real> xo = pair_xi(A.T.Yp, A.T, l, unif<Real>(w), unif<Real>(~w));
     A.out[i] = (double)xo.xi;
   }
@@ -856,6 +1127,16 @@ Consts consts_of(const qed_ctx *c) {
   k.seed = c->cfg.seed;
   k.max_substeps = c->cfg.max_substeps;
   k.pair_sign = c->cfg.pair_sign;
+  k.inv_aS = 1.0 / c->cfg.a_S;
+  k.alpha_aS = c->cfg.alpha * c->cfg.a_S;
+  k.f_dt = (float)k.dt;
+  k.f_wdt_max = (float)k.wdt_max;
+  k.f_xi_min_energy = (float)k.xi_min_energy;
+  k.f_chi_pair_min = (float)k.chi_pair_min;
+  k.f_spec_lo = (float)k.spec_lo;
+  k.f_spec_scale = (float)k.spec_scale;
+  k.f_inv_aS = (float)k.inv_aS;
+  k.f_alpha_aS = (float)k.alpha_aS;
   return k;
 }
 
@@ -865,6 +1146,25 @@ Out out_of(const qed_ctx *c) {
 
 template <class Real> size_t lepton_smem(const qed_ctx *c) {
   return sizeof(Real) * ((size_t)c->gl.n + (size_t)c->gl.n * c->gy.n);
+}
+
+static cudaError_t launch_flag_list(qed_ctx *c, const uint8_t *flags, uint8_t want, const int64_t *n0,
+                                    const int64_t *n1, const Out &o, cudaStream_t st) {
+  HeavyListArgs h{};
+  h.flags = flags;
+  h.want = want;
+  h.list = c->heavy_list;
+  h.count = c->heavy_n;
+  h.n0 = n0;
+  h.n1 = n1;
+  h.o = o;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_heavy_list, TILE, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  k_heavy_list<<<c->num_sms * per_sm, TILE, 0, st>>>(h);
+  c->launches += 1;
+  return cudaGetLastError();
 }
 
 template <class Real, int FM, int MODE, int PASS>
@@ -882,28 +1182,53 @@ static cudaError_t launch_lepton_pass(qed_ctx *c, const LeptonArgs<Real> &a, cud
   return cudaGetLastError();
 }
 
-// Main pass, then (for emission) the ordered list of deferred particles and
-// the heavy pass over it.
 template <class Real, int FM, int MODE>
-static cudaError_t launch_lepton_t(qed_ctx *c, const LeptonArgs<Real> &a, cudaStream_t st) {
-  cudaError_t e = launch_lepton_pass<Real, FM, MODE, PASS_MAIN>(c, a, st);
-  if (e != cudaSuccess || MODE == MODE_PUSH) return e;
-  HeavyListArgs h{};
-  h.flags = a.heavy_flags;
-  h.list = c->heavy_list;
-  h.count = c->heavy_n;
-  h.n0 = a.sp[0].d_n;
-  h.n1 = a.nsp > 1 ? a.sp[1].d_n : nullptr;
-  h.o = a.o;
+static cudaError_t launch_stream(qed_ctx *c, const LeptonArgs<Real> &a, cudaStream_t st) {
+  size_t sm = sizeof(Real) == 8 ? 0 : lepton_smem<Real>(c);
+  auto kern = k_lepton_stream<Real, FM, MODE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_heavy_list, TILE, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE, sm);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
-  k_heavy_list<<<c->num_sms * per_sm, TILE, 0, st>>>(h);
+  kern<<<c->num_sms * per_sm, TILE, sm, st>>>(a);
   c->launches += 1;
-  e = cudaGetLastError();
+  return cudaGetLastError();
+}
+
+template <class Real, int FM, int MODE>
+static cudaError_t launch_emit1(qed_ctx *c, const LeptonArgs<Real> &a, cudaStream_t st) {
+  size_t sm = sizeof(Real) == 8 ? 0 : lepton_smem<Real>(c);
+  auto kern = k_lepton_emit1<Real, FM, MODE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  return launch_lepton_pass<Real, FM, MODE, PASS_HEAVY>(c, a, st);
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE, sm);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  kern<<<c->num_sms * per_sm, TILE, sm, st>>>(a);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+
+// Emission: the streaming pass, then for each deferred class (1: one event,
+// 2: several sub-steps) the ordered list of its particles and the full pass
+// over that list, which appends the photons (class-1 photons first, each class
+// in particle order).
+template <class Real, int FM, int MODE>
+static cudaError_t launch_lepton_t(qed_ctx *c, const LeptonArgs<Real> &a, cudaStream_t st) {
+  if (MODE == MODE_PUSH) return launch_lepton_pass<Real, FM, MODE, PASS_MAIN>(c, a, st);
+  cudaError_t e = launch_stream<Real, FM, MODE>(c, a, st);
+  const int64_t *n1 = a.nsp > 1 ? a.sp[1].d_n : nullptr;
+  if (e == cudaSuccess) e = launch_flag_list(c, a.heavy_flags, 1, a.sp[0].d_n, n1, a.o, st);
+  if (e == cudaSuccess) e = launch_emit1<Real, FM, MODE>(c, a, st);
+  for (uint8_t cls = 2; cls <= 5 && e == cudaSuccess; ++cls) {
+    e = launch_flag_list(c, a.heavy_flags, cls, a.sp[0].d_n, n1, a.o, st);
+    if (e == cudaSuccess) e = launch_lepton_pass<Real, FM, MODE, PASS_HEAVY>(c, a, st);
+  }
+  return e;
 }
 
 template <class Real, int MODE>
@@ -938,9 +1263,18 @@ cudaError_t launch_lepton(qed_ctx *c, const qed_species *s0, const qed_species *
 template <class Real, int FM>
 static cudaError_t launch_photon_t(qed_ctx *c, const PhotonArgs<Real> &a, cudaStream_t st) {
   size_t sm = sizeof(Real) * (size_t)c->glp.n;
-  auto kern = k_photon<Real, FM>;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE, sm);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_photon_stream<Real, FM>,
+                                                                TILE, sm);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  k_photon_stream<Real, FM><<<c->num_sms * per_sm, TILE, sm, st>>>(a);
+  c->launches += 1;
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_flag_list(c, a.flags, 1, a.n_active, nullptr, a.o, st);
+  if (e != cudaSuccess) return e;
+  auto kern = k_photon<Real, FM, 1>;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE, sm);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   kern<<<c->num_sms * per_sm, TILE, sm, st>>>(a);
@@ -962,6 +1296,9 @@ cudaError_t launch_photon(qed_ctx *c, const qed_species *g, const qed_species *e
   a.T = tables_of<Real>(c);
   a.o = out_of(c);
   a.step = step;
+  a.flags = c->heavy_flags;
+  a.list = c->heavy_list;
+  a.list_n = c->heavy_n;
   if (f->mode == QED_FIELDS_UNIFORM) return launch_photon_t<Real, FM_UNIFORM>(c, a, st);
   if (f->mode == QED_FIELDS_PER_PARTICLE) return launch_photon_t<Real, FM_PER_PARTICLE>(c, a, st);
   return launch_photon_t<Real, FM_GRID>(c, a, st);
