@@ -218,6 +218,25 @@ int qed_reset_counters(qed_ctx *ctx, qed_stream_t stream);
 int qed_profile_begin(qed_ctx *ctx, int max_steps);
 int qed_profile_end(qed_ctx *ctx, double *lepton_ms, double *photon_ms, int64_t *steps);
 
+/* Allocation-free stable compaction (no counterpart in the paper; it is a
+ * service for callers that cannot allocate device memory -- an application
+ * that owns every allocation through its own pool, a sandbox that forbids
+ * cudaMalloc, or code where an allocation would synchronise the device).
+ * Same result as qed_compact, but needs no qed_ctx: its only scratch (the
+ * scan's look-back state and two counters) lives in a file-scope static
+ * device array of 512 KiB per device, held until the process exits.
+ *   s         species to compact in place (alive required; element type given
+ *             by precision, QED_FP32 -> float, QED_FP64 -> double; the six
+ *             field arrays are moved when all six are non-NULL)
+ *   d_status  optional caller-owned device uint32 OR-ed with QED_STATUS_* bits
+ * Returns QED_ERR_CAPACITY if s->capacity exceeds 16,777,216 particles.  Calls
+ * no allocating routine.  Every call shares the static array: calls that
+ * overlap on the GPU race, so issue them to one stream or order them.  The
+ * first call on a device performs a one-time set-up (cudaGetSymbolAddress of
+ * the array with that device current); make it before any stream capture. */
+int qed_compact_noalloc(const qed_species *s, int precision, uint32_t *d_status,
+                        qed_stream_t stream);
+
 /* Number of kernel launches this context has issued (for accounting). */
 int64_t qed_launch_count(const qed_ctx *ctx);
 

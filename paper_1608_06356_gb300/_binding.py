@@ -90,6 +90,7 @@ SIGNATURES = {
     "qed_reset_counters": (C.c_int, [_P, _P]),
     "qed_launch_count": (C.c_int64, [_P]),
     "qed_profile_begin": (C.c_int, [_P, C.c_int]),
+    "qed_compact_noalloc": (C.c_int, [C.POINTER(qed_species), C.c_int, _P, _P]),
     "qed_profile_end": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                   C.POINTER(C.c_int64)]),
 }
