@@ -124,6 +124,58 @@ def host_workload(n, seed, chunk=1 << 22):
     return out
 
 
+def sampler_comparison(api, torch, n, args, reps=5):
+    """Isolated inverse-CDF sampler (qed_sample_xi) at n samples, table vs the
+    learned network (trained here on the device), with the spectral error."""
+    rng = np.random.default_rng(123)
+    chi = torch.tensor(np.exp(rng.uniform(np.log(1e-3), np.log(1e2), n)).astype(np.float32), device="cuda")
+    gam = torch.tensor(np.exp(rng.uniform(np.log(1e2), np.log(1e4), n)).astype(np.float32), device="cuda")
+    out = torch.empty(n, device="cuda")
+    res = {}
+    ctx_t = api.qed_init_tables(api.config(dt=DT, seed=5))
+    ctx_m = api.qed_init_tables(api.config(dt=DT, seed=5, sampler=1))
+    api.qed_mlp_load(ctx_m, api.mlp_init_params(0))
+    t0 = time.perf_counter()
+    loss = api.qed_mlp_train(ctx_m, int(args.mlp_train_samples), lr=6e-3, seed=7)
+    train_s = time.perf_counter() - t0
+    peak, kind = peaks()
+    for name, ctx in (("table", ctx_t), ("mlp", ctx_m)):
+        for s in range(3):
+            api.qed_sample_xi(ctx, chi, gam, out, s)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for s in range(reps):
+            api.qed_sample_xi(ctx, chi, gam, out, 10 + s)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / reps
+        res[name] = {"samples_per_s": n / (ms * 1e-3), "ms_per_launch": ms,
+                     "achieved_gbs": 12 * n / (ms * 1e-3) / 1e9,
+                     "frac_hbm": 12 * n / (ms * 1e-3) / 1e9 / peak}
+    # tensor work of the network: layers 2 and 3, 64x64 MACs, three split-BF16 products each
+    res["mlp"]["tensor_tflops"] = 2 * 3 * 2 * 64 * 64 * res["mlp"]["samples_per_s"] / 1e12
+    # spectral error: 64 log bins of xi at five chi values, 2^16 paired draws each
+    errs = []
+    nu = 1 << 16
+    for c in (3e-3, 0.03, 0.3, 3.0, 30.0):
+        cc = torch.full((nu,), c, device="cuda")
+        gg = torch.full((nu,), 1000.0, device="cuda")
+        xm, xt = torch.empty(nu, device="cuda"), torch.empty(nu, device="cuda")
+        api.qed_sample_xi(ctx_m, cc, gg, xm, 5)
+        api.qed_sample_xi(ctx_t, cc, gg, xt, 5)
+        edges = np.exp(np.linspace(np.log(2e-3), 0.0, 65))
+        pm = np.histogram(xm.cpu().numpy(), edges)[0] / nu
+        pt = np.histogram(xt.cpu().numpy(), edges)[0] / nu
+        big = pt >= 1e-3
+        errs.append(float(np.max(np.abs(pm[big] - pt[big]) / pt[big])))
+    res["mlp"].update({"train_samples": int(args.mlp_train_samples), "train_s": train_s,
+                       "train_loss_mse_lndelta": loss, "spectral_error_max_rel": max(errs)})
+    res["mlp_over_table_speed"] = res["mlp"]["samples_per_s"] / res["table"]["samples_per_s"]
+    res["n"] = n
+    return res
+
+
 def cpu_baseline(sample_n=12288, steps=2, seed=0):
     """The FP64 oracle as it stands on a bounded sample of the same workload."""
     import oracle as O
@@ -193,6 +245,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--ref-particles", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sampler-bench", type=int, default=1)
+    ap.add_argument("--mlp-train-samples", type=float, default=4e9)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -345,12 +399,13 @@ def main():
                "note": "state on pinned host memory; every step copies all species in, runs "
                        "qed_step_fused, reads the counts and copies all species back"}
 
+    sampler = sampler_comparison(api, torch, n, args) if args.sampler_bench else None
     status = c_after["status"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_desc(n), "roofline": roofline, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clocks,
+            "gpu_launches": launches, "clocks": clocks, "sampler_table_vs_mlp": sampler,
             "counters": {"emit_events": emitted,
                          "pair_events": c_after["pair_events"] - c_before["pair_events"],
                          "substeps": c_after["substeps"] - c_before["substeps"],

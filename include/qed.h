@@ -68,6 +68,7 @@ enum {
 };
 
 enum { QED_FP32 = 0, QED_FP64 = 1 };
+enum { QED_SAMPLER_TABLE = 0, QED_SAMPLER_MLP = 1 };
 enum { QED_FIELDS_UNIFORM = 0, QED_FIELDS_PER_PARTICLE = 1, QED_FIELDS_GRID = 2 };
 
 /* ---- configuration ---------------------------------------------------- */
@@ -87,6 +88,8 @@ typedef struct {
   double spec_lo, spec_hi; /* photon-energy histogram: 64 log bins over [spec_lo, spec_hi) m c^2 */
   int64_t max_particles;   /* largest per-species capacity any call will use (sizes scan state) */
   int64_t max_substeps;    /* cap on N per particle per step (status bit when hit) */
+  int sampler;             /* QED_SAMPLER_TABLE (default) or QED_SAMPLER_MLP (FP32 contexts) */
+  int pad2_;
 } qed_config;
 
 /* Fill *cfg with the paper-derived defaults (FP32, dt = 0.01, seed 0). */
@@ -208,6 +211,31 @@ int qed_table_get(qed_ctx *ctx, int which, double *host_out, size_t n, double *d
 /* Counters: copy to host (synchronises `stream`) / zero them (async). */
 int qed_read_counters(qed_ctx *ctx, qed_counters *out, qed_stream_t stream);
 int qed_reset_counters(qed_ctx *ctx, qed_stream_t stream);
+
+/* ---- learned inverse CDF (surrogate for the tabulated inverse of Eq. 7) --
+ * A 2 -> 64 -> 64 -> 64 -> 1 SiLU network maps x0 = (ln chi + 1.1512925)/5.7564627,
+ * x1 = (kappa + 3.25)/6.75 to z; ln delta = z + 3 kappa - 2 ln(1 + e^kappa), where
+ * kappa = ln(-ln(1 - u)) and delta = 2 xi/(3 chi (1 - xi)).  Domain chi in
+ * [1e-3, 1e2], kappa in [-10, 3.5]; outside it the table is used.  Inference
+ * runs in BF16 on the tensor cores with FP32 accumulation; training in FP32.
+ * Parameters: 8577 floats, W1[2][64], b1[64], W2[64][64], b2[64], W3[64][64],
+ * b3[64], W4[64], b4 (row index = input unit).  With sampler = QED_SAMPLER_MLP
+ * the single-event emission pass and qed_sample_xi draw xi with the network.
+ *
+ * qed_mlp_load: copy host weights in (resets the optimiser state).
+ * qed_mlp_get:  copy the FP32 weights out.
+ * qed_mlp_train: n_samples samples drawn on the device over the domain, targets
+ *   from the FP64 inverse table; Adam (beta 0.9/0.999) with cosine decay from
+ *   lr to lr/100; mini-batch 128 x 2 per CTA, one CTA per SM.  *final_loss gets
+ *   the mean squared error of z over the last 8 steps.  Synchronous.
+ * qed_mlp_grad: gradient of mean((z - t)^2) at the current weights for a given
+ *   batch (device x[n][2], t[n]) into device grad[8577]; *loss (host) optional. */
+int qed_mlp_load(qed_ctx *ctx, const float *host_w, size_t n);
+int qed_mlp_get(qed_ctx *ctx, float *host_w, size_t n);
+int qed_mlp_train(qed_ctx *ctx, int64_t n_samples, float lr, uint64_t seed, double *final_loss,
+                  qed_stream_t stream);
+int qed_mlp_grad(qed_ctx *ctx, const float *x, const float *t, int64_t n, float *grad,
+                 double *loss, qed_stream_t stream);
 
 /* Measurement hooks.  qed_profile_begin creates CUDA events (call it outside
  * any timed or captured region) so that each of the next max_steps calls of

@@ -15,6 +15,8 @@ LIB_PATH = os.path.join(HERE, "libqed.so")
 
 QED_OK = 0
 QED_FP32, QED_FP64 = 0, 1
+QED_SAMPLER_TABLE, QED_SAMPLER_MLP = 0, 1
+MLP_NP = 8577
 QED_FIELDS_UNIFORM, QED_FIELDS_PER_PARTICLE, QED_FIELDS_GRID = 0, 1, 2
 QED_STATUS_CAPACITY, QED_STATUS_DOMAIN, QED_STATUS_NONFINITE = 1, 2, 4
 QED_STATUS_TIMEOUT, QED_STATUS_SUBSTEPS = 8, 16
@@ -37,7 +39,8 @@ class qed_config(C.Structure):
                 ("chi_pair_min", C.c_double), ("chi_pair_max", C.c_double),
                 ("fwd_per_unit", C.c_double), ("inv_per_unit", C.c_double),
                 ("seed", C.c_uint64), ("spec_lo", C.c_double), ("spec_hi", C.c_double),
-                ("max_particles", C.c_int64), ("max_substeps", C.c_int64)]
+                ("max_particles", C.c_int64), ("max_substeps", C.c_int64),
+                ("sampler", C.c_int), ("pad2_", C.c_int)]
 
 
 class qed_species(C.Structure):
@@ -91,6 +94,10 @@ SIGNATURES = {
     "qed_launch_count": (C.c_int64, [_P]),
     "qed_profile_begin": (C.c_int, [_P, C.c_int]),
     "qed_compact_noalloc": (C.c_int, [C.POINTER(qed_species), C.c_int, _P, _P]),
+    "qed_mlp_load": (C.c_int, [_P, _P, C.c_size_t]),
+    "qed_mlp_get": (C.c_int, [_P, _P, C.c_size_t]),
+    "qed_mlp_train": (C.c_int, [_P, C.c_int64, C.c_float, C.c_uint64, C.POINTER(C.c_double), _P]),
+    "qed_mlp_grad": (C.c_int, [_P, _P, _P, C.c_int64, _P, C.POINTER(C.c_double), _P]),
     "qed_profile_end": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                   C.POINTER(C.c_int64)]),
 }

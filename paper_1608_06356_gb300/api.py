@@ -293,3 +293,48 @@ def qed_profile_end(ctx: Context) -> tuple[float, float, int]:
     a, b, n = C.c_double(), C.c_double(), C.c_int64()
     B.check(B.lib().qed_profile_end(ctx.handle, C.byref(a), C.byref(b), C.byref(n)), "qed_profile_end")
     return a.value, b.value, n.value
+
+
+def qed_mlp_load(ctx: Context, weights) -> None:
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32))
+    B.check(B.lib().qed_mlp_load(ctx.handle, w.ctypes.data, w.size), "qed_mlp_load")
+
+
+def qed_mlp_get(ctx: Context) -> np.ndarray:
+    w = np.zeros(B.MLP_NP, dtype=np.float32)
+    B.check(B.lib().qed_mlp_get(ctx.handle, w.ctypes.data, w.size), "qed_mlp_get")
+    return w
+
+
+def qed_mlp_train(ctx: Context, n_samples: int, lr: float = 3e-3, seed: int = 1, stream=None) -> float:
+    loss = C.c_double()
+    B.check(B.lib().qed_mlp_train(ctx.handle, int(n_samples), float(lr), int(seed), C.byref(loss),
+                                  _stream(stream)), "qed_mlp_train")
+    return loss.value
+
+
+def qed_mlp_grad(ctx: Context, x: torch.Tensor, t: torch.Tensor, stream=None):
+    x = x.to(torch.float32).contiguous()
+    t = t.to(torch.float32).contiguous()
+    g = torch.zeros(B.MLP_NP, dtype=torch.float32, device=x.device)
+    loss = C.c_double()
+    B.check(B.lib().qed_mlp_grad(ctx.handle, x.data_ptr(), t.data_ptr(), t.numel(), g.data_ptr(),
+                                 C.byref(loss), _stream(stream)), "qed_mlp_grad")
+    return g, loss.value
+
+
+def mlp_init_params(seed: int = 0) -> np.ndarray:
+    """Initial weights of the learned inverse CDF: uniform(+-sqrt(6/(fan_in +
+    fan_out))) weights, zero biases, in the C ABI's parameter order."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_in, fan_out, is_w in ((2, 64, 1), (0, 64, 0), (64, 64, 1), (0, 64, 0), (64, 64, 1),
+                                  (0, 64, 0), (64, 1, 1), (0, 1, 0)):
+        if is_w:
+            lim = np.sqrt(6.0 / (fan_in + fan_out))
+            parts.append(rng.uniform(-lim, lim, fan_in * fan_out))
+        else:
+            parts.append(np.zeros(fan_out))
+    w = np.concatenate(parts).astype(np.float32)
+    assert w.size == B.MLP_NP
+    return w

@@ -76,7 +76,7 @@ static void free_ctx(qed_ctx *c) {
   if (!c) return;
   void *ptrs[] = {c->R64, c->F64, c->Y64, c->P64, c->Yp64, c->R32, c->F32, c->Y32,
                   c->P32, c->Yp32, c->tile_state, c->sync, c->snap, c->d_counters,
-                  c->heavy_flags, c->heavy_list, c->heavy_n};
+                  c->heavy_flags, c->heavy_list, c->heavy_n, c->mlp_mem};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   free(c);
@@ -140,7 +140,9 @@ static bool cfg_valid(const qed_config *c) {
          (c->precision == QED_FP32 || c->precision == QED_FP64) && c->chi_min > 0 &&
          c->chi_max > c->chi_min && c->chi_pair_min > 0 && c->chi_pair_max > c->chi_pair_min &&
          c->spec_lo > 0 && c->spec_hi > c->spec_lo && c->max_particles > 0 &&
-         c->max_particles <= ((int64_t)1 << 31) && c->max_substeps >= 1;
+         c->max_particles <= ((int64_t)1 << 31) && c->max_substeps >= 1 &&
+         (c->sampler == QED_SAMPLER_TABLE ||
+          (c->sampler == QED_SAMPLER_MLP && c->precision == QED_FP32));
 }
 
 extern "C" int qed_init_tables(const qed_config *cfg, qed_ctx **out, qed_stream_t stream) {
@@ -208,6 +210,7 @@ extern "C" int qed_init_tables(const qed_config *cfg, qed_ctx **out, qed_stream_
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { free_ctx(c); return cuda_fail(e, "init"); }
   rc = build_tables(c, st);
+  if (rc == QED_OK) rc = mlp_alloc(c);
   if (rc != QED_OK) { free_ctx(c); return rc; }
   *out = c;
   return QED_OK;

@@ -298,31 +298,43 @@ __device__ __forceinline__ RateOut<Real> photon_rate(const Real *R, const Real *
   return o;
 }
 
-// xi from the inverse table.  wmin = -ln(1 - u_min); r2, c2 = 1 - r2.
-// Returns xi and 1 - xi (accurate when xi -> 1).
-template <class Real> struct XiOut { Real xi, omxi; };
+// kappa = ln(-ln(1 - u)) of u = u_min + r2 (1 - u_min), where
+// -ln(1 - u) = -ln(1 - r2) - ln(1 - u_min) and wmin = e^kmin = -ln(1 - u_min).
+template <class Real>
+__device__ __forceinline__ Real photon_kappa(Real kmin, Real r2, Real c2) {
+  Real wc = r2 < (Real)0.5 ? -m_log1p(-r2) : -m_log(c2);
+  return m_log(wc + m_exp(kmin));
+}
 
+// ln delta from the inverse table at (l, kappa) (linear asymptotes outside).
+template <class Real>
+__device__ __forceinline__ Real photon_lndelta_table(const Real *Yt, const Tables<Real> &T,
+                                                     Real l_clamped, Real k, Tally &tl) {
+  if (k > T.gk.hi) {
+    tl.status |= QED_STATUS_DOMAIN;
+    tl.domain += 1;
+    return interp2(Yt, T.gl, l_clamped, T.gk, T.gk.hi) + (k - T.gk.hi);
+  }
+  if (k < T.gk.lo) return interp2(Yt, T.gl, l_clamped, T.gk, T.gk.lo) + (Real)3 * (k - T.gk.lo);
+  return interp2(Yt, T.gl, l_clamped, T.gk, k);
+}
+
+// xi and 1 - xi from ln delta: xi = a/(1+a), a = 1.5 chi delta.
+template <class Real> struct XiOut { Real xi, omxi; };
+template <class Real>
+__device__ __forceinline__ XiOut<Real> xi_from_lndelta(Real chi, Real Y) {
+  Real a = (Real)1.5 * chi * m_exp(Y);
+  Real inv = (Real)1 / ((Real)1 + a);
+  return XiOut<Real>{a * inv, inv};
+}
+
+// xi from the inverse table.  kmin = ln(-ln(1 - u_min)); r2, c2 = 1 - r2.
 template <class Real>
 __device__ __forceinline__ XiOut<Real> photon_xi(const Real *Yt, const Tables<Real> &T,
                                                  Real l_clamped, Real chi, Real kmin, Real r2,
                                                  Real c2, Tally &tl) {
-  // -ln(1 - u) for u = u_min + r2 (1 - u_min): -ln(1 - r2) - ln(1 - u_min)
-  Real wc = r2 < (Real)0.5 ? -m_log1p(-r2) : -m_log(c2);
-  Real wt = wc + m_exp(kmin);
-  Real k = m_log(wt);
-  Real Y;
-  if (k > T.gk.hi) {
-    Y = interp2(Yt, T.gl, l_clamped, T.gk, T.gk.hi) + (k - T.gk.hi);
-    tl.status |= QED_STATUS_DOMAIN;
-    tl.domain += 1;
-  } else if (k < T.gk.lo) {
-    Y = interp2(Yt, T.gl, l_clamped, T.gk, T.gk.lo) + (Real)3 * (k - T.gk.lo);
-  } else {
-    Y = interp2(Yt, T.gl, l_clamped, T.gk, k);
-  }
-  Real a = (Real)1.5 * chi * m_exp(Y);
-  Real inv = (Real)1 / ((Real)1 + a);
-  return XiOut<Real>{a * inv, inv};
+  Real k = photon_kappa(kmin, r2, c2);
+  return xi_from_lndelta(chi, photon_lndelta_table(Yt, T, l_clamped, k, tl));
 }
 
 // Pair rate (Eq. 6 integrated over 0 < xi < 1).

@@ -29,6 +29,14 @@ struct qed_ctx {
   // persistent-grid sizes per kernel
   int grid_lepton, grid_photon, grid_compact;
   int64_t launches;
+  // learned inverse CDF: FP32 weights, Adam moments, gradient, BF16 fragments,
+  // per-CTA partial gradients and losses (one allocation)
+  void *mlp_mem;
+  float *mlp_w, *mlp_m, *mlp_v, *mlp_g, *mlp_partial;
+  uint32_t *mlp_frag;
+  double *mlp_loss;
+  int mlp_parts, mlp_ready;
+  int64_t mlp_step;
   // measurement hooks (qed_profile_begin/end): 3 events per profiled step
   cudaEvent_t *prof_ev;
   int prof_max, prof_n;
@@ -36,5 +44,6 @@ struct qed_ctx {
 
 namespace qed {
 int build_tables(qed_ctx *c, cudaStream_t st);
+int mlp_alloc(qed_ctx *c);
 constexpr int TILE = 256;  // particles per tile = threads per block in the step kernels
 }  // namespace qed

@@ -17,6 +17,7 @@
 #include <cstdio>
 
 #include "qed_internal.h"
+#include "qed_mlp.cuh"
 
 namespace qed {
 
@@ -186,6 +187,9 @@ template <class Real> struct LeptonArgs {
   uint8_t *heavy_flags;     // [main-pass slots] 1 = deferred to the heavy pass
   const int *heavy_list;    // ordered main-pass slots of the deferred particles
   const int64_t *heavy_n;   // length of heavy_list
+  const uint32_t *mlp_frag; // learned inverse CDF (used when use_mlp)
+  const float *mlp_w;
+  int use_mlp;
 };
 
 template <class Real, int FM>
@@ -613,6 +617,12 @@ __global__ void __launch_bounds__(TILE) k_lepton_emit1(LeptonArgs<Real> A) {
   constexpr bool kSmem = sizeof(Real) == 4;
   Real *sR = kSmem ? reinterpret_cast<Real *>(smem_raw) : const_cast<Real *>(A.T.R);
   Real *sF = kSmem ? sR + A.T.gl.n : const_cast<Real *>(A.T.F);
+  // learned sampler image after the tables (FP32 contexts only)
+  uint32_t *s_frag = reinterpret_cast<uint32_t *>(
+      smem_raw + (kSmem ? (((size_t)A.T.gl.n * (1 + A.T.gy.n) * sizeof(Real) + 15) & ~(size_t)15) : 0));
+  float *s_fw = reinterpret_cast<float *>(s_frag + MLP_FRAG_WORDS);
+  const bool use_mlp = kSmem && A.use_mlp;
+  if (use_mlp) mlp_stage(s_frag, s_fw, A.mlp_frag, A.mlp_w);
   __shared__ long long s_meta[8];
   __shared__ BlockTally bt;
   if (kSmem) {
@@ -634,19 +644,26 @@ __global__ void __launch_bounds__(TILE) k_lepton_emit1(LeptonArgs<Real> A) {
   const Real dt = sel<Real>(A.C.dt, A.C.f_dt);
   Tally tl;
   tl.clear();
-  for (int64_t h = blockIdx.x * (int64_t)TILE + threadIdx.x; h < nl;
-       h += (int64_t)gridDim.x * TILE) {
-    const int64_t slot = A.heavy_list[h];
+  // warp-uniform loop (the learned sampler is a warp-collective call)
+  for (int64_t hb = blockIdx.x * (int64_t)TILE + (threadIdx.x & ~31); hb < nl;
+       hb += (int64_t)gridDim.x * TILE) {
+    const int64_t h = hb + (threadIdx.x & 31);
+    const bool active = h < nl;
+    const int64_t slot = active ? A.heavy_list[h] : 0;
     const int64_t tile = slot / TILE;
     const int si = tile < T0 ? 0 : 1;
     const Sp<Real> &S = A.sp[si];
     const int64_t i = (tile - (si ? T0 : 0)) * TILE + (slot % TILE);
-    Real x = S.x[i], y = S.y[i], z = S.z[i];
-    Real px = S.px[i], py = S.py[i], pz = S.pz[i];
-    Real E[3], B[3];
-    get_fields<Real, FM>(S, A.f, i, x, y, z, E, B);
-    const uint64_t pid = S.id[i];
-    const Real wt = S.w[i];
+    Real x = 0, y = 0, z = 0, px = 0, py = 0, pz = 1, wt = 0;
+    Real E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
+    uint64_t pid = 0;
+    if (active) {
+      x = S.x[i]; y = S.y[i]; z = S.z[i];
+      px = S.px[i]; py = S.py[i]; pz = S.pz[i];
+      get_fields<Real, FM>(S, A.f, i, x, y, z, E, B);
+      pid = S.id[i];
+      wt = S.w[i];
+    }
     Real g;
     if (MODE != MODE_EMIT) {
       g = boris(px, py, pz, E, B, S.q, dt);
@@ -658,7 +675,20 @@ __global__ void __launch_bounds__(TILE) k_lepton_emit1(LeptonArgs<Real> A) {
     Real chi = chi_lepton(px, py, pz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
     RateOut<Real> ro = photon_rate(sR, sF, A.T, A.C, chi, g, tl);
     U4 r = draw(A.C.seed, pid, A.step, 0, STREAM_EMIT);
-    XiOut<Real> xo = photon_xi(A.T.Y, A.T, ro.l, chi, ro.kmin, unif<Real>(r.y), unif<Real>(~r.y), tl);
+    const Real kap = photon_kappa(ro.kmin, unif<Real>(r.y), unif<Real>(~r.y));
+    Real Y = 0;
+    bool in_mlp = false;
+    if (use_mlp) {
+      const float lchi = (float)m_log(chi);
+      in_mlp = active && lchi >= MLP_L_LO && lchi <= MLP_L_HI && (float)kap >= MLP_K_LO &&
+               (float)kap <= MLP_K_HI;
+      const float zz = mlp_infer_warp(s_frag, s_fw, (lchi - MLP_LC) / MLP_LS,
+                                      ((float)kap - MLP_KC) / MLP_KS);
+      Y = (Real)(zz + mlp_baseline((float)kap));
+    }
+    if (!active) continue;
+    if (!in_mlp) Y = photon_lndelta_table(A.T.Y, A.T, ro.l, kap, tl);
+    XiOut<Real> xo = xi_from_lndelta(chi, Y);
     Real g2 = g * xo.omxi, eph = g * xo.xi;
     if (g2 < (Real)1) { g2 = (Real)1; eph = g - (Real)1; }
     Real pm = m_sqrt(px * px + py * py + pz * pz);
@@ -976,27 +1006,46 @@ struct SampleArgs {
   Consts C;
   Tables<float> T;
   Out o;
+  const uint32_t *mlp_frag;
+  const float *mlp_w;
+  int use_mlp;
 };
 
 __global__ void __launch_bounds__(TILE) k_sample_xi(SampleArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float *sR = reinterpret_cast<float *>(smem_raw);
   float *sF = sR + A.T.gl.n;
+  uint32_t *s_frag = reinterpret_cast<uint32_t *>(
+      smem_raw + (((size_t)A.T.gl.n * (1 + A.T.gy.n) * sizeof(float) + 15) & ~(size_t)15));
+  float *s_fw = reinterpret_cast<float *>(s_frag + MLP_FRAG_WORDS);
   load_tables_smem(sR, A.T.R, A.T.gl.n);
   load_tables_smem(sF, A.T.F, A.T.gl.n * A.T.gy.n);
+  if (A.use_mlp) mlp_stage(s_frag, s_fw, A.mlp_frag, A.mlp_w);
   __syncthreads();
   Tally tl;
   tl.clear();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A.n; i += stride) {
-    float chi = __ldcs(A.chi + i), g = __ldcs(A.gamma + i);
+  // warp-uniform loop (the learned sampler is a warp-collective call)
+  for (int64_t ib = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); ib < A.n; ib += stride) {
+    const int64_t i = ib + (threadIdx.x & 31);
+    const bool active = i < A.n;
+    float chi = active ? __ldcs(A.chi + i) : 1.f, g = active ? __ldcs(A.gamma + i) : 1e3f;
     RateOut<float> ro = photon_rate(sR, sF, A.T, A.C, chi, g, tl);
     U4 r = draw(A.C.seed, (uint64_t)i, A.step, 0, STREAM_EMIT);
+    const float kap = photon_kappa(ro.kmin, unif<float>(r.y), unif<float>(~r.y));
+    float Y = 0.f;
+    bool in_mlp = false;
+    if (A.use_mlp) {
+      const float lchi = logf(chi);
+      in_mlp = lchi >= MLP_L_LO && lchi <= MLP_L_HI && kap >= MLP_K_LO && kap <= MLP_K_HI;
+      Y = mlp_infer_warp(s_frag, s_fw, (lchi - MLP_LC) / MLP_LS, (kap - MLP_KC) / MLP_KS) +
+          mlp_baseline(kap);
+    }
+    if (!active) continue;
     float xi = 0.f;
     if (ro.W > 0.f) {
-      XiOut<float> xo = photon_xi(A.T.Y, A.T, ro.l, chi, ro.kmin, unif<float>(r.y),
-                                  unif<float>(~r.y), tl);
-      xi = xo.xi;
+      if (!in_mlp) Y = photon_lndelta_table(A.T.Y, A.T, ro.l, kap, tl);
+      xi = xi_from_lndelta(chi, Y).xi;
     }
     __stcs(A.xi + i, xi);
   }
@@ -1200,6 +1249,7 @@ static cudaError_t launch_stream(qed_ctx *c, const LeptonArgs<Real> &a, cudaStre
 template <class Real, int FM, int MODE>
 static cudaError_t launch_emit1(qed_ctx *c, const LeptonArgs<Real> &a, cudaStream_t st) {
   size_t sm = sizeof(Real) == 8 ? 0 : lepton_smem<Real>(c);
+  if (sm && a.use_mlp) sm = ((sm + 15) & ~(size_t)15) + MLP_SMEM_BYTES;
   auto kern = k_lepton_emit1<Real, FM, MODE>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
@@ -1255,6 +1305,9 @@ cudaError_t launch_lepton(qed_ctx *c, const qed_species *s0, const qed_species *
   a.heavy_flags = c->heavy_flags;
   a.heavy_list = c->heavy_list;
   a.heavy_n = c->heavy_n;
+  a.mlp_frag = c->mlp_frag;
+  a.mlp_w = c->mlp_w;
+  a.use_mlp = c->cfg.sampler == QED_SAMPLER_MLP && c->mlp_ready;
   if (mode == MODE_PUSH) return launch_lepton_m<Real, MODE_PUSH>(c, a, f->mode, st);
   if (mode == MODE_EMIT) return launch_lepton_m<Real, MODE_EMIT>(c, a, f->mode, st);
   return launch_lepton_m<Real, MODE_FUSED>(c, a, f->mode, st);
@@ -1331,7 +1384,11 @@ cudaError_t launch_sample_xi(qed_ctx *c, const float *chi, const float *gamma, f
   a.C = consts_of(c);
   a.T = tables_of<float>(c);
   a.o = out_of(c);
+  a.mlp_frag = c->mlp_frag;
+  a.mlp_w = c->mlp_w;
+  a.use_mlp = c->cfg.sampler == QED_SAMPLER_MLP && c->mlp_ready;
   size_t sm = lepton_smem<float>(c);
+  if (a.use_mlp) sm = ((sm + 15) & ~(size_t)15) + MLP_SMEM_BYTES;
   cudaError_t e = cudaFuncSetAttribute(k_sample_xi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
