@@ -173,7 +173,79 @@ def sampler_comparison(api, torch, n, args, reps=5):
                        "train_loss_mse_lndelta": loss, "spectral_error_max_rel": max(errs)})
     res["mlp_over_table_speed"] = res["mlp"]["samples_per_s"] / res["table"]["samples_per_s"]
     res["n"] = n
+    res["_weights"] = api.qed_mlp_get(ctx_m)
     return res
+
+
+def batched_runs_bench(api, torch, mlp_weights, steps=4):
+    """256 independent ensembles of uneven size (log-uniform in [1e3, 1e6]) with
+    per-run chi ranges (two sorted log-uniform draws in [0.01, 10]), advanced
+    together: eager launches vs one captured CUDA graph per `steps` steps,
+    table and learned samplers."""
+    from paper_1608_06356_gb300 import workloads as W
+    sizes, ranges = W.batched_runs(256, seed=0)
+    parts, off = [], 0
+    for r, (n, (lo, hi)) in enumerate(zip(sizes, ranges)):
+        st, _, _ = W.chi_target(int(n), seed=5000 + r, chi_lo=lo, chi_hi=hi, id0=off)
+        st = {k: (v.astype(np.float32) if v.dtype.kind == "f" else v) for k, v in st.items()}
+        st["tag"] = np.full(int(n), r, dtype=np.uint32)
+        parts.append(st)
+        off += int(n)
+    host = {k: np.concatenate([q[k] for q in parts]) for k in parts[0]}
+    n = off
+    F = api.Fields.per_particle()
+    out = {"runs": 256, "particles": int(n), "steps": steps}
+    for name, sampler in (("table", 0), ("mlp", 1)):
+        res = {}
+        for mode in ("eager", "graph"):
+            ctx = api.qed_init_tables(api.config(dt=DT, seed=11, sampler=sampler,
+                                                 max_particles=int(0.4 * n * (steps + 2)) + n))
+            if sampler:
+                api.qed_mlp_load(ctx, mlp_weights)
+            e = api.Species.empty(2 * n, -1, fields=True, tag=True).load(**host)
+            p = api.Species.empty(n, 1, fields=True, tag=True)
+            g = api.Species.empty(int(0.4 * n * (steps + 2)), 0, fields=True, tag=True)
+            cnt = torch.zeros((steps, 3), dtype=torch.int64, device="cuda")
+            if mode == "graph":  # capture (first call), then time a replay from the same state
+                api.qed_run_batched(ctx, e, p, g, F, 0, steps)
+                torch.cuda.synchronize()
+                e.load(**host)
+                p.n.zero_()
+                g.n.zero_()
+            else:  # load kernels once, then restore the state
+                api.qed_step_fused(ctx, e, p, g, F, 0)
+                api.qed_compact(ctx, g)
+                torch.cuda.synchronize()
+                e.load(**host)
+                p.n.zero_()
+                g.n.zero_()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            l0 = ctx.launches
+            a.record()
+            if mode == "graph":
+                runs_out = api.qed_run_batched(ctx, e, p, g, F, 0, steps, n_runs=256)
+            else:
+                for k in range(steps):
+                    cnt[k, 0].copy_(e.n[0] + p.n[0])
+                    cnt[k, 1].copy_(g.n[0])
+                    api.qed_step_fused(ctx, e, p, g, F, k)
+                    api.qed_compact(ctx, g)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            if mode == "eager":
+                ps = float(cnt.sum().item())
+                res["particle_steps"] = ps
+                res["eager_launches"] = ctx.launches - l0
+            res[mode + "_ms_per_step"] = ms / steps
+            if mode == "graph":
+                res["photons_per_run_min_max"] = [int(runs_out.min()), int(runs_out.max())]
+        ps = res["particle_steps"]
+        res["eager_particle_steps_per_s"] = ps / (res["eager_ms_per_step"] * steps * 1e-3)
+        res["graph_particle_steps_per_s"] = ps / (res["graph_ms_per_step"] * steps * 1e-3)
+        out[name] = res
+    return out
 
 
 def cpu_baseline(sample_n=12288, steps=2, seed=0):
@@ -246,6 +318,7 @@ def main():
     ap.add_argument("--ref-particles", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sampler-bench", type=int, default=1)
+    ap.add_argument("--batched-bench", type=int, default=1)
     ap.add_argument("--mlp-train-samples", type=float, default=4e9)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -400,12 +473,17 @@ def main():
                        "qed_step_fused, reads the counts and copies all species back"}
 
     sampler = sampler_comparison(api, torch, n, args) if args.sampler_bench else None
+    wts = sampler.pop("_weights", None) if sampler else None
+    batched = None
+    if args.batched_bench:
+        batched = batched_runs_bench(api, torch, wts if wts is not None else api.mlp_init_params(0))
     status = c_after["status"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_desc(n), "roofline": roofline, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks, "sampler_table_vs_mlp": sampler,
+            "batched_runs": batched,
             "counters": {"emit_events": emitted,
                          "pair_events": c_after["pair_events"] - c_before["pair_events"],
                          "substeps": c_after["substeps"] - c_before["substeps"],

@@ -102,7 +102,9 @@ void qed_config_default(qed_config *cfg);
  * ex..bz: per-particle fields (QED_FIELDS_PER_PARTICLE); children inherit
  * their parent's fields; NULL otherwise.
  * d_n: device int64 holding the current count; appends beyond `capacity` are
- * dropped and counted.  q: -1 electron, +1 positron, 0 photon.              */
+ * dropped and counted.  q: -1 electron, +1 positron, 0 photon.
+ * tag: optional user tag (e.g. the index of an independent run), copied to the
+ * particles a particle creates and moved by compaction; NULL if unused.      */
 typedef struct {
   void *x, *y, *z, *px, *py, *pz, *w;
   uint64_t *id;
@@ -112,6 +114,7 @@ typedef struct {
   int64_t capacity;
   int q;
   int pad_;
+  uint32_t *tag;
 } qed_species;
 
 /* ---- fields -------------------------------------------------------------
@@ -236,6 +239,31 @@ int qed_mlp_train(qed_ctx *ctx, int64_t n_samples, float lr, uint64_t seed, doub
                   qed_stream_t stream);
 int qed_mlp_grad(qed_ctx *ctx, const float *x, const float *t, int64_t n, float *grad,
                  double *loss, qed_stream_t stream);
+
+/* Batched independent runs (many ensembles of uneven size advanced together).
+ * The runs are concatenated in e, p, g (per-particle fields carry each run's
+ * fields; tag holds the run index, 0 .. n_runs-1).  Advances `steps` fused
+ * steps (qed_step_fused, then stable compaction of dead photons) starting at
+ * step index step0, as one CUDA graph: captured on the first call for a given
+ * combination of species, fields and steps, cached in the context and
+ * replayed by later calls.  The step index is read by the kernels from a
+ * device counter the graph advances, so every replay draws fresh numbers.
+ * d_run_photons (device int64[n_runs], optional) receives the number of alive
+ * photons per run after the last step.  The first call for a combination
+ * captures the graph on `stream` (so it must not itself be capturing). */
+int qed_run_batched(qed_ctx *ctx, const qed_species *e, const qed_species *p,
+                    const qed_species *g, const qed_fields *f, int64_t step0, int steps,
+                    int n_runs, int64_t *d_run_photons, qed_stream_t stream);
+
+/* Autotuner of the persistent launches: times `reps` fused steps (plus photon
+ * compaction) for each persistent-grid occupancy factor 1..max on the given
+ * species -- which it advances, so pass a disposable copy -- keeps the
+ * fastest factor in the context for all later launches and returns it in
+ * *best_factor; per-candidate milliseconds go to ms_out[0..max-1] if non-NULL
+ * (host, max 8 entries).  factor 0 = as many CTAs per SM as fit. */
+int qed_autotune(qed_ctx *ctx, const qed_species *e, const qed_species *p, const qed_species *g,
+                 const qed_fields *f, int reps, int *best_factor, double *ms_out,
+                 qed_stream_t stream);
 
 /* Measurement hooks.  qed_profile_begin creates CUDA events (call it outside
  * any timed or captured region) so that each of the next max_steps calls of

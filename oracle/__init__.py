@@ -71,7 +71,8 @@ class _Species(C.Structure):
     _fields_ = [("x", _PD), ("y", _PD), ("z", _PD), ("px", _PD), ("py", _PD), ("pz", _PD),
                 ("w", _PD), ("id", C.POINTER(C.c_uint64)), ("alive", C.POINTER(C.c_uint8)),
                 ("ex", _PD), ("ey", _PD), ("ez", _PD), ("bx", _PD), ("by", _PD), ("bz", _PD),
-                ("n", C.c_int64), ("capacity", C.c_int64), ("q", C.c_double)]
+                ("n", C.c_int64), ("capacity", C.c_int64), ("q", C.c_double),
+                ("tag", C.POINTER(C.c_uint32))]
 
 
 class Counters(C.Structure):
@@ -314,7 +315,7 @@ class Species:
     """FP64 SoA particle buffers owned by numpy, with capacity for appends."""
 
     def __init__(self, capacity: int, q: float, per_particle_fields: bool = False,
-                 with_alive: bool = False):
+                 with_alive: bool = False, with_tag: bool = False):
         self.capacity = int(capacity)
         self.q = float(q)
         cap = max(self.capacity, 1)
@@ -325,6 +326,7 @@ class Species:
         self.has_fields = per_particle_fields
         for nm in _FIELD_NAMES:
             setattr(self, nm, np.zeros(cap) if per_particle_fields else None)
+        self.tag = np.zeros(cap, dtype=np.uint32) if with_tag else None
         self.n = 0
 
     def load(self, **arrays):
@@ -354,6 +356,8 @@ class Species:
             a = getattr(self, nm)
             setattr(s, nm, _dp(a) if a is not None else _PD())
         s.n, s.capacity, s.q = self.n, self.capacity, self.q
+        s.tag = (self.tag.ctypes.data_as(C.POINTER(C.c_uint32)) if self.tag is not None
+                 else C.POINTER(C.c_uint32)())
         return s
 
 

@@ -550,6 +550,7 @@ typedef struct {
   double *ex, *ey, *ez, *bx, *by, *bz; /* per-particle fields or NULL */
   int64_t n, capacity;
   double q; /* -1 electron, +1 positron, 0 photon */
+  uint32_t *tag; /* optional user tag, inherited by children (NULL = none) */
 } orc_species;
 
 typedef struct {
@@ -563,6 +564,7 @@ typedef struct {
   double x, y, z, px, py, pz, w;
   uint64_t id;
   double f[6];
+  uint32_t tag;
 } orc_child;
 
 typedef struct {
@@ -622,6 +624,7 @@ static void lepton_one(const orc_config *cfg, const orc_fields *f, orc_species *
     c.x = s->x[i]; c.y = s->y[i]; c.z = s->z[i];
     c.px = eph * n[0]; c.py = eph * n[1]; c.pz = eph * n[2];
     c.w = s->w[i];
+    c.tag = s->tag ? s->tag[i] : 0u;
     uint32_t cid[4];
     orc_draw(cfg->seed, s->id[i], step, k, ORC_STREAM_PHOTON_ID, cid);
     c.id = (uint64_t)cid[0] | ((uint64_t)cid[1] << 32);
@@ -671,6 +674,7 @@ static void photon_one(const orc_config *cfg, const orc_fields *f, orc_species *
     orc_child c;
     c.x = s->x[i]; c.y = s->y[i]; c.z = s->z[i];
     c.w = s->w[i];
+    c.tag = s->tag ? s->tag[i] : 0u;
     for (int q = 0; q < 3; ++q) { c.f[q] = E[q]; c.f[3 + q] = B[q]; }
     c.px = pe * n[0]; c.py = pe * n[1]; c.pz = pe * n[2];
     c.id = (uint64_t)cid[0] | ((uint64_t)cid[1] << 32);
@@ -700,6 +704,7 @@ static void append_children(orc_species *s, const orc_childlist *l, int64_t *dro
     s->x[k] = c->x; s->y[k] = c->y; s->z[k] = c->z;
     s->px[k] = c->px; s->py[k] = c->py; s->pz[k] = c->pz;
     s->w[k] = c->w; s->id[k] = c->id;
+    if (s->tag) s->tag[k] = c->tag;
     if (s->alive) s->alive[k] = 1;
     if (s->ex) {
       s->ex[k] = c->f[0]; s->ey[k] = c->f[1]; s->ez[k] = c->f[2];
@@ -777,6 +782,7 @@ int64_t orc_compact(orc_species *s) {
     s->x[k] = s->x[i]; s->y[k] = s->y[i]; s->z[k] = s->z[i];
     s->px[k] = s->px[i]; s->py[k] = s->py[i]; s->pz[k] = s->pz[i];
     s->w[k] = s->w[i]; s->id[k] = s->id[i]; s->alive[k] = 1;
+    if (s->tag) s->tag[k] = s->tag[i];
     if (s->ex) {
       s->ex[k] = s->ex[i]; s->ey[k] = s->ey[i]; s->ez[k] = s->ez[i];
       s->bx[k] = s->bx[i]; s->by[k] = s->by[i]; s->bz[k] = s->bz[i];

@@ -47,7 +47,8 @@ class qed_species(C.Structure):
     _fields_ = [(n, C.c_void_p) for n in ("x", "y", "z", "px", "py", "pz", "w")] + \
                [("id", C.c_void_p), ("alive", C.c_void_p)] + \
                [(n, C.c_void_p) for n in ("ex", "ey", "ez", "bx", "by", "bz")] + \
-               [("d_n", C.c_void_p), ("capacity", C.c_int64), ("q", C.c_int), ("pad_", C.c_int)]
+               [("d_n", C.c_void_p), ("capacity", C.c_int64), ("q", C.c_int), ("pad_", C.c_int),
+                ("tag", C.c_void_p)]
 
 
 class qed_fields(C.Structure):
@@ -94,6 +95,12 @@ SIGNATURES = {
     "qed_launch_count": (C.c_int64, [_P]),
     "qed_profile_begin": (C.c_int, [_P, C.c_int]),
     "qed_compact_noalloc": (C.c_int, [C.POINTER(qed_species), C.c_int, _P, _P]),
+    "qed_run_batched": (C.c_int, [_P, C.POINTER(qed_species), C.POINTER(qed_species),
+                                  C.POINTER(qed_species), C.POINTER(qed_fields), C.c_int64, C.c_int,
+                                  C.c_int, _P, _P]),
+    "qed_autotune": (C.c_int, [_P, C.POINTER(qed_species), C.POINTER(qed_species),
+                               C.POINTER(qed_species), C.POINTER(qed_fields), C.c_int,
+                               C.POINTER(C.c_int), C.POINTER(C.c_double), _P]),
     "qed_mlp_load": (C.c_int, [_P, _P, C.c_size_t]),
     "qed_mlp_get": (C.c_int, [_P, _P, C.c_size_t]),
     "qed_mlp_train": (C.c_int, [_P, C.c_int64, C.c_float, C.c_uint64, C.POINTER(C.c_double), _P]),

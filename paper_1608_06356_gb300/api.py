@@ -94,6 +94,7 @@ class Species:
     bx: torch.Tensor | None = None
     by: torch.Tensor | None = None
     bz: torch.Tensor | None = None
+    tag: torch.Tensor | None = None   # int32 storage of the uint32 tags
 
     @property
     def capacity(self) -> int:
@@ -101,7 +102,7 @@ class Species:
 
     @staticmethod
     def empty(capacity: int, q: int, dtype=torch.float32, device="cuda", fields=False,
-              alive=None) -> "Species":
+              alive=None, tag=False) -> "Species":
         cap = max(int(capacity), 0)
         mk = lambda: torch.zeros(cap, dtype=dtype, device=device)
         kw = {k: mk() for k in STATE}
@@ -112,6 +113,7 @@ class Species:
         return Species(id=torch.zeros(cap, dtype=torch.int64, device=device),
                        n=torch.zeros(1, dtype=torch.int64, device=device), q=q,
                        alive=torch.zeros(cap, dtype=torch.uint8, device=device) if alive else None,
+                       tag=torch.zeros(cap, dtype=torch.int32, device=device) if tag else None,
                        **kw)
 
     def load(self, **arrays) -> "Species":
@@ -121,6 +123,8 @@ class Species:
             t = torch.as_tensor(np.ascontiguousarray(v)) if isinstance(v, np.ndarray) else v
             if k == "id":
                 t = t.to(torch.int64) if t.dtype != torch.uint64 else t.view(torch.int64)
+            if k == "tag":
+                t = t.to(torch.int32)
             n = t.numel() if n is None else n
             getattr(self, k)[:n].copy_(t.reshape(-1))
         if self.alive is not None and "alive" not in arrays and n:
@@ -133,7 +137,7 @@ class Species:
 
     def host(self, names=None) -> dict:
         n = self.count()
-        names = names or [k for k in STATE + ("id", "alive") + FIELD_NAMES
+        names = names or [k for k in STATE + ("id", "alive", "tag") + FIELD_NAMES
                           if getattr(self, k) is not None]
         out = {}
         for k in names:
@@ -141,12 +145,12 @@ class Species:
             if t is None:
                 continue
             a = t[:n].cpu().numpy()
-            out[k] = a.view(np.uint64) if k == "id" else a
+            out[k] = a.view(np.uint64) if k == "id" else (a.view(np.uint32) if k == "tag" else a)
         return out
 
     def struct(self) -> B.qed_species:
         s = B.qed_species()
-        for k in STATE + FIELD_NAMES + ("id", "alive"):
+        for k in STATE + FIELD_NAMES + ("id", "alive", "tag"):
             t = getattr(self, k)
             setattr(s, k, t.data_ptr() if t is not None and t.numel() else None)
         s.d_n = self.n.data_ptr()
@@ -338,3 +342,25 @@ def mlp_init_params(seed: int = 0) -> np.ndarray:
     w = np.concatenate(parts).astype(np.float32)
     assert w.size == B.MLP_NP
     return w
+
+
+def qed_run_batched(ctx: Context, e: Species, p: Species, g: Species, f, step0: int, steps: int,
+                    n_runs: int = 0, stream=None) -> torch.Tensor | None:
+    """Advance the concatenated runs by `steps` fused steps as one CUDA graph.
+    Returns the alive photons per run (device int64[n_runs]) when n_runs > 0."""
+    out = torch.zeros(max(n_runs, 1), dtype=torch.int64, device="cuda") if n_runs else None
+    B.check(B.lib().qed_run_batched(ctx.handle, C.byref(e.struct()), C.byref(p.struct()),
+                                    C.byref(g.struct()), C.byref(f), int(step0), int(steps),
+                                    int(n_runs), out.data_ptr() if out is not None else None,
+                                    _stream(stream)), "qed_run_batched")
+    return out
+
+
+def qed_autotune(ctx: Context, e: Species, p: Species, g: Species, f, reps: int = 3,
+                 stream=None) -> tuple[int, list]:
+    best = C.c_int()
+    ms = (C.c_double * 8)()
+    B.check(B.lib().qed_autotune(ctx.handle, C.byref(e.struct()), C.byref(p.struct()),
+                                 C.byref(g.struct()), C.byref(f), int(reps), C.byref(best), ms,
+                                 _stream(stream)), "qed_autotune")
+    return best.value, [ms[i] for i in range(8)]

@@ -94,6 +94,9 @@ extern "C" void qed_destroy(qed_ctx *c) {
   if (!c) return;
   cudaDeviceSynchronize();
   prof_release(c);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+  if (c->d_step) cudaFree(c->d_step);
   free_ctx(c);
 }
 
@@ -209,6 +212,12 @@ extern "C" int qed_init_tables(const qed_config *cfg, qed_ctx **out, qed_stream_
   e = cudaMemcpyAsync(c->sync, init_sync, sizeof(init_sync), cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { free_ctx(c); return cuda_fail(e, "init"); }
+  if (cudaMalloc(&c->d_step, sizeof(int64_t)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (c->d_step) cudaFree(c->d_step);
+    free_ctx(c);
+    return QED_ERR_NOMEM;
+  }
   rc = build_tables(c, st);
   if (rc == QED_OK) rc = mlp_alloc(c);
   if (rc != QED_OK) { free_ctx(c); return rc; }

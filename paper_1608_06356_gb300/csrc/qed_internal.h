@@ -37,6 +37,14 @@ struct qed_ctx {
   double *mlp_loss;
   int mlp_parts, mlp_ready;
   int64_t mlp_step;
+  // graph replay: device step counter read by the kernels when non-null
+  int64_t *d_step;
+  int use_dstep;
+  cudaGraphExec_t graph_exec;
+  cudaStream_t capture_stream;  // non-blocking stream the graph is captured on
+  unsigned long long graph_key[24];
+  // persistent-grid occupancy factor (0 = as many CTAs per SM as fit)
+  int grid_factor;
   // measurement hooks (qed_profile_begin/end): 3 events per profiled step
   cudaEvent_t *prof_ev;
   int prof_max, prof_n;
@@ -45,5 +53,12 @@ struct qed_ctx {
 namespace qed {
 int build_tables(qed_ctx *c, cudaStream_t st);
 int mlp_alloc(qed_ctx *c);
+// CTAs per SM for a persistent launch: the occupancy limit, capped by the
+// autotuned factor when one is set
+inline int persistent_blocks_per_sm(const qed_ctx *c, int occupancy) {
+  int b = occupancy < 1 ? 1 : occupancy;
+  if (c->grid_factor > 0 && c->grid_factor < b) b = c->grid_factor;
+  return b;
+}
 constexpr int TILE = 256;  // particles per tile = threads per block in the step kernels
 }  // namespace qed

@@ -82,6 +82,7 @@ template <class Real> struct NoallocCompactArgs {
   Real *v[13];  // x y z px py pz w ex ey ez bx by bz (field arrays may be null)
   uint64_t *id;
   uint8_t *alive;
+  uint32_t *tag;       // optional
   int64_t *d_n;
   uint32_t *d_status;  // caller-owned, may be null
   ScanState scan;
@@ -115,8 +116,10 @@ __global__ void __launch_bounds__(TILE) k_compact_noalloc(NoallocCompactArgs<Rea
     uint32_t keep = 0;
     Real r[13];
     uint64_t id = 0;
+    uint32_t tg = 0;
     if (i < n && A.alive[i]) {
       keep = 1;
+      if (A.tag) tg = A.tag[i];
 #pragma unroll
       for (int c = 0; c < 7; ++c) r[c] = A.v[c][i];
       if (fields) {
@@ -145,6 +148,7 @@ __global__ void __launch_bounds__(TILE) k_compact_noalloc(NoallocCompactArgs<Rea
       }
       A.id[d] = id;
       A.alive[d] = 1;
+      if (A.tag) A.tag[d] = tg;
     }
   }
   if (threadIdx.x == 0 && status && A.d_status) atomicOr(A.d_status, status);
@@ -180,6 +184,7 @@ int launch_noalloc(const qed_species *s, uint32_t *d_status, cudaStream_t st) {
   for (int c = 0; c < 13; ++c) a.v[c] = static_cast<Real *>(arrs[c]);
   a.id = s->id;
   a.alive = s->alive;
+  a.tag = s->tag;
   a.d_n = s->d_n;
   a.d_status = d_status;
   a.scan = ScanState{scratch, sync, NOALLOC_MAX_TILES};

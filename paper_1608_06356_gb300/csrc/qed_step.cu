@@ -29,6 +29,7 @@ template <class Real> struct Sp {
   int64_t *d_n;
   int64_t cap;
   Real q;
+  uint32_t *tag;  // optional, inherited by children
 };
 
 template <class Real> struct Fld {
@@ -187,6 +188,7 @@ template <class Real> struct LeptonArgs {
   uint8_t *heavy_flags;     // [main-pass slots] 1 = deferred to the heavy pass
   const int *heavy_list;    // ordered main-pass slots of the deferred particles
   const int64_t *heavy_n;   // length of heavy_list
+  const int64_t *d_step;    // if set, the step index is read here (graph replay)
   const uint32_t *mlp_frag; // learned inverse CDF (used when use_mlp)
   const float *mlp_w;
   int use_mlp;
@@ -218,11 +220,12 @@ __device__ __forceinline__ int spec_bin(const Consts &C, Real eps) {
 template <class Real>
 __device__ __forceinline__ void write_child(const Sp<Real> &d, int64_t slot, Real x, Real y, Real z,
                                             Real px, Real py, Real pz, Real w, uint64_t id,
-                                            const Real E[3], const Real B[3]) {
+                                            const Real E[3], const Real B[3], uint32_t tag) {
   d.x[slot] = x; d.y[slot] = y; d.z[slot] = z;
   d.px[slot] = px; d.py[slot] = py; d.pz[slot] = pz;
   d.w[slot] = w;
   d.id[slot] = id;
+  if (d.tag) d.tag[slot] = tag;
   if (d.alive) d.alive[slot] = 1;
   if (d.ex) {
     d.ex[slot] = E[0]; d.ey[slot] = E[1]; d.ez[slot] = E[2];
@@ -240,6 +243,7 @@ enum { PASS_MAIN = 0, PASS_HEAVY = 1 };
 
 template <class Real, int FM, int MODE, int PASS>
 __global__ void __launch_bounds__(TILE, 3) k_lepton(LeptonArgs<Real> A) {
+  const int64_t step_ = A.d_step ? *A.d_step : A.step;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // FP32 tables are staged in shared memory; the finer FP64 tables are read
   // through L1/L2 (the FP64 path serves small, launch-bound ensembles).
@@ -300,6 +304,7 @@ __global__ void __launch_bounds__(TILE, 3) k_lepton(LeptonArgs<Real> A) {
     Real x = 0, y = 0, z = 0, px = 0, py = 0, pz = 0, wt = 0, g = 1;
     Real E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
     uint64_t pid = 0;
+    uint32_t ptag = 0;
     uint32_t cnt = 0;
     uint8_t heavy = 0;
     Real nx = 0, ny = 0, nz = 0;
@@ -313,7 +318,7 @@ __global__ void __launch_bounds__(TILE, 3) k_lepton(LeptonArgs<Real> A) {
       x = S.x[i]; y = S.y[i]; z = S.z[i];
       px = S.px[i]; py = S.py[i]; pz = S.pz[i];
       get_fields<Real, FM>(S, A.f, i, x, y, z, E, B);
-      if (emit) { wt = S.w[i]; pid = S.id[i]; }
+      if (emit) { wt = S.w[i]; pid = S.id[i]; if (S.tag) ptag = S.tag[i]; }
       if (MODE != MODE_EMIT) {
         g = boris(px, py, pz, E, B, S.q, dt);
         Real ig = dt / g;
@@ -348,7 +353,7 @@ __global__ void __launch_bounds__(TILE, 3) k_lepton(LeptonArgs<Real> A) {
           if (pm > (Real)0) { Real ip = (Real)1 / pm; nx = px * ip; ny = py * ip; nz = pz * ip; }
           g_init = g; chi_init = chi; ro_init = ro;
           for (int64_t k = 0; k < N; ++k) {
-            U4 r = draw(A.C.seed, pid, A.step, k, STREAM_EMIT);
+            U4 r = draw(A.C.seed, pid, step_, k, STREAM_EMIT);
             if (!(ro.W * dts > unif<Real>(r.x))) continue;
             XiOut<Real> xo = photon_xi(A.T.Y, A.T, ro.l, chi, ro.kmin, unif<Real>(r.y),
                                        unif<Real>(~r.y), tl);
@@ -402,9 +407,9 @@ __global__ void __launch_bounds__(TILE, 3) k_lepton(LeptonArgs<Real> A) {
           if (b >= 0) atomicAdd(&bt.hist[b], 1ull);
           int64_t slot = base + j;
           if (slot >= A.ph.cap) { tl.dropped += 1; tl.status |= QED_STATUS_CAPACITY; continue; }
-          U4 cid = draw(A.C.seed, pid, A.step, kk, STREAM_PHOTON_ID);
+          U4 cid = draw(A.C.seed, pid, step_, kk, STREAM_PHOTON_ID);
           write_child(A.ph, slot, x, y, z, eph * nx, eph * ny, eph * nz, wt,
-                      (uint64_t)cid.x | ((uint64_t)cid.y << 32), Ec, Bc);
+                      (uint64_t)cid.x | ((uint64_t)cid.y << 32), Ec, Bc, ptag);
         }
       } else {
         // replay the emission loop (deterministic: same draws, same tables)
@@ -415,7 +420,7 @@ __global__ void __launch_bounds__(TILE, 3) k_lepton(LeptonArgs<Real> A) {
         const Real dts = dt / (Real)N;
         uint32_t j = 0;
         for (int64_t k = 0; k < N && j < cnt; ++k) {
-          U4 r = draw(A.C.seed, pid, A.step, k, STREAM_EMIT);
+          U4 r = draw(A.C.seed, pid, step_, k, STREAM_EMIT);
           if (!(ro.W * dts > unif<Real>(r.x))) continue;
           XiOut<Real> xo = photon_xi(A.T.Y, A.T, ro.l, chi, ro.kmin, unif<Real>(r.y),
                                      unif<Real>(~r.y), dummy);
@@ -429,9 +434,9 @@ __global__ void __launch_bounds__(TILE, 3) k_lepton(LeptonArgs<Real> A) {
             tl.dropped += 1;
             tl.status |= QED_STATUS_CAPACITY;
           } else {
-            U4 cid = draw(A.C.seed, pid, A.step, k, STREAM_PHOTON_ID);
+            U4 cid = draw(A.C.seed, pid, step_, k, STREAM_PHOTON_ID);
             write_child(A.ph, slot, x, y, z, eph * nx, eph * ny, eph * nz, wt,
-                        (uint64_t)cid.x | ((uint64_t)cid.y << 32), Ec, Bc);
+                        (uint64_t)cid.x | ((uint64_t)cid.y << 32), Ec, Bc, ptag);
           }
           Real pm2 = m_sqrt((g2 - (Real)1) * (g2 + (Real)1));
           gg = g2;
@@ -458,6 +463,7 @@ __global__ void __launch_bounds__(TILE, 3) k_lepton(LeptonArgs<Real> A) {
 // ---------------------------------------------------------------------------
 template <class Real, int FM, int MODE>
 __global__ void __launch_bounds__(TILE) k_lepton_stream(LeptonArgs<Real> A) {
+  const int64_t step_ = A.d_step ? *A.d_step : A.step;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool kSmem = sizeof(Real) == 4;
   Real *sR = kSmem ? reinterpret_cast<Real *>(smem_raw) : const_cast<Real *>(A.T.R);
@@ -516,7 +522,7 @@ __global__ void __launch_bounds__(TILE) k_lepton_stream(LeptonArgs<Real> A) {
           const Real q = wdt / wdt_max;
           flag = q <= (Real)3 ? 2 : (q <= (Real)7 ? 3 : (q <= (Real)15 ? 4 : 5));
         } else {
-          U4 r = draw(A.C.seed, pid, A.step, 0, STREAM_EMIT);
+          U4 r = draw(A.C.seed, pid, step_, 0, STREAM_EMIT);
           if (wdt > unif<Real>(r.x)) flag = 1;
         }
         if (flag == 0) {
@@ -613,6 +619,7 @@ __global__ void __launch_bounds__(TILE) k_heavy_list(HeavyListArgs A) {
 // ---------------------------------------------------------------------------
 template <class Real, int FM, int MODE>
 __global__ void __launch_bounds__(TILE) k_lepton_emit1(LeptonArgs<Real> A) {
+  const int64_t step_ = A.d_step ? *A.d_step : A.step;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool kSmem = sizeof(Real) == 4;
   Real *sR = kSmem ? reinterpret_cast<Real *>(smem_raw) : const_cast<Real *>(A.T.R);
@@ -657,12 +664,14 @@ __global__ void __launch_bounds__(TILE) k_lepton_emit1(LeptonArgs<Real> A) {
     Real x = 0, y = 0, z = 0, px = 0, py = 0, pz = 1, wt = 0;
     Real E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
     uint64_t pid = 0;
+    uint32_t ptag = 0;
     if (active) {
       x = S.x[i]; y = S.y[i]; z = S.z[i];
       px = S.px[i]; py = S.py[i]; pz = S.pz[i];
       get_fields<Real, FM>(S, A.f, i, x, y, z, E, B);
       pid = S.id[i];
       wt = S.w[i];
+      if (S.tag) ptag = S.tag[i];
     }
     Real g;
     if (MODE != MODE_EMIT) {
@@ -674,7 +683,7 @@ __global__ void __launch_bounds__(TILE) k_lepton_emit1(LeptonArgs<Real> A) {
     }
     Real chi = chi_lepton(px, py, pz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
     RateOut<Real> ro = photon_rate(sR, sF, A.T, A.C, chi, g, tl);
-    U4 r = draw(A.C.seed, pid, A.step, 0, STREAM_EMIT);
+    U4 r = draw(A.C.seed, pid, step_, 0, STREAM_EMIT);
     const Real kap = photon_kappa(ro.kmin, unif<Real>(r.y), unif<Real>(~r.y));
     Real Y = 0;
     bool in_mlp = false;
@@ -703,9 +712,9 @@ __global__ void __launch_bounds__(TILE) k_lepton_emit1(LeptonArgs<Real> A) {
     if (b >= 0) atomicAdd(&bt.hist[b], 1ull);
     const int64_t out = base + h;
     if (out < A.ph.cap) {
-      U4 cid = draw(A.C.seed, pid, A.step, 0, STREAM_PHOTON_ID);
+      U4 cid = draw(A.C.seed, pid, step_, 0, STREAM_PHOTON_ID);
       write_child(A.ph, out, x, y, z, eph * nx, eph * ny, eph * nz, wt,
-                  (uint64_t)cid.x | ((uint64_t)cid.y << 32), E, B);
+                  (uint64_t)cid.x | ((uint64_t)cid.y << 32), E, B, ptag);
     } else {
       tl.dropped += 1;
       tl.status |= QED_STATUS_CAPACITY;
@@ -743,6 +752,7 @@ template <class Real> struct PhotonArgs {
   uint8_t *flags;       // streaming pass: 1 = redo in the ordered pass
   const int *list;      // ordered pass: photon indices to process
   const int64_t *list_n;
+  const int64_t *d_step;  // if set, the step index is read here (graph replay)
 };
 
 // ---------------------------------------------------------------------------
@@ -753,6 +763,7 @@ template <class Real> struct PhotonArgs {
 // ---------------------------------------------------------------------------
 template <class Real, int FM>
 __global__ void __launch_bounds__(TILE) k_photon_stream(PhotonArgs<Real> A) {
+  const int64_t step_ = A.d_step ? *A.d_step : A.step;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real *sP = reinterpret_cast<Real *>(smem_raw);
   __shared__ long long s_meta[2];
@@ -784,7 +795,7 @@ __global__ void __launch_bounds__(TILE) k_photon_stream(PhotonArgs<Real> A) {
       if (wdt > wdt_max) {
         flag = 1;
       } else if (ro.W > (Real)0) {
-        U4 r = draw(A.C.seed, A.ph.id[i], A.step, 0, STREAM_PAIR);
+        U4 r = draw(A.C.seed, A.ph.id[i], step_, 0, STREAM_PAIR);
         if (wdt > unif<Real>(r.x)) flag = 1;
       }
       if (!flag) {
@@ -806,6 +817,7 @@ __global__ void __launch_bounds__(TILE) k_photon_stream(PhotonArgs<Real> A) {
 
 template <class Real, int FM, int LIST>
 __global__ void __launch_bounds__(TILE) k_photon(PhotonArgs<Real> A) {
+  const int64_t step_ = A.d_step ? *A.d_step : A.step;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real *sP = reinterpret_cast<Real *>(smem_raw);
   __shared__ uint32_t scan_sm[33];
@@ -840,6 +852,7 @@ __global__ void __launch_bounds__(TILE) k_photon(PhotonArgs<Real> A) {
     Real x = 0, y = 0, z = 0, px = 0, py = 0, pz = 0, wt = 0, k = 0;
     Real E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
     uint64_t pid = 0;
+    uint32_t ptag = 0;
     uint32_t cnt = 0;
     Real ge = 0, gp = 0;
     int64_t ks = 0;
@@ -847,6 +860,7 @@ __global__ void __launch_bounds__(TILE) k_photon(PhotonArgs<Real> A) {
       x = A.ph.x[i]; y = A.ph.y[i]; z = A.ph.z[i];
       px = A.ph.px[i]; py = A.ph.py[i]; pz = A.ph.pz[i];
       wt = A.ph.w[i]; pid = A.ph.id[i];
+      if (A.ph.tag) ptag = A.ph.tag[i];
       get_fields<Real, FM>(A.ph, A.f, i, x, y, z, E, B);
       k = m_sqrt(px * px + py * py + pz * pz);
       if (k > (Real)0) {
@@ -867,7 +881,7 @@ __global__ void __launch_bounds__(TILE) k_photon(PhotonArgs<Real> A) {
       const Real dts = dt / (Real)N;
       tl.substeps += N;
       for (int64_t s = 0; s < N; ++s) {
-        U4 r = draw(A.C.seed, pid, A.step, s, STREAM_PAIR);
+        U4 r = draw(A.C.seed, pid, step_, s, STREAM_PAIR);
         if (!(ro.W * dts > unif<Real>(r.x))) continue;
         XiOut<Real> xo = pair_xi(A.T.Yp, A.T, ro.l, unif<Real>(r.y), unif<Real>(~r.y));
         ge = xo.xi * k;
@@ -901,16 +915,16 @@ __global__ void __launch_bounds__(TILE) k_photon(PhotonArgs<Real> A) {
       const int64_t off = s_meta[1] + excl;
       Real ik = (Real)1 / k;
       Real nx = px * ik, ny = py * ik, nz = pz * ik;
-      U4 cid = draw(A.C.seed, pid, A.step, ks, STREAM_PAIR_ID);
+      U4 cid = draw(A.C.seed, pid, step_, ks, STREAM_PAIR_ID);
       Real pe = m_sqrt((ge - (Real)1) * (ge + (Real)1));
       Real pp = m_sqrt((gp - (Real)1) * (gp + (Real)1));
       if (ne + off < A.el.cap)
         write_child(A.el, ne + off, x, y, z, pe * nx, pe * ny, pe * nz, wt,
-                    (uint64_t)cid.x | ((uint64_t)cid.y << 32), E, B);
+                    (uint64_t)cid.x | ((uint64_t)cid.y << 32), E, B, ptag);
       else { tl.dropped += 1; tl.status |= QED_STATUS_CAPACITY; }
       if (np + off < A.po.cap)
         write_child(A.po, np + off, x, y, z, pp * nx, pp * ny, pp * nz, wt,
-                    (uint64_t)cid.z | ((uint64_t)cid.w << 32), E, B);
+                    (uint64_t)cid.z | ((uint64_t)cid.w << 32), E, B, ptag);
       else { tl.dropped += 1; tl.status |= QED_STATUS_CAPACITY; }
     }
   }
@@ -955,8 +969,10 @@ __global__ void __launch_bounds__(TILE) k_compact(CompactArgs<Real> A) {
     uint32_t keep = 0;
     Real v[13];
     uint64_t id = 0;
+    uint32_t tg = 0;
     if (i < n && A.s.alive[i]) {
       keep = 1;
+      if (A.s.tag) tg = A.s.tag[i];
       v[0] = A.s.x[i]; v[1] = A.s.y[i]; v[2] = A.s.z[i];
       v[3] = A.s.px[i]; v[4] = A.s.py[i]; v[5] = A.s.pz[i]; v[6] = A.s.w[i];
       id = A.s.id[i];
@@ -981,6 +997,7 @@ __global__ void __launch_bounds__(TILE) k_compact(CompactArgs<Real> A) {
       A.s.px[d] = v[3]; A.s.py[d] = v[4]; A.s.pz[d] = v[5]; A.s.w[d] = v[6];
       A.s.id[d] = id;
       A.s.alive[d] = 1;
+      if (A.s.tag) A.s.tag[d] = tg;
       if (fields) {
         A.s.ex[d] = v[7]; A.s.ey[d] = v[8]; A.s.ez[d] = v[9];
         A.s.bx[d] = v[10]; A.s.by[d] = v[11]; A.s.bz[d] = v[12];
@@ -1136,6 +1153,7 @@ template <class Real> Sp<Real> to_sp(const qed_species *s) {
   d.ex = (Real *)s->ex; d.ey = (Real *)s->ey; d.ez = (Real *)s->ez;
   d.bx = (Real *)s->bx; d.by = (Real *)s->by; d.bz = (Real *)s->bz;
   d.d_n = s->d_n; d.cap = s->capacity; d.q = (Real)s->q;
+  d.tag = s->tag;
   return d;
 }
 
@@ -1210,7 +1228,7 @@ static cudaError_t launch_flag_list(qed_ctx *c, const uint8_t *flags, uint8_t wa
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_heavy_list, TILE, 0);
   if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
+  per_sm = persistent_blocks_per_sm(c, per_sm);
   k_heavy_list<<<c->num_sms * per_sm, TILE, 0, st>>>(h);
   c->launches += 1;
   return cudaGetLastError();
@@ -1225,7 +1243,7 @@ static cudaError_t launch_lepton_pass(qed_ctx *c, const LeptonArgs<Real> &a, cud
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE, sm);
   if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
+  per_sm = persistent_blocks_per_sm(c, per_sm);
   kern<<<c->num_sms * per_sm, TILE, sm, st>>>(a);
   c->launches += 1;
   return cudaGetLastError();
@@ -1240,7 +1258,7 @@ static cudaError_t launch_stream(qed_ctx *c, const LeptonArgs<Real> &a, cudaStre
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE, sm);
   if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
+  per_sm = persistent_blocks_per_sm(c, per_sm);
   kern<<<c->num_sms * per_sm, TILE, sm, st>>>(a);
   c->launches += 1;
   return cudaGetLastError();
@@ -1256,7 +1274,7 @@ static cudaError_t launch_emit1(qed_ctx *c, const LeptonArgs<Real> &a, cudaStrea
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE, sm);
   if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
+  per_sm = persistent_blocks_per_sm(c, per_sm);
   kern<<<c->num_sms * per_sm, TILE, sm, st>>>(a);
   c->launches += 1;
   return cudaGetLastError();
@@ -1308,6 +1326,7 @@ cudaError_t launch_lepton(qed_ctx *c, const qed_species *s0, const qed_species *
   a.mlp_frag = c->mlp_frag;
   a.mlp_w = c->mlp_w;
   a.use_mlp = c->cfg.sampler == QED_SAMPLER_MLP && c->mlp_ready;
+  a.d_step = c->use_dstep ? c->d_step : nullptr;
   if (mode == MODE_PUSH) return launch_lepton_m<Real, MODE_PUSH>(c, a, f->mode, st);
   if (mode == MODE_EMIT) return launch_lepton_m<Real, MODE_EMIT>(c, a, f->mode, st);
   return launch_lepton_m<Real, MODE_FUSED>(c, a, f->mode, st);
@@ -1320,7 +1339,7 @@ static cudaError_t launch_photon_t(qed_ctx *c, const PhotonArgs<Real> &a, cudaSt
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_photon_stream<Real, FM>,
                                                                 TILE, sm);
   if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
+  per_sm = persistent_blocks_per_sm(c, per_sm);
   k_photon_stream<Real, FM><<<c->num_sms * per_sm, TILE, sm, st>>>(a);
   c->launches += 1;
   e = cudaGetLastError();
@@ -1329,7 +1348,7 @@ static cudaError_t launch_photon_t(qed_ctx *c, const PhotonArgs<Real> &a, cudaSt
   auto kern = k_photon<Real, FM, 1>;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE, sm);
   if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
+  per_sm = persistent_blocks_per_sm(c, per_sm);
   kern<<<c->num_sms * per_sm, TILE, sm, st>>>(a);
   c->launches += 1;
   return cudaGetLastError();
@@ -1352,6 +1371,7 @@ cudaError_t launch_photon(qed_ctx *c, const qed_species *g, const qed_species *e
   a.flags = c->heavy_flags;
   a.list = c->heavy_list;
   a.list_n = c->heavy_n;
+  a.d_step = c->use_dstep ? c->d_step : nullptr;
   if (f->mode == QED_FIELDS_UNIFORM) return launch_photon_t<Real, FM_UNIFORM>(c, a, st);
   if (f->mode == QED_FIELDS_PER_PARTICLE) return launch_photon_t<Real, FM_PER_PARTICLE>(c, a, st);
   return launch_photon_t<Real, FM_GRID>(c, a, st);
@@ -1365,7 +1385,7 @@ cudaError_t launch_compact(qed_ctx *c, const qed_species *s, cudaStream_t st) {
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_compact<Real>, TILE, 0);
   if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
+  per_sm = persistent_blocks_per_sm(c, per_sm);
   k_compact<Real><<<c->num_sms * per_sm, TILE, 0, st>>>(a);
   c->launches += 1;
   return cudaGetLastError();
@@ -1394,7 +1414,7 @@ cudaError_t launch_sample_xi(qed_ctx *c, const float *chi, const float *gamma, f
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample_xi, TILE, sm);
   if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
+  per_sm = persistent_blocks_per_sm(c, per_sm);
   k_sample_xi<<<c->num_sms * per_sm, TILE, sm, st>>>(a);
   c->launches += 1;
   return cudaGetLastError();
