@@ -50,6 +50,21 @@ def workload_desc(n):
             "sampler": "table", "l2": "inputs larger than L2 (>= 5.4 GB read per step)"}
 
 
+def rank_id_offset(rank: int) -> int:
+    """Particle ids of rank r start at r << 40, so shards never share an id."""
+    return int(rank) << 40
+
+
+def reduce_over_ranks(dist, ms: float, particle_steps: float, device):
+    """Timing across ranks: the slowest rank's time and the total work."""
+    import torch
+    tt = torch.tensor([ms, particle_steps], dtype=torch.float64, device=device)
+    mx = tt.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(tt[1])
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -352,7 +367,7 @@ def main():
     cap_p = 2 * n
     ctx = api.qed_init_tables(api.config(dt=DT, seed=1 + rank, max_particles=max(cap_g, cap_e)))
     host = host_workload(n, seed=rank)
-    host["id"] += np.uint64(rank) << np.uint64(40)
+    host["id"] += np.uint64(rank_id_offset(rank))
     e = api.Species.empty(cap_e, -1, fields=True).load(**host)
     p = api.Species.empty(cap_p, +1, fields=True)
     g = api.Species.empty(cap_g, 0, fields=True)
@@ -398,11 +413,7 @@ def main():
     t_max = ms
     ps_total = ps_local
     if world > 1:
-        tt = torch.tensor([ms, ps_local], dtype=torch.float64, device="cuda")
-        mx = tt.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        t_max, ps_total = float(mx[0]), float(tt[1])
+        t_max, ps_total = reduce_over_ranks(dist, ms, ps_local, "cuda")
     value = ps_total / (t_max * 1e-3)
 
     # roofline of the dominant (lepton) kernel: algorithmic bytes / event time
