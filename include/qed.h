@@ -64,7 +64,10 @@ enum {
   QED_STATUS_DOMAIN = 2u,   /* chi (or delta_min) outside the table range: clamped */
   QED_STATUS_NONFINITE = 4u,/* non-finite momentum or field met (particle skipped) */
   QED_STATUS_TIMEOUT = 8u,  /* a look-back wait hit its iteration limit */
-  QED_STATUS_SUBSTEPS = 16u /* sub-step count was capped at qed_config.max_substeps */
+  QED_STATUS_SUBSTEPS = 16u,/* sub-step count was capped at qed_config.max_substeps */
+  QED_STATUS_REPLAY = 32u   /* a replayed emission chain found fewer photons than its
+                               counting pass (should not happen); the missing photons
+                               were written with zero energy */
 };
 
 enum { QED_FP32 = 0, QED_FP64 = 1 };
@@ -86,7 +89,10 @@ typedef struct {
   double inv_per_unit;  /* inverse-table nodes per unit of kappa (0 = default) */
   uint64_t seed;        /* Philox4x32-10 key */
   double spec_lo, spec_hi; /* photon-energy histogram: 64 log bins over [spec_lo, spec_hi) m c^2 */
-  int64_t max_particles;   /* largest per-species capacity any call will use (sizes scan state) */
+  int64_t max_particles;   /* largest per-species capacity any call will use (sizes scan
+                              state and the sub-step scratch, about 70 (FP32) or 110
+                              (FP64) bytes per particle); default 2^24, at most
+                              2^30 - 4096 */
   int64_t max_substeps;    /* cap on N per particle per step (status bit when hit) */
   int sampler;             /* QED_SAMPLER_TABLE (default) or QED_SAMPLER_MLP (FP32 contexts) */
   int pad2_;

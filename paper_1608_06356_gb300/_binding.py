@@ -19,7 +19,7 @@ QED_SAMPLER_TABLE, QED_SAMPLER_MLP = 0, 1
 MLP_NP = 8577
 QED_FIELDS_UNIFORM, QED_FIELDS_PER_PARTICLE, QED_FIELDS_GRID = 0, 1, 2
 QED_STATUS_CAPACITY, QED_STATUS_DOMAIN, QED_STATUS_NONFINITE = 1, 2, 4
-QED_STATUS_TIMEOUT, QED_STATUS_SUBSTEPS = 8, 16
+QED_STATUS_TIMEOUT, QED_STATUS_SUBSTEPS, QED_STATUS_REPLAY = 8, 16, 32
 
 ERRORS = {-1: "QED_ERR_ARG", -2: "QED_ERR_CUDA", -3: "QED_ERR_CAPACITY", -4: "QED_ERR_DOMAIN",
           -5: "QED_ERR_TIMEOUT", -6: "QED_ERR_NOCONV", -7: "QED_ERR_NOMEM", -8: "QED_ERR_UNSUPPORTED"}

@@ -53,7 +53,7 @@ extern "C" void qed_config_default(qed_config *c) {
   c->seed = 0;
   c->spec_lo = 2.0;
   c->spec_hi = 1000.0;
-  c->max_particles = (int64_t)1 << 26;
+  c->max_particles = (int64_t)1 << 24;
   c->max_substeps = (int64_t)1 << 16;
 }
 
@@ -76,7 +76,10 @@ static void free_ctx(qed_ctx *c) {
   if (!c) return;
   void *ptrs[] = {c->R64, c->F64, c->Y64, c->P64, c->Yp64, c->R32, c->F32, c->Y32,
                   c->P32, c->Yp32, c->tile_state, c->sync, c->snap, c->d_counters,
-                  c->heavy_flags, c->heavy_list, c->heavy_n, c->mlp_mem};
+                  c->heavy_flags, c->heavy_list, c->heavy_n, c->cls_chunk_cnt,
+                  c->cls_chunk_off, c->cls_off, c->sub_cnt, c->sub_gf, c->rec_e,
+                  c->rec_k, c->sub_meta, c->stage, c->stage_tag, c->stage_idx, c->stage_n,
+                  c->mlp_mem};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   free(c);
@@ -143,7 +146,7 @@ static bool cfg_valid(const qed_config *c) {
          (c->precision == QED_FP32 || c->precision == QED_FP64) && c->chi_min > 0 &&
          c->chi_max > c->chi_min && c->chi_pair_min > 0 && c->chi_pair_max > c->chi_pair_min &&
          c->spec_lo > 0 && c->spec_hi > c->spec_lo && c->max_particles > 0 &&
-         c->max_particles <= ((int64_t)1 << 31) && c->max_substeps >= 1 &&
+         c->max_particles <= ((int64_t)1 << 30) - 4096 && c->max_substeps >= 1 &&
          (c->sampler == QED_SAMPLER_TABLE ||
           (c->sampler == QED_SAMPLER_MLP && c->precision == QED_FP32));
 }
@@ -191,14 +194,39 @@ extern "C" int qed_init_tables(const qed_config *cfg, qed_ctx **out, qed_stream_
     if (!a.bytes) continue;
     if (cudaMalloc(a.p, a.bytes) != cudaSuccess) { free_ctx(c); return QED_ERR_NOMEM; }
   }
-  c->max_tiles = (cfg->max_particles + TILE - 1) / TILE * 2 + 2;
+  // one look-back word per 32-particle warp tile of the sub-step pass (the
+  // 256-particle block tiles of the other passes need fewer)
+  c->max_tiles = (cfg->max_particles + 31) / 32 * 2 + 2;
+  // the deferral flags and lists are indexed by 256-particle block-tile slots
+  // of the two lepton species
+  c->heavy_slots = ((cfg->max_particles + TILE - 1) / TILE * 2 + 2) * TILE;
+  c->cls_chunks = c->heavy_slots / CLS_CHUNK_FLAGS + 1;
+  // emission records for the first max_particles / 4 entries of the sub-step
+  // list; later entries (and particles with more than SUB_REC photons) replay
+  c->rec_cap = cfg->max_particles / 4 > 4096 ? cfg->max_particles / 4 : 4096;
+  const size_t rsize = f64 ? sizeof(double) : sizeof(float);
+  // staging records for the leptons the streaming pass defers (a record is
+  // 16 words); past stage_cap a deferred particle is gathered from its arrays
+  c->stage_cap = cfg->max_particles / 2 > 65536 ? cfg->max_particles / 2 : 65536;
   if (cudaMalloc(&c->tile_state, sizeof(unsigned long long) * c->max_tiles) != cudaSuccess ||
       cudaMalloc(&c->sync, sizeof(unsigned int) * 4) != cudaSuccess ||
       cudaMalloc(&c->snap, sizeof(int64_t) * 4) != cudaSuccess ||
       cudaMalloc(&c->d_counters, sizeof(qed_counters)) != cudaSuccess ||
-      cudaMalloc(&c->heavy_flags, (size_t)c->max_tiles * TILE + 4096) != cudaSuccess ||
-      cudaMalloc(&c->heavy_list, sizeof(int) * (size_t)c->max_tiles * TILE) != cudaSuccess ||
-      cudaMalloc(&c->heavy_n, sizeof(int64_t)) != cudaSuccess) {
+      cudaMalloc(&c->heavy_flags, (size_t)c->heavy_slots + 4096) != cudaSuccess ||
+      cudaMalloc(&c->heavy_list, sizeof(int) * (size_t)c->heavy_slots) != cudaSuccess ||
+      cudaMalloc(&c->heavy_n, sizeof(int64_t)) != cudaSuccess ||
+      cudaMalloc(&c->cls_chunk_cnt, sizeof(unsigned long long) * (size_t)c->cls_chunks) != cudaSuccess ||
+      cudaMalloc(&c->cls_chunk_off, sizeof(uint32_t) * 5 * (size_t)c->cls_chunks) != cudaSuccess ||
+      cudaMalloc(&c->cls_off, sizeof(int64_t) * 8) != cudaSuccess ||
+      cudaMalloc(&c->sub_cnt, sizeof(uint32_t) * (size_t)c->heavy_slots) != cudaSuccess ||
+      cudaMalloc(&c->sub_gf, rsize * (size_t)c->rec_cap) != cudaSuccess ||
+      cudaMalloc(&c->rec_e, rsize * SUB_REC * (size_t)c->rec_cap) != cudaSuccess ||
+      cudaMalloc(&c->rec_k, sizeof(uint32_t) * SUB_REC * (size_t)c->rec_cap) != cudaSuccess ||
+      cudaMalloc(&c->stage, 2 * 8 * rsize * (size_t)c->stage_cap) != cudaSuccess ||
+      cudaMalloc(&c->stage_tag, sizeof(uint32_t) * (size_t)c->stage_cap) != cudaSuccess ||
+      cudaMalloc(&c->stage_idx, sizeof(int32_t) * (size_t)c->heavy_slots) != cudaSuccess ||
+      cudaMalloc(&c->stage_n, sizeof(unsigned int)) != cudaSuccess ||
+      cudaMalloc(&c->sub_meta, 2 * sizeof(int64_t)) != cudaSuccess) {
     free_ctx(c);
     return QED_ERR_NOMEM;
   }
@@ -206,6 +234,7 @@ extern "C" int qed_init_tables(const qed_config *cfg, qed_ctx **out, qed_stream_
   if (e == cudaSuccess) e = cudaMemsetAsync(c->sync, 0, sizeof(unsigned int) * 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->snap, 0, sizeof(int64_t) * 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counters, 0, sizeof(qed_counters), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->stage_n, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) { free_ctx(c); return cuda_fail(e, "memset"); }
   // epoch starts at 1 so that zeroed state words never look valid
   unsigned int init_sync[4] = {0u, 0u, 1u, 0u};

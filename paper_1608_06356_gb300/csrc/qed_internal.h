@@ -22,9 +22,29 @@ struct qed_ctx {
   unsigned int *sync;  // [0] tile counter, [1] done counter, [2] epoch
   int64_t max_tiles;
   int64_t *snap;       // [4] counts snapshotted at the start of a fused step
-  uint8_t *heavy_flags;  // [max_tiles * TILE] main-pass deferral flags
-  int *heavy_list;       // [max_tiles * TILE] ordered deferred slots
-  int64_t *heavy_n;      // length of heavy_list
+  int64_t heavy_slots;   // block-tile slots of both lepton species
+  uint8_t *heavy_flags;  // [heavy_slots] main-pass deferral flags
+  int *heavy_list;       // [heavy_slots] ordered deferred slots
+  int64_t *heavy_n;      // length of heavy_list (photon pass)
+  // class list of the streaming lepton pass: per-chunk packed counts and
+  // per-class offsets, class starts
+  unsigned long long *cls_chunk_cnt;  // [cls_chunks]
+  uint32_t *cls_chunk_off;            // [cls_chunks][5]
+  int64_t *cls_off;                   // [8]
+  int64_t cls_chunks;
+  // sub-step passes: photons per entry, final gamma and emission records
+  uint32_t *sub_cnt;  // [heavy_slots]
+  void *sub_gf;       // Real [rec_cap]
+  void *rec_e;        // Real [SUB_REC][rec_cap]
+  uint32_t *rec_k;    // [SUB_REC][rec_cap]
+  int64_t rec_cap;
+  int64_t *sub_meta;  // [2] photons of the sub-step entries, photon count before them
+  // staging records of the flagged leptons (streaming pass -> later passes)
+  void *stage;          // Stage<Real> [stage_cap] (64 B FP32, 128 B FP64)
+  uint32_t *stage_tag;  // [stage_cap]
+  int32_t *stage_idx;   // [heavy_slots]
+  unsigned int *stage_n;
+  int64_t stage_cap;
   qed_counters *d_counters;
   // persistent-grid sizes per kernel
   int grid_lepton, grid_photon, grid_compact;
@@ -61,4 +81,6 @@ inline int persistent_blocks_per_sm(const qed_ctx *c, int occupancy) {
   return b;
 }
 constexpr int TILE = 256;  // particles per tile = threads per block in the step kernels
+constexpr int SUB_REC = 4; // emission records kept per particle by the sub-step counting pass
+constexpr int CLS_CHUNK_FLAGS = 2048;  // flags per chunk of the class-list passes
 }  // namespace qed

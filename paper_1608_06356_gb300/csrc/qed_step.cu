@@ -41,6 +41,9 @@ template <class Real> struct Fld {
 
 enum { FM_UNIFORM = 0, FM_PER_PARTICLE = 1, FM_GRID = 2 };
 enum { MODE_PUSH = 0, MODE_EMIT = 1, MODE_FUSED = 2 };
+// classes of the streaming lepton pass: 1 one sub-step with an event; 2-5 more
+// than one sub-step, binned by N (<= 3, <= 7, <= 15, >= 16)
+constexpr int NCLS = 5;
 
 struct Out {
   qed_counters *cnt;
@@ -176,6 +179,20 @@ __device__ __forceinline__ void load_tables_smem(Real *dst, const Real *src, int
 // ---------------------------------------------------------------------------
 // Lepton kernel (electrons and positrons in one launch)
 // ---------------------------------------------------------------------------
+// Pushed state of a flagged lepton, written once by the streaming pass so the
+// later passes read 64 (FP32) or 128 (FP64) contiguous bytes per particle
+// instead of gathering a 4- or 8-byte word from each of 14 arrays.
+template <class Real> struct alignas(16) Stage {
+  Real p[3], e[3], b[3];
+  uint32_t id_lo, id_hi;
+  Real w;
+  Real x[3];
+  uint32_t slot;
+};
+static_assert(sizeof(Stage<float>) == 64, "FP32 staging record");
+static_assert(sizeof(Stage<double>) == 128, "FP64 staging record");
+constexpr uint32_t STAGE_BATCH = 256;  // records a warp reserves at a time
+
 template <class Real> struct LeptonArgs {
   Sp<Real> sp[2];
   int nsp;
@@ -189,6 +206,18 @@ template <class Real> struct LeptonArgs {
   const int *heavy_list;    // ordered main-pass slots of the deferred particles
   const int64_t *heavy_n;   // length of heavy_list
   const int64_t *d_step;    // if set, the step index is read here (graph replay)
+  const int64_t *cls_off;   // class list: class c occupies [cls_off[c-1], cls_off[c])
+  Stage<Real> *stage;       // pushed state of the flagged leptons (streaming pass)
+  uint32_t *stage_tag;      // their tags (species with tags)
+  int32_t *stage_idx;       // [slot] staging index of a flagged slot, -1 if not staged
+  unsigned int *stage_n;    // staging allocation counter (reset by the class-list scan)
+  int64_t stage_cap;
+  uint32_t *sub_cnt;        // sub-step passes: photons per class-2..5 entry
+  Real *sub_gf;             // final gamma per entry (entries < rec_cap)
+  Real *rec_e;              // [REC][rec_cap] photon energies
+  uint32_t *rec_k;          // [REC][rec_cap] their sub-step indices
+  int64_t rec_cap;
+  const int64_t *sub_meta;  // [0] photons of the sub-step entries, [1] photon count before them
   const uint32_t *mlp_frag; // learned inverse CDF (used when use_mlp)
   const float *mlp_w;
   int use_mlp;
@@ -233,224 +262,42 @@ __device__ __forceinline__ void write_child(const Sp<Real> &d, int64_t slot, Rea
   }
 }
 
-// Particles whose step needs more than HEAVY_SUBSTEPS generator sub-steps
-// are deferred by the main pass (no state is written for them) and processed
-// by a second pass over a compacted, ordered list of them.  Mixing them with
-// light particles would make every warp, and through the look-back every
-// tile in flight, wait for the slowest lane.
-constexpr int64_t HEAVY_SUBSTEPS = 8;
-enum { PASS_MAIN = 0, PASS_HEAVY = 1 };
-
-template <class Real, int FM, int MODE, int PASS>
-__global__ void __launch_bounds__(TILE, 3) k_lepton(LeptonArgs<Real> A) {
-  const int64_t step_ = A.d_step ? *A.d_step : A.step;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  // FP32 tables are staged in shared memory; the finer FP64 tables are read
-  // through L1/L2 (the FP64 path serves small, launch-bound ensembles).
-  constexpr bool kSmem = sizeof(Real) == 4;
-  Real *sR = kSmem ? reinterpret_cast<Real *>(smem_raw) : const_cast<Real *>(A.T.R);
-  Real *sF = kSmem ? sR + A.T.gl.n : const_cast<Real *>(A.T.F);
-  __shared__ uint32_t scan_sm[33];
-  __shared__ long long s_meta[8];  // tile id, prefix, counts
-  __shared__ BlockTally bt;
-  constexpr bool emit = MODE != MODE_PUSH;
-  constexpr bool defer = emit && PASS == PASS_MAIN;
-  if (emit && kSmem) {
-    load_tables_smem(sR, A.T.R, A.T.gl.n);
-    load_tables_smem(sF, A.T.F, A.T.gl.n * A.T.gy.n);
-  }
-  block_tally_init(&bt);
+// ---------------------------------------------------------------------------
+// Push-only pass (qed_gather_push): field gather, Boris push and position
+// update of every lepton; no emission, so no ordering is needed.
+// ---------------------------------------------------------------------------
+template <class Real, int FM>
+__global__ void __launch_bounds__(TILE) k_lepton_push(LeptonArgs<Real> A) {
+  __shared__ long long s_meta[2];
   if (threadIdx.x == 0) {
-    s_meta[2] = *(volatile int64_t *)A.sp[0].d_n;
-    s_meta[3] = A.nsp > 1 ? *(volatile int64_t *)A.sp[1].d_n : 0;
-    s_meta[4] = emit ? *(volatile int64_t *)A.ph.d_n : 0;
-    s_meta[5] = (long long)A.o.scan.sync[2];
-    s_meta[6] = PASS == PASS_HEAVY ? *(volatile int64_t *)A.heavy_n : 0;
+    s_meta[0] = *(volatile int64_t *)A.sp[0].d_n;
+    s_meta[1] = A.nsp > 1 ? *(volatile int64_t *)A.sp[1].d_n : 0;
   }
   __syncthreads();
-  const int64_t n0 = s_meta[2], n1 = s_meta[3], nph = s_meta[4];
-  const uint32_t epoch = (uint32_t)s_meta[5];
-  const int64_t T0 = (n0 + TILE - 1) / TILE, T1 = (n1 + TILE - 1) / TILE;
-  const int64_t nheavy = s_meta[6];
-  const int64_t ntiles = PASS == PASS_HEAVY ? (nheavy + TILE - 1) / TILE : T0 + T1;
-  const Real inv_aS = sel<Real>(A.C.inv_aS, A.C.f_inv_aS);
+  const int64_t n0 = s_meta[0], n1 = s_meta[1];
   const Real dt = sel<Real>(A.C.dt, A.C.f_dt);
-  Tally tl;
-  tl.clear();
-
-  for (;;) {
-    if (threadIdx.x == 0) s_meta[0] = (long long)atomicAdd(&A.o.scan.sync[0], 1u);
-    __syncthreads();
-    const int64_t t = s_meta[0];
-    __syncthreads();
-    if (t >= ntiles) break;
-    // this lane's particle: species si, index i (main-pass slot g = tile * TILE + lane)
-    int64_t g_slot;
-    bool active;
-    if (PASS == PASS_HEAVY) {
-      const int64_t h = t * TILE + threadIdx.x;
-      active = h < nheavy;
-      g_slot = active ? (int64_t)A.heavy_list[h] : 0;
-    } else {
-      g_slot = t * TILE + threadIdx.x;
-      active = true;
-    }
-    const int64_t tile_main = g_slot / TILE;
-    const int si = tile_main < T0 ? 0 : 1;
+  uint32_t status = 0;
+  for (int64_t g = blockIdx.x * (int64_t)TILE + threadIdx.x; g < n0 + n1;
+       g += (int64_t)gridDim.x * TILE) {
+    const int si = g < n0 ? 0 : 1;
     const Sp<Real> &S = A.sp[si];
-    const int64_t i = (tile_main - (si ? T0 : 0)) * TILE + (g_slot % TILE);
-    active = active && i < (si ? n1 : n0);
-
-    Real x = 0, y = 0, z = 0, px = 0, py = 0, pz = 0, wt = 0, g = 1;
-    Real E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
-    uint64_t pid = 0;
-    uint32_t ptag = 0;
-    uint32_t cnt = 0;
-    uint8_t heavy = 0;
-    Real nx = 0, ny = 0, nz = 0;
-    Real eph0 = 0, eph1 = 0;
-    int64_t k0 = 0, k1 = 0;
-    // state at the start of the emission loop (for a replay when cnt > 2)
-    Real g_init = 1, chi_init = 0;
-    RateOut<Real> ro_init{0, 0, 0};
-    int64_t N = 1;
-    if (active) {
-      x = S.x[i]; y = S.y[i]; z = S.z[i];
-      px = S.px[i]; py = S.py[i]; pz = S.pz[i];
-      get_fields<Real, FM>(S, A.f, i, x, y, z, E, B);
-      if (emit) { wt = S.w[i]; pid = S.id[i]; if (S.tag) ptag = S.tag[i]; }
-      if (MODE != MODE_EMIT) {
-        g = boris(px, py, pz, E, B, S.q, dt);
-        Real ig = dt / g;
-        x += px * ig; y += py * ig; z += pz * ig;
-      } else {
-        g = m_sqrt((Real)1 + px * px + py * py + pz * pz);
-      }
-      if (!(g < (Real)1e30)) { tl.status |= QED_STATUS_NONFINITE; }
-      else if (emit) {
-        Real chi = chi_lepton(px, py, pz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
-        Tally t0;
-        t0.clear();
-        RateOut<Real> ro = photon_rate(sR, sF, A.T, A.C, chi, g, t0);
-        Real wdt = ro.W * dt;
-        const Real wdt_max = sel<Real>(A.C.wdt_max, A.C.f_wdt_max);
-        if (wdt > wdt_max) {
-          Real nn = m_ceil(wdt / wdt_max);
-          if (nn > (Real)A.C.max_substeps) {
-            nn = (Real)A.C.max_substeps;
-            t0.status |= QED_STATUS_SUBSTEPS;
-          }
-          N = (int64_t)nn;
-        }
-        if (defer && N > HEAVY_SUBSTEPS) {
-          heavy = 1;  // the heavy pass redoes this particle from its stored state
-        } else {
-          tl.status |= t0.status;
-          tl.domain += t0.domain;
-          const Real dts = dt / (Real)N;
-          tl.substeps += N;
-          Real pm = m_sqrt(px * px + py * py + pz * pz);
-          if (pm > (Real)0) { Real ip = (Real)1 / pm; nx = px * ip; ny = py * ip; nz = pz * ip; }
-          g_init = g; chi_init = chi; ro_init = ro;
-          for (int64_t k = 0; k < N; ++k) {
-            U4 r = draw(A.C.seed, pid, step_, k, STREAM_EMIT);
-            if (!(ro.W * dts > unif<Real>(r.x))) continue;
-            XiOut<Real> xo = photon_xi(A.T.Y, A.T, ro.l, chi, ro.kmin, unif<Real>(r.y),
-                                       unif<Real>(~r.y), tl);
-            // eps_ph = xi gamma directly (gamma - gamma(1-xi) cancels for soft photons)
-            Real g2 = g * xo.omxi, eph = g * xo.xi;
-            if (g2 < (Real)1) { g2 = (Real)1; eph = g - (Real)1; }
-            if (cnt == 0) { eph0 = eph; k0 = k; }
-            else if (cnt == 1) { eph1 = eph; k1 = k; }
-            ++cnt;
-            Real pm2 = m_sqrt((g2 - (Real)1) * (g2 + (Real)1));
-            px = pm2 * nx; py = pm2 * ny; pz = pm2 * nz;
-            g = g2;
-            chi = chi_lepton(px, py, pz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
-            ro = photon_rate(sR, sF, A.T, A.C, chi, g, tl);
-          }
-          tl.events += cnt;
-        }
-      }
-      if (!heavy) {
-        if (MODE != MODE_EMIT) { S.x[i] = x; S.y[i] = y; S.z[i] = z; }
-        if (MODE != MODE_EMIT || cnt) { S.px[i] = px; S.py[i] = py; S.pz[i] = pz; }
-      }
+    const int64_t i = si ? g - n0 : g;
+    Real x = S.x[i], y = S.y[i], z = S.z[i];
+    Real px = S.px[i], py = S.py[i], pz = S.pz[i];
+    Real E[3], B[3];
+    get_fields<Real, FM>(S, A.f, i, x, y, z, E, B);
+    const Real gm = boris(px, py, pz, E, B, S.q, dt);
+    if (!(gm < (Real)1e30)) {  // non-finite state: left as it was
+      status |= QED_STATUS_NONFINITE;
+      continue;
     }
-    if (defer) A.heavy_flags[t * TILE + threadIdx.x] = heavy;
-    if (!emit) continue;
-
-    // ---- stable append: block scan + decoupled look-back
-    uint32_t excl = block_excl_scan(cnt, scan_sm);
-    uint32_t agg = scan_sm[32];
-    if (threadIdx.x < 32) {
-      uint32_t st = 0;
-      uint32_t pre = lookback_warp(A.o.scan, t, epoch, agg, st);
-      if (threadIdx.x == 0) {
-        s_meta[1] = pre;
-        if (st) tl.status |= st;
-        if (t == ntiles - 1) {  // last tile: publish the new photon count
-          int64_t nn = nph + (int64_t)pre + agg;
-          *A.ph.d_n = nn < A.ph.cap ? nn : A.ph.cap;
-        }
-      }
-    }
-    __syncthreads();
-    const int64_t base = nph + s_meta[1] + excl;
-    if (cnt) {
-      const Real Ec[3] = {E[0], E[1], E[2]}, Bc[3] = {B[0], B[1], B[2]};
-      if (cnt <= 2) {
-        for (uint32_t j = 0; j < cnt; ++j) {
-          Real eph = j == 0 ? eph0 : eph1;
-          int64_t kk = j == 0 ? k0 : k1;
-          int b = spec_bin(A.C, eph);
-          if (b >= 0) atomicAdd(&bt.hist[b], 1ull);
-          int64_t slot = base + j;
-          if (slot >= A.ph.cap) { tl.dropped += 1; tl.status |= QED_STATUS_CAPACITY; continue; }
-          U4 cid = draw(A.C.seed, pid, step_, kk, STREAM_PHOTON_ID);
-          write_child(A.ph, slot, x, y, z, eph * nx, eph * ny, eph * nz, wt,
-                      (uint64_t)cid.x | ((uint64_t)cid.y << 32), Ec, Bc, ptag);
-        }
-      } else {
-        // replay the emission loop (deterministic: same draws, same tables)
-        Tally dummy;
-        dummy.clear();
-        Real gg = g_init, chi = chi_init;
-        RateOut<Real> ro = ro_init;
-        const Real dts = dt / (Real)N;
-        uint32_t j = 0;
-        for (int64_t k = 0; k < N && j < cnt; ++k) {
-          U4 r = draw(A.C.seed, pid, step_, k, STREAM_EMIT);
-          if (!(ro.W * dts > unif<Real>(r.x))) continue;
-          XiOut<Real> xo = photon_xi(A.T.Y, A.T, ro.l, chi, ro.kmin, unif<Real>(r.y),
-                                     unif<Real>(~r.y), dummy);
-          Real g2 = gg * xo.omxi, eph = gg * xo.xi;
-          if (g2 < (Real)1) { g2 = (Real)1; eph = gg - (Real)1; }
-          int b = spec_bin(A.C, eph);
-          if (b >= 0) atomicAdd(&bt.hist[b], 1ull);
-          int64_t slot = base + j;
-          ++j;
-          if (slot >= A.ph.cap) {
-            tl.dropped += 1;
-            tl.status |= QED_STATUS_CAPACITY;
-          } else {
-            U4 cid = draw(A.C.seed, pid, step_, k, STREAM_PHOTON_ID);
-            write_child(A.ph, slot, x, y, z, eph * nx, eph * ny, eph * nz, wt,
-                        (uint64_t)cid.x | ((uint64_t)cid.y << 32), Ec, Bc, ptag);
-          }
-          Real pm2 = m_sqrt((g2 - (Real)1) * (g2 + (Real)1));
-          gg = g2;
-          chi = chi_lepton(pm2 * nx, pm2 * ny, pm2 * nz, gg, E[0], E[1], E[2], B[0], B[1], B[2],
-                           inv_aS);
-          ro = photon_rate(sR, sF, A.T, A.C, chi, gg, dummy);
-        }
-      }
-    }
+    const Real ig = dt / gm;
+    S.x[i] = x + px * ig; S.y[i] = y + py * ig; S.z[i] = z + pz * ig;
+    S.px[i] = px; S.py[i] = py; S.pz[i] = pz;
   }
-  tally_flush(&bt, tl);
-  __syncthreads();
-  block_tally_commit(&bt, A.o.cnt, 0);
-  launch_epilogue(A.o.scan, epoch);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) status |= __shfl_xor_sync(0xFFFFFFFFu, status, o);
+  if ((threadIdx.x & 31) == 0 && status) atomicOr(&A.o.cnt->status, status);
 }
 
 // ---------------------------------------------------------------------------
@@ -462,7 +309,7 @@ __global__ void __launch_bounds__(TILE, 3) k_lepton(LeptonArgs<Real> A) {
 // stored state, by the ordered passes that append photons.
 // ---------------------------------------------------------------------------
 template <class Real, int FM, int MODE>
-__global__ void __launch_bounds__(TILE) k_lepton_stream(LeptonArgs<Real> A) {
+__global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 4 : 2) k_lepton_stream(LeptonArgs<Real> A) {
   const int64_t step_ = A.d_step ? *A.d_step : A.step;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool kSmem = sizeof(Real) == 4;
@@ -485,8 +332,12 @@ __global__ void __launch_bounds__(TILE) k_lepton_stream(LeptonArgs<Real> A) {
   const int64_t nslots = (T0 + T1) * TILE;
   const Real inv_aS = sel<Real>(A.C.inv_aS, A.C.f_inv_aS);
   const Real dt = sel<Real>(A.C.dt, A.C.f_dt), wdt_max = sel<Real>(A.C.wdt_max, A.C.f_wdt_max);
+  const int lane = threadIdx.x & 31;
+  // this warp's current batch of staging records (warp-uniform)
+  uint32_t batch_base = 0, batch_used = STAGE_BATCH;
   Tally tl;
   tl.clear();
+  // nslots is a multiple of TILE: every lane of a warp runs the same iterations
   for (int64_t slot = blockIdx.x * (int64_t)TILE + threadIdx.x; slot < nslots;
        slot += (int64_t)gridDim.x * TILE) {
     const int64_t tile = slot / TILE;
@@ -494,12 +345,14 @@ __global__ void __launch_bounds__(TILE) k_lepton_stream(LeptonArgs<Real> A) {
     const Sp<Real> &S = A.sp[si];
     const int64_t i = (tile - (si ? T0 : 0)) * TILE + (slot % TILE);
     uint8_t flag = 0;
+    Real x = 0, y = 0, z = 0, px = 0, py = 0, pz = 0;
+    Real E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
+    uint64_t pid = 0;
     if (i < (si ? n1 : n0)) {
-      Real x = S.x[i], y = S.y[i], z = S.z[i];
-      Real px = S.px[i], py = S.py[i], pz = S.pz[i];
-      Real E[3], B[3];
+      x = S.x[i]; y = S.y[i]; z = S.z[i];
+      px = S.px[i]; py = S.py[i]; pz = S.pz[i];
       get_fields<Real, FM>(S, A.f, i, x, y, z, E, B);
-      const uint64_t pid = S.id[i];
+      pid = S.id[i];
       Real g;
       if (MODE != MODE_EMIT) {
         g = boris(px, py, pz, E, B, S.q, dt);
@@ -537,6 +390,431 @@ __global__ void __launch_bounds__(TILE) k_lepton_stream(LeptonArgs<Real> A) {
       }
     }
     A.heavy_flags[slot] = flag;
+    // stage the pushed state of the flagged particles (warp-collective)
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, flag != 0);
+    if (m) {
+      const uint32_t cm = __popc(m);
+      if (batch_used + cm > STAGE_BATCH) {
+        uint32_t nb = 0;
+        if (lane == 0) nb = atomicAdd(A.stage_n, STAGE_BATCH);
+        batch_base = __shfl_sync(0xFFFFFFFFu, nb, 0);
+        batch_used = 0;
+      }
+      if (flag) {
+        const uint64_t pos = (uint64_t)batch_base + batch_used + __popc(m & ((1u << lane) - 1u));
+        int32_t sidx = -1;
+        if (pos < (uint64_t)A.stage_cap) {
+          sidx = (int32_t)pos;
+          Stage<Real> r;
+          r.p[0] = px; r.p[1] = py; r.p[2] = pz;
+          r.e[0] = E[0]; r.e[1] = E[1]; r.e[2] = E[2];
+          r.b[0] = B[0]; r.b[1] = B[1]; r.b[2] = B[2];
+          r.id_lo = (uint32_t)pid; r.id_hi = (uint32_t)(pid >> 32);
+          r.w = S.w[i];
+          r.x[0] = x; r.x[1] = y; r.x[2] = z;
+          r.slot = (uint32_t)slot;
+          const uint4 *src = reinterpret_cast<const uint4 *>(&r);
+          uint4 *dst = reinterpret_cast<uint4 *>(A.stage + pos);
+#pragma unroll
+          for (int q = 0; q < (int)(sizeof(Stage<Real>) / 16); ++q) dst[q] = src[q];
+          if (S.tag) A.stage_tag[pos] = S.tag[i];
+          // the later passes read the staged copy; the pushed position and
+          // momentum go to the arrays now, with the rest of the tile
+          if (MODE != MODE_EMIT) {
+            S.x[i] = x; S.y[i] = y; S.z[i] = z;
+            S.px[i] = px; S.py[i] = py; S.pz[i] = pz;
+          }
+        }
+        A.stage_idx[slot] = sidx;
+      }
+      batch_used += cm;
+    }
+  }
+  tally_flush(&bt, tl);
+  __syncthreads();
+  block_tally_commit(&bt, A.o.cnt, 0);
+}
+
+// ---------------------------------------------------------------------------
+// Sub-step passes over the particles that need N > 1 generator sub-steps
+// (classes 2-5 of the class list).  The work is split in two so that no
+// expensive emission chain ever waits on another:
+//   counting pass: redo the particle from its stored state (gather, push,
+//     chi, rate, N) and run its Method I chain -- per sub-step one Philox
+//     draw, on an event xi from the inverse table and the recoil -- writing
+//     only the number of photons, the final gamma and the first REC
+//     emission records (photon energy, sub-step index).  Particles are
+//     independent here: no scan, no ordering.
+//   writing pass: an exclusive scan of the counts (decoupled look-back over
+//     32-entry warp tiles; a tile's aggregate is known as soon as it has read
+//     its counts, so no tile waits on another's emission work) gives every
+//     particle its photon slots; the particle is pushed again (the same
+//     arithmetic), its photons written from the records -- or, for a particle
+//     with more than REC photons, from a replay of its chain -- and its final
+//     state stored.
+// Within a warp the chain is split into a scan phase (each lane draws until
+// its next event) and an emission phase that the lanes with an event execute
+// together, so lanes of different event counts stay converged.
+// ---------------------------------------------------------------------------
+constexpr int REC = SUB_REC;
+
+// A class-list entry's particle after the push.  Entry e >= 0 is staging
+// record e (written by the streaming pass, which has also stored the pushed
+// position and momentum); e < 0 is slot -e-1, a particle the staging area had
+// no room for, gathered and pushed again from its unchanged stored state.
+template <class Real> struct Entry {
+  Real x, y, z, px, py, pz, g, w;
+  Real E[3], B[3];
+  uint64_t id;
+  uint32_t tag;
+  int64_t i;     // index in species si
+  int si;
+  bool staged;
+};
+
+template <class Real, int FM, int MODE>
+__device__ __forceinline__ void load_entry(const LeptonArgs<Real> &A, int32_t e, int64_t T0,
+                                           Real dt, Entry<Real> &P) {
+  int64_t slot;
+  P.staged = e >= 0;
+  if (P.staged) {
+    Stage<Real> r;
+    const uint4 *src = reinterpret_cast<const uint4 *>(A.stage + e);
+    uint4 *dst = reinterpret_cast<uint4 *>(&r);
+#pragma unroll
+    for (int q = 0; q < (int)(sizeof(Stage<Real>) / 16); ++q) dst[q] = __ldcs(src + q);
+    P.px = r.p[0]; P.py = r.p[1]; P.pz = r.p[2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { P.E[c] = r.e[c]; P.B[c] = r.b[c]; }
+    P.id = (uint64_t)r.id_lo | ((uint64_t)r.id_hi << 32);
+    P.w = r.w;
+    P.x = r.x[0]; P.y = r.x[1]; P.z = r.x[2];
+    slot = r.slot;
+  } else {
+    slot = -(int64_t)e - 1;
+  }
+  const int64_t tile = slot / TILE;
+  P.si = tile < T0 ? 0 : 1;
+  P.i = (tile - (P.si ? T0 : 0)) * TILE + (slot % TILE);
+  const Sp<Real> &S = A.sp[P.si];
+  if (P.staged) {
+    P.tag = S.tag ? A.stage_tag[e] : 0u;
+    P.g = m_sqrt((Real)1 + P.px * P.px + P.py * P.py + P.pz * P.pz);
+    return;
+  }
+  const int64_t i = P.i;
+  P.x = S.x[i]; P.y = S.y[i]; P.z = S.z[i];
+  P.px = S.px[i]; P.py = S.py[i]; P.pz = S.pz[i];
+  get_fields<Real, FM>(S, A.f, i, P.x, P.y, P.z, P.E, P.B);
+  P.id = S.id[i];
+  P.w = S.w[i];
+  P.tag = S.tag ? S.tag[i] : 0u;
+  if (MODE != MODE_EMIT) {
+    P.g = boris(P.px, P.py, P.pz, P.E, P.B, S.q, dt);
+    Real ig = dt / P.g;
+    P.x += P.px * ig; P.y += P.py * ig; P.z += P.pz * ig;
+  } else {
+    P.g = m_sqrt((Real)1 + P.px * P.px + P.py * P.py + P.pz * P.pz);
+  }
+}
+
+// Final state of an entry after its emissions (final gamma g, unit direction
+// n): a staged particle already has its pushed position stored.
+template <class Real, int MODE>
+__device__ __forceinline__ void store_entry(const LeptonArgs<Real> &A, const Entry<Real> &P,
+                                            Real g, Real nx, Real ny, Real nz) {
+  const Sp<Real> &S = A.sp[P.si];
+  const int64_t i = P.i;
+  const Real pm = m_sqrt((g - (Real)1) * (g + (Real)1));
+  if (MODE != MODE_EMIT && !P.staged) { S.x[i] = P.x; S.y[i] = P.y; S.z[i] = P.z; }
+  S.px[i] = pm * nx; S.py[i] = pm * ny; S.pz[i] = pm * nz;
+}
+
+template <class Real>
+__device__ __forceinline__ void unit_dir(const Entry<Real> &P, Real &nx, Real &ny, Real &nz) {
+  nx = ny = nz = 0;
+  const Real pm = m_sqrt(P.px * P.px + P.py * P.py + P.pz * P.pz);
+  if (pm > (Real)0) { Real ip = (Real)1 / pm; nx = P.px * ip; ny = P.py * ip; nz = P.pz * ip; }
+}
+
+// Sub-step count of a particle (Method I: N = max(1, ceil(W Dt / wdt_max))).
+template <class Real>
+__device__ __forceinline__ int64_t substep_count(const Consts &C, Real W, Real dt, Real wdt_max,
+                                                 uint32_t &status) {
+  const Real wdt = W * dt;
+  if (!(wdt > wdt_max)) return 1;
+  Real nn = m_ceil(wdt / wdt_max);
+  if (nn > (Real)C.max_substeps) {
+    nn = (Real)C.max_substeps;
+    status |= QED_STATUS_SUBSTEPS;
+  }
+  return (int64_t)nn;
+}
+
+template <class Real, int FM, int MODE>
+__global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 3 : 2) k_substep_count(LeptonArgs<Real> A) {
+  const int64_t step_ = A.d_step ? *A.d_step : A.step;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr bool kSmem = sizeof(Real) == 4;
+  Real *sR = kSmem ? reinterpret_cast<Real *>(smem_raw) : const_cast<Real *>(A.T.R);
+  Real *sF = kSmem ? sR + A.T.gl.n : const_cast<Real *>(A.T.F);
+  __shared__ long long s_meta[4];
+  __shared__ BlockTally bt;
+  if (kSmem) {
+    load_tables_smem(sR, A.T.R, A.T.gl.n);
+    load_tables_smem(sF, A.T.F, A.T.gl.n * A.T.gy.n);
+  }
+  block_tally_init(&bt);
+  if (threadIdx.x == 0) {
+    s_meta[0] = *(volatile int64_t *)A.sp[0].d_n;
+    s_meta[1] = A.cls_off[1];
+    s_meta[2] = A.cls_off[NCLS];
+  }
+  __syncthreads();
+  const int64_t T0 = (s_meta[0] + TILE - 1) / TILE;
+  const int64_t begin = s_meta[1], nh = s_meta[2] - s_meta[1];
+  const int64_t nwt = (nh + 31) / 32;
+  const int lane = threadIdx.x & 31;
+  const Real inv_aS = sel<Real>(A.C.inv_aS, A.C.f_inv_aS);
+  const Real dt = sel<Real>(A.C.dt, A.C.f_dt);
+  const Real wdt_max = sel<Real>(A.C.wdt_max, A.C.f_wdt_max);
+  const int64_t rc = A.rec_cap;
+  Tally tl;
+  tl.clear();
+  // warp tiles of 32 entries, strided over the grid's warps; the heaviest
+  // classes sit at the end of the list and are taken first
+  const int64_t nwarps = (int64_t)gridDim.x * (TILE / 32);
+  for (int64_t f = blockIdx.x * (int64_t)(TILE / 32) + (threadIdx.x >> 5); f < nwt; f += nwarps) {
+    const int64_t h = (nwt - 1 - f) * 32 + lane;
+    const bool active = h < nh;
+    Entry<Real> P;
+    P.x = P.y = P.z = P.px = P.py = (Real)0;
+    P.pz = P.g = (Real)1;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { P.E[c] = (Real)0; P.B[c] = (Real)0; }
+    P.id = 0;
+    if (active) load_entry<Real, FM, MODE>(A, A.heavy_list[begin + h], T0, dt, P);
+    Real px = P.px, py = P.py, pz = P.pz, g = P.g;
+    const Real *E = P.E, *B = P.B;
+    const uint64_t pid = P.id;
+    Real chi = chi_lepton(px, py, pz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
+    Tally t0;  // an idle lane tallies nothing
+    t0.clear();
+    RateOut<Real> ro = photon_rate(sR, sF, A.T, A.C, chi, g, t0);
+    int64_t N = substep_count(A.C, ro.W, dt, wdt_max, t0.status);
+    if (active) {
+      tl.status |= t0.status;
+      tl.domain += t0.domain;
+      tl.substeps += N;
+    } else {
+      N = 0;
+    }
+    const Real dts = dt / (Real)(N > 0 ? N : 1);
+    Real nx, ny, nz;
+    unit_dir(P, nx, ny, nz);
+    uint32_t cnt = 0;
+    int64_t k = 0;
+    for (;;) {
+      bool ev = false;  // scan: draw until this lane's next event
+      uint32_t wy = 0;
+      while (k < N) {
+        U4 r = draw(A.C.seed, pid, step_, k, STREAM_EMIT);
+        if (ro.W * dts > unif<Real>(r.x)) { ev = true; wy = r.y; break; }
+        ++k;
+      }
+      if (!__any_sync(0xFFFFFFFFu, ev)) break;
+      if (ev) {  // emission, by every lane with an event
+        XiOut<Real> xo = photon_xi(A.T.Y, A.T, ro.l, chi, ro.kmin, unif<Real>(wy), unif<Real>(~wy), tl);
+        Real g2 = g * xo.omxi, eph = g * xo.xi;
+        if (g2 < (Real)1) { g2 = (Real)1; eph = g - (Real)1; }
+        if (cnt < REC && h < rc) {
+          A.rec_e[cnt * rc + h] = eph;
+          A.rec_k[cnt * rc + h] = (uint32_t)k;
+        }
+        ++cnt;
+        int b = spec_bin(A.C, eph);
+        if (b >= 0) atomicAdd(&bt.hist[b], 1ull);
+        Real pm2 = m_sqrt((g2 - (Real)1) * (g2 + (Real)1));
+        px = pm2 * nx; py = pm2 * ny; pz = pm2 * nz;
+        g = g2;
+        chi = chi_lepton(px, py, pz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
+        ro = photon_rate(sR, sF, A.T, A.C, chi, g, tl);
+        ++k;
+      }
+    }
+    if (active) {
+      tl.events += cnt;
+      A.sub_cnt[h] = cnt;
+      if (h < rc) A.sub_gf[h] = g;
+    }
+  }
+  tally_flush(&bt, tl);
+  __syncthreads();
+  block_tally_commit(&bt, A.o.cnt, 0);
+}
+
+// Exclusive scan, in place, of the sub-step entries' photon counts (single
+// pass, decoupled look-back over 4096-entry tiles).  The total and the photon
+// count at launch go to sub_meta[0] and sub_meta[1]; the last tile publishes
+// the new photon count.
+struct SubScanArgs {
+  uint32_t *cnt;
+  const int64_t *cls_off;
+  int64_t *sub_meta;
+  int64_t *ph_n;
+  int64_t ph_cap;
+  Out o;
+};
+constexpr int SCAN_ITEMS = 16;
+
+__global__ void __launch_bounds__(TILE) k_sub_scan(SubScanArgs A) {
+  __shared__ uint32_t scan_sm[33];
+  __shared__ long long s_meta[6];
+  if (threadIdx.x == 0) {
+    s_meta[2] = A.cls_off[NCLS] - A.cls_off[1];
+    s_meta[3] = *(volatile int64_t *)A.ph_n;
+    s_meta[4] = (long long)A.o.scan.sync[2];
+  }
+  __syncthreads();
+  const int64_t nh = s_meta[2], nph = s_meta[3];
+  const uint32_t epoch = (uint32_t)s_meta[4];
+  const int64_t per_tile = (int64_t)TILE * SCAN_ITEMS;
+  const int64_t ntiles = (nh + per_tile - 1) / per_tile;
+  uint32_t status = 0;
+  if (ntiles == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+    A.sub_meta[0] = 0;
+    A.sub_meta[1] = nph;
+  }
+  for (;;) {
+    if (threadIdx.x == 0) s_meta[0] = (long long)atomicAdd(&A.o.scan.sync[0], 1u);
+    __syncthreads();
+    const int64_t t = s_meta[0];
+    __syncthreads();
+    if (t >= ntiles) break;
+    const int64_t first = t * per_tile + (int64_t)threadIdx.x * SCAN_ITEMS;
+    uint32_t v[SCAN_ITEMS];
+    uint32_t sum = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+      v[j] = first + j < nh ? A.cnt[first + j] : 0u;
+      sum += v[j];
+    }
+    const uint32_t excl = block_excl_scan(sum, scan_sm);
+    const uint32_t agg = scan_sm[32];
+    if (threadIdx.x < 32) {
+      const uint32_t pre = lookback_warp(A.o.scan, t, epoch, agg, status);
+      if (threadIdx.x == 0) {
+        s_meta[1] = pre;
+        if (t == ntiles - 1) {
+          const int64_t tot = (int64_t)pre + agg;
+          A.sub_meta[0] = tot;
+          A.sub_meta[1] = nph;
+          *A.ph_n = nph + tot < A.ph_cap ? nph + tot : A.ph_cap;
+        }
+      }
+    }
+    __syncthreads();
+    uint32_t run = (uint32_t)s_meta[1] + excl;
+#pragma unroll
+    for (int j = 0; j < SCAN_ITEMS; ++j) {
+      if (first + j < nh) A.cnt[first + j] = run;
+      run += v[j];
+    }
+  }
+  if (threadIdx.x == 0 && status) atomicOr(&A.o.cnt->status, status);
+  launch_epilogue(A.o.scan, epoch);
+}
+
+template <class Real, int FM, int MODE>
+__global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 3 : 2) k_substep_write(LeptonArgs<Real> A) {
+  const int64_t step_ = A.d_step ? *A.d_step : A.step;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr bool kSmem = sizeof(Real) == 4;
+  Real *sR = kSmem ? reinterpret_cast<Real *>(smem_raw) : const_cast<Real *>(A.T.R);
+  Real *sF = kSmem ? sR + A.T.gl.n : const_cast<Real *>(A.T.F);
+  __shared__ long long s_meta[5];
+  __shared__ BlockTally bt;
+  if (kSmem) {  // for replays
+    load_tables_smem(sR, A.T.R, A.T.gl.n);
+    load_tables_smem(sF, A.T.F, A.T.gl.n * A.T.gy.n);
+  }
+  block_tally_init(&bt);
+  if (threadIdx.x == 0) {
+    s_meta[0] = *(volatile int64_t *)A.sp[0].d_n;
+    s_meta[1] = A.cls_off[1];
+    s_meta[2] = A.cls_off[NCLS];
+    s_meta[3] = A.sub_meta[0];  // photons of all entries
+    s_meta[4] = A.sub_meta[1];  // photon count before them
+  }
+  __syncthreads();
+  const int64_t T0 = (s_meta[0] + TILE - 1) / TILE;
+  const int64_t begin = s_meta[1], nh = s_meta[2] - s_meta[1];
+  const uint32_t total = (uint32_t)s_meta[3];
+  const int64_t nph = s_meta[4];
+  const Real inv_aS = sel<Real>(A.C.inv_aS, A.C.f_inv_aS);
+  const Real dt = sel<Real>(A.C.dt, A.C.f_dt);
+  const Real wdt_max = sel<Real>(A.C.wdt_max, A.C.f_wdt_max);
+  const int64_t rc = A.rec_cap;
+  Tally tl;
+  tl.clear();
+  for (int64_t h = blockIdx.x * (int64_t)TILE + threadIdx.x; h < nh; h += (int64_t)gridDim.x * TILE) {
+    // sub_cnt holds the exclusive prefix of the counts now
+    const uint32_t off = A.sub_cnt[h];
+    const uint32_t cnt = (h + 1 < nh ? A.sub_cnt[h + 1] : total) - off;
+    const int32_t e = A.heavy_list[begin + h];
+    if (cnt == 0 && e >= 0) continue;  // staged, no photon: the streaming pass stored it
+    const int64_t out0 = nph + (int64_t)off;
+    Entry<Real> P;
+    load_entry<Real, FM, MODE>(A, e, T0, dt, P);
+    Real nx, ny, nz;
+    unit_dir(P, nx, ny, nz);
+    Real g = P.g;
+    if (cnt == 0) {
+      store_entry<Real, MODE>(A, P, g, nx, ny, nz);
+      continue;
+    }
+    auto put = [&](uint32_t j, Real eph, int64_t kk) {
+      const int64_t out = out0 + j;
+      if (out >= A.ph.cap) {
+        tl.dropped += 1;
+        tl.status |= QED_STATUS_CAPACITY;
+        return;
+      }
+      U4 cid = draw(A.C.seed, P.id, step_, kk, STREAM_PHOTON_ID);
+      write_child(A.ph, out, P.x, P.y, P.z, eph * nx, eph * ny, eph * nz, P.w,
+                  (uint64_t)cid.x | ((uint64_t)cid.y << 32), P.E, P.B, P.tag);
+    };
+    if (cnt <= REC && h < rc) {
+      for (uint32_t j = 0; j < cnt; ++j) put(j, A.rec_e[j * rc + h], (int64_t)A.rec_k[j * rc + h]);
+      g = A.sub_gf[h];
+    } else {
+      // more photons than records: replay the chain (same draws, same tables)
+      Tally dummy;
+      dummy.clear();
+      const Real *E = P.E, *B = P.B;
+      Real chi = chi_lepton(P.px, P.py, P.pz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
+      RateOut<Real> ro = photon_rate(sR, sF, A.T, A.C, chi, g, dummy);
+      const int64_t N = substep_count(A.C, ro.W, dt, wdt_max, dummy.status);
+      const Real dts = dt / (Real)N;
+      uint32_t j = 0;
+      for (int64_t kk = 0; kk < N && j < cnt; ++kk) {
+        U4 r = draw(A.C.seed, P.id, step_, kk, STREAM_EMIT);
+        if (!(ro.W * dts > unif<Real>(r.x))) continue;
+        XiOut<Real> xo = photon_xi(A.T.Y, A.T, ro.l, chi, ro.kmin, unif<Real>(r.y), unif<Real>(~r.y), dummy);
+        Real g2 = g * xo.omxi, eph = g * xo.xi;
+        if (g2 < (Real)1) { g2 = (Real)1; eph = g - (Real)1; }
+        put(j++, eph, kk);
+        Real pm2 = m_sqrt((g2 - (Real)1) * (g2 + (Real)1));
+        g = g2;
+        chi = chi_lepton(pm2 * nx, pm2 * ny, pm2 * nz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
+        ro = photon_rate(sR, sF, A.T, A.C, chi, g, dummy);
+      }
+      if (j != cnt) {  // the replay disagreed with the count: zero-energy photons fill the slots
+        tl.status |= QED_STATUS_REPLAY;
+        for (; j < cnt; ++j) put(j, (Real)0, 0);
+      }
+    }
+    store_entry<Real, MODE>(A, P, g, nx, ny, nz);
   }
   tally_flush(&bt, tl);
   __syncthreads();
@@ -611,6 +889,200 @@ __global__ void __launch_bounds__(TILE) k_heavy_list(HeavyListArgs A) {
 }
 
 // ---------------------------------------------------------------------------
+// Class list of the streaming pass's flagged leptons: one ordered list,
+// class-major (all class-1 slots in slot order, then class 2, ..., class 5),
+// built by a count, a scan and a scatter pass -- no CTA waits on another.
+// off[c - 1] is the first list position of class c and off[NCLS] the length.
+// Flags are read 8 per thread (one 8-byte load), 2048 per chunk; a chunk's
+// per-class counts (<= 2048 each) are packed 12 bits per class in a uint64.
+// ---------------------------------------------------------------------------
+constexpr int CLS_ITEMS = 8;
+constexpr int CLS_CHUNK = TILE * CLS_ITEMS;
+static_assert(CLS_CHUNK == CLS_CHUNK_FLAGS, "class-list chunk size");
+constexpr int CLS_SCAN_THREADS = 1024;
+constexpr int CLS_SCAN_PER_THREAD = 8;  // chunks per thread per round of the scan
+
+struct ClassListArgs {
+  const uint8_t *flags;
+  const int64_t *n0, *n1;  // species counts (size the streaming pass's slot range)
+  int *list;
+  unsigned long long *chunk_cnt;  // [chunks] packed per-class counts
+  uint32_t *chunk_off;            // [chunks][NCLS] first list position per class
+  int64_t *off;                   // [NCLS + 1]
+  const int32_t *stage_idx;       // [slot] staging record of a flagged slot (-1: none)
+  unsigned int *stage_n;          // staging counter, reset by the scan for the next step
+};
+
+__device__ __forceinline__ int64_t cls_nslots(const ClassListArgs &A) {
+  const int64_t n0 = *(volatile const int64_t *)A.n0;
+  const int64_t n1 = A.n1 ? *(volatile const int64_t *)A.n1 : 0;
+  return ((n0 + TILE - 1) / TILE + (n1 + TILE - 1) / TILE) * TILE;
+}
+
+// This thread's 8 flags of chunk c and their packed per-class counts.  The
+// slot range is a multiple of TILE, so a group of 8 is all in or all out.
+__device__ __forceinline__ unsigned long long cls_load(const ClassListArgs &A, int64_t c,
+                                                       int64_t nslots, uint2 &raw) {
+  const int64_t first = c * CLS_CHUNK + (int64_t)threadIdx.x * CLS_ITEMS;
+  raw = make_uint2(0u, 0u);
+  if (first < nslots) raw = *reinterpret_cast<const uint2 *>(A.flags + first);
+  const uint8_t *fl = reinterpret_cast<const uint8_t *>(&raw);
+  unsigned long long packed = 0;
+#pragma unroll
+  for (int j = 0; j < CLS_ITEMS; ++j)
+    if (fl[j] >= 1 && fl[j] <= NCLS) packed += 1ull << (12 * (fl[j] - 1));
+  return packed;
+}
+
+// Block-wide exclusive scan of a uint64 per thread; sm needs 33 words and
+// receives the block total in sm[32].
+__device__ __forceinline__ unsigned long long block_excl_scan64(unsigned long long v,
+                                                               unsigned long long *sm) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned long long incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) sm[wid] = incl;
+  __syncthreads();
+  if (wid == 0) {
+    unsigned long long w = lane < nw ? sm[lane] : 0ull, wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long u = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+      if (lane >= o) wi += u;
+    }
+    if (lane < nw) sm[lane] = wi - w;
+    if (lane == nw - 1) sm[32] = wi;
+  }
+  __syncthreads();
+  const unsigned long long r = sm[wid] + incl - v;
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ uint32_t cls_field(unsigned long long p, int c) {
+  return (uint32_t)(p >> (12 * c)) & 0xFFFu;
+}
+
+__global__ void __launch_bounds__(TILE) k_cls_count(ClassListArgs A) {
+  __shared__ unsigned long long sm[33];
+  const int64_t nslots = cls_nslots(A);
+  const int64_t nchunks = (nslots + CLS_CHUNK - 1) / CLS_CHUNK;
+  for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    uint2 raw;
+    const unsigned long long p = cls_load(A, c, nslots, raw);
+    block_excl_scan64(p, sm);
+    if (threadIdx.x == 0) A.chunk_cnt[c] = sm[32];
+  }
+}
+
+// One CTA: class totals, class starts, and every chunk's per-class offset.
+__global__ void __launch_bounds__(CLS_SCAN_THREADS) k_cls_scan(ClassListArgs A) {
+  __shared__ unsigned long long tot[NCLS];
+  __shared__ unsigned long long sm[33];
+  __shared__ int64_t base[NCLS];
+  const int64_t nslots = cls_nslots(A);
+  const int64_t nchunks = (nslots + CLS_CHUNK - 1) / CLS_CHUNK;
+  if (threadIdx.x < NCLS) tot[threadIdx.x] = 0;
+  if (threadIdx.x == 0) *A.stage_n = 0u;  // the streaming pass of this step is done with it
+  __syncthreads();
+  unsigned long long mine[NCLS] = {0, 0, 0, 0, 0};
+  for (int64_t c = threadIdx.x; c < nchunks; c += blockDim.x) {
+    const unsigned long long p = A.chunk_cnt[c];
+#pragma unroll
+    for (int k = 0; k < NCLS; ++k) mine[k] += cls_field(p, k);
+  }
+#pragma unroll
+  for (int k = 0; k < NCLS; ++k) {
+    unsigned long long v = mine[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&tot[k], v);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t b = 0;
+    for (int k = 0; k < NCLS; ++k) {
+      base[k] = b;
+      A.off[k] = b;
+      b += (int64_t)tot[k];
+    }
+    A.off[NCLS] = b;
+  }
+  __syncthreads();
+  // per-class running prefix over chunks; each round a thread takes
+  // CLS_SCAN_PER_THREAD consecutive chunks.  A round's prefixes stay below
+  // 2^25 per class (2048 * 8 * 1024), so two classes share a packed scan.
+  int64_t carry[NCLS];
+#pragma unroll
+  for (int k = 0; k < NCLS; ++k) carry[k] = base[k];
+  const int64_t per_round = (int64_t)blockDim.x * CLS_SCAN_PER_THREAD;
+  for (int64_t r0 = 0; r0 < nchunks; r0 += per_round) {
+    const int64_t c0 = r0 + (int64_t)threadIdx.x * CLS_SCAN_PER_THREAD;
+    uint32_t t[NCLS + 1] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < CLS_SCAN_PER_THREAD; ++j) {
+      const int64_t c = c0 + j;
+      if (c < nchunks) {
+        const unsigned long long p = A.chunk_cnt[c];
+#pragma unroll
+        for (int k = 0; k < NCLS; ++k) t[k] += cls_field(p, k);
+      }
+    }
+    uint32_t run[NCLS + 1], rtot[NCLS + 1];
+#pragma unroll
+    for (int q = 0; q < (NCLS + 1) / 2; ++q) {
+      const unsigned long long v = (unsigned long long)t[2 * q] | ((unsigned long long)t[2 * q + 1] << 32);
+      const unsigned long long e = block_excl_scan64(v, sm), tt = sm[32];
+      run[2 * q] = (uint32_t)e;
+      run[2 * q + 1] = (uint32_t)(e >> 32);
+      rtot[2 * q] = (uint32_t)tt;
+      rtot[2 * q + 1] = (uint32_t)(tt >> 32);
+    }
+#pragma unroll
+    for (int j = 0; j < CLS_SCAN_PER_THREAD; ++j) {
+      const int64_t c = c0 + j;
+      if (c < nchunks) {
+        const unsigned long long p = A.chunk_cnt[c];
+#pragma unroll
+        for (int k = 0; k < NCLS; ++k) {
+          A.chunk_off[c * NCLS + k] = (uint32_t)(carry[k] + run[k]);
+          run[k] += cls_field(p, k);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NCLS; ++k) carry[k] += (int64_t)rtot[k];
+  }
+}
+
+__global__ void __launch_bounds__(TILE) k_cls_scatter(ClassListArgs A) {
+  __shared__ unsigned long long sm[33];
+  const int64_t nslots = cls_nslots(A);
+  const int64_t nchunks = (nslots + CLS_CHUNK - 1) / CLS_CHUNK;
+  for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    uint2 raw;
+    const unsigned long long p = cls_load(A, c, nslots, raw);
+    unsigned long long ex = block_excl_scan64(p, sm);
+    if (!p) continue;
+    const uint8_t *fl = reinterpret_cast<const uint8_t *>(&raw);
+    const int64_t first = c * CLS_CHUNK + (int64_t)threadIdx.x * CLS_ITEMS;
+#pragma unroll
+    for (int j = 0; j < CLS_ITEMS; ++j) {
+      const int k = (int)fl[j] - 1;
+      if (k < 0 || k >= NCLS) continue;
+      // list entry: the staging record, or -(slot + 1) for an unstaged slot
+      const int32_t sidx = A.stage_idx[first + j];
+      A.list[A.chunk_off[c * NCLS + k] + cls_field(ex, k)] = sidx >= 0 ? sidx : -(int32_t)(first + j) - 1;
+      ex += 1ull << (12 * k);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Single-event pass: particles whose one sub-step drew an event (class 1 of
 // the streaming pass) each emit exactly one photon, so the photon of list
 // entry h goes to slot (count at launch) + h -- no scan is needed.  The
@@ -639,7 +1111,7 @@ __global__ void __launch_bounds__(TILE) k_lepton_emit1(LeptonArgs<Real> A) {
   block_tally_init(&bt);
   if (threadIdx.x == 0) {
     s_meta[0] = *(volatile int64_t *)A.sp[0].d_n;
-    s_meta[1] = *(volatile const int64_t *)A.heavy_n;
+    s_meta[1] = A.cls_off[1];  // class 1 occupies [0, cls_off[1])
     s_meta[2] = *(volatile int64_t *)A.ph.d_n;
     s_meta[3] = (long long)A.o.scan.sync[2];
   }
@@ -656,33 +1128,25 @@ __global__ void __launch_bounds__(TILE) k_lepton_emit1(LeptonArgs<Real> A) {
        hb += (int64_t)gridDim.x * TILE) {
     const int64_t h = hb + (threadIdx.x & 31);
     const bool active = h < nl;
-    const int64_t slot = active ? A.heavy_list[h] : 0;
-    const int64_t tile = slot / TILE;
-    const int si = tile < T0 ? 0 : 1;
-    const Sp<Real> &S = A.sp[si];
-    const int64_t i = (tile - (si ? T0 : 0)) * TILE + (slot % TILE);
-    Real x = 0, y = 0, z = 0, px = 0, py = 0, pz = 1, wt = 0;
-    Real E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
-    uint64_t pid = 0;
-    uint32_t ptag = 0;
-    if (active) {
-      x = S.x[i]; y = S.y[i]; z = S.z[i];
-      px = S.px[i]; py = S.py[i]; pz = S.pz[i];
-      get_fields<Real, FM>(S, A.f, i, x, y, z, E, B);
-      pid = S.id[i];
-      wt = S.w[i];
-      if (S.tag) ptag = S.tag[i];
-    }
-    Real g;
-    if (MODE != MODE_EMIT) {
-      g = boris(px, py, pz, E, B, S.q, dt);
-      Real ig = dt / g;
-      x += px * ig; y += py * ig; z += pz * ig;
-    } else {
-      g = m_sqrt((Real)1 + px * px + py * py + pz * pz);
-    }
+    Entry<Real> P;
+    P.x = P.y = P.z = P.px = P.py = P.w = (Real)0;
+    P.pz = P.g = (Real)1;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { P.E[c] = (Real)0; P.B[c] = (Real)0; }
+    P.id = 0;
+    P.tag = 0;
+    if (active) load_entry<Real, FM, MODE>(A, A.heavy_list[h], T0, dt, P);
+    const Real px = P.px, py = P.py, pz = P.pz, g = P.g;
+    const Real *E = P.E, *B = P.B;
+    const uint64_t pid = P.id;
     Real chi = chi_lepton(px, py, pz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
-    RateOut<Real> ro = photon_rate(sR, sF, A.T, A.C, chi, g, tl);
+    Tally t0;  // an idle lane tallies nothing
+    t0.clear();
+    RateOut<Real> ro = photon_rate(sR, sF, A.T, A.C, chi, g, t0);
+    if (active) {
+      tl.status |= t0.status;
+      tl.domain += t0.domain;
+    }
     U4 r = draw(A.C.seed, pid, step_, 0, STREAM_EMIT);
     const Real kap = photon_kappa(ro.kmin, unif<Real>(r.y), unif<Real>(~r.y));
     Real Y = 0;
@@ -700,12 +1164,9 @@ __global__ void __launch_bounds__(TILE) k_lepton_emit1(LeptonArgs<Real> A) {
     XiOut<Real> xo = xi_from_lndelta(chi, Y);
     Real g2 = g * xo.omxi, eph = g * xo.xi;
     if (g2 < (Real)1) { g2 = (Real)1; eph = g - (Real)1; }
-    Real pm = m_sqrt(px * px + py * py + pz * pz);
-    Real ip = pm > (Real)0 ? (Real)1 / pm : (Real)0;
-    Real nx = px * ip, ny = py * ip, nz = pz * ip;
-    Real pm2 = m_sqrt((g2 - (Real)1) * (g2 + (Real)1));
-    if (MODE != MODE_EMIT) { S.x[i] = x; S.y[i] = y; S.z[i] = z; }
-    S.px[i] = pm2 * nx; S.py[i] = pm2 * ny; S.pz[i] = pm2 * nz;
+    Real nx, ny, nz;
+    unit_dir(P, nx, ny, nz);
+    store_entry<Real, MODE>(A, P, g2, nx, ny, nz);
     tl.events += 1;
     tl.substeps += 1;
     int b = spec_bin(A.C, eph);
@@ -713,8 +1174,8 @@ __global__ void __launch_bounds__(TILE) k_lepton_emit1(LeptonArgs<Real> A) {
     const int64_t out = base + h;
     if (out < A.ph.cap) {
       U4 cid = draw(A.C.seed, pid, step_, 0, STREAM_PHOTON_ID);
-      write_child(A.ph, out, x, y, z, eph * nx, eph * ny, eph * nz, wt,
-                  (uint64_t)cid.x | ((uint64_t)cid.y << 32), E, B, ptag);
+      write_child(A.ph, out, P.x, P.y, P.z, eph * nx, eph * ny, eph * nz, P.w,
+                  (uint64_t)cid.x | ((uint64_t)cid.y << 32), P.E, P.B, P.tag);
     } else {
       tl.dropped += 1;
       tl.status |= QED_STATUS_CAPACITY;
@@ -1234,25 +1695,24 @@ static cudaError_t launch_flag_list(qed_ctx *c, const uint8_t *flags, uint8_t wa
   return cudaGetLastError();
 }
 
-template <class Real, int FM, int MODE, int PASS>
-static cudaError_t launch_lepton_pass(qed_ctx *c, const LeptonArgs<Real> &a, cudaStream_t st) {
-  size_t sm = (MODE == MODE_PUSH || sizeof(Real) == 8) ? 0 : lepton_smem<Real>(c);
-  auto kern = k_lepton<Real, FM, MODE, PASS>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
+template <class Real, int FM>
+static cudaError_t launch_push(qed_ctx *c, const LeptonArgs<Real> &a, cudaStream_t st) {
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE, sm);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lepton_push<Real, FM>, TILE, 0);
   if (e != cudaSuccess) return e;
   per_sm = persistent_blocks_per_sm(c, per_sm);
-  kern<<<c->num_sms * per_sm, TILE, sm, st>>>(a);
+  k_lepton_push<Real, FM><<<c->num_sms * per_sm, TILE, 0, st>>>(a);
   c->launches += 1;
   return cudaGetLastError();
 }
 
-template <class Real, int FM, int MODE>
-static cudaError_t launch_stream(qed_ctx *c, const LeptonArgs<Real> &a, cudaStream_t st) {
+// A persistent launch of an emission kernel that stages the FP32 rate and
+// forward tables (and, when `mlp` is set, the learned sampler) in shared memory.
+template <class Real, class Kern>
+static cudaError_t launch_tables_kernel(qed_ctx *c, Kern kern, const LeptonArgs<Real> &a, bool mlp,
+                                        cudaStream_t st) {
   size_t sm = sizeof(Real) == 8 ? 0 : lepton_smem<Real>(c);
-  auto kern = k_lepton_stream<Real, FM, MODE>;
+  if (sm && mlp) sm = ((sm + 15) & ~(size_t)15) + MLP_SMEM_BYTES;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -1264,38 +1724,61 @@ static cudaError_t launch_stream(qed_ctx *c, const LeptonArgs<Real> &a, cudaStre
   return cudaGetLastError();
 }
 
-template <class Real, int FM, int MODE>
-static cudaError_t launch_emit1(qed_ctx *c, const LeptonArgs<Real> &a, cudaStream_t st) {
-  size_t sm = sizeof(Real) == 8 ? 0 : lepton_smem<Real>(c);
-  if (sm && a.use_mlp) sm = ((sm + 15) & ~(size_t)15) + MLP_SMEM_BYTES;
-  auto kern = k_lepton_emit1<Real, FM, MODE>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
+// The class list of the streaming pass's flags (three launches).
+static cudaError_t launch_class_lists(qed_ctx *c, const int64_t *n0, const int64_t *n1,
+                                      cudaStream_t st) {
+  ClassListArgs a{};
+  a.flags = c->heavy_flags;
+  a.n0 = n0;
+  a.n1 = n1;
+  a.list = c->heavy_list;
+  a.chunk_cnt = c->cls_chunk_cnt;
+  a.chunk_off = c->cls_chunk_off;
+  a.off = c->cls_off;
+  a.stage_idx = c->stage_idx;
+  a.stage_n = c->stage_n;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE, sm);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cls_count, TILE, 0);
+  if (e != cudaSuccess) return e;
+  const int grid = c->num_sms * (per_sm > 0 ? per_sm : 1);
+  k_cls_count<<<grid, TILE, 0, st>>>(a);
+  k_cls_scan<<<1, CLS_SCAN_THREADS, 0, st>>>(a);
+  k_cls_scatter<<<grid, TILE, 0, st>>>(a);
+  c->launches += 3;
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_sub_scan(qed_ctx *c, int64_t *ph_n, int64_t ph_cap, cudaStream_t st) {
+  SubScanArgs a{};
+  a.cnt = c->sub_cnt;
+  a.cls_off = c->cls_off;
+  a.sub_meta = c->sub_meta;
+  a.ph_n = ph_n;
+  a.ph_cap = ph_cap;
+  a.o = out_of(c);
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sub_scan, TILE, 0);
   if (e != cudaSuccess) return e;
   per_sm = persistent_blocks_per_sm(c, per_sm);
-  kern<<<c->num_sms * per_sm, TILE, sm, st>>>(a);
+  k_sub_scan<<<c->num_sms * per_sm, TILE, 0, st>>>(a);
   c->launches += 1;
   return cudaGetLastError();
 }
 
-
-// Emission: the streaming pass, then for each deferred class (1: one event,
-// 2: several sub-steps) the ordered list of its particles and the full pass
-// over that list, which appends the photons (class-1 photons first, each class
-// in particle order).
+// Emission: the streaming pass finishes the particles with one sub-step and
+// no event and classes the rest; the class list orders them (class 1 first,
+// each class in particle order); the single-event pass appends the class-1
+// photons; the counting and writing sub-step passes append those of classes
+// 2-5 after them.
 template <class Real, int FM, int MODE>
 static cudaError_t launch_lepton_t(qed_ctx *c, const LeptonArgs<Real> &a, cudaStream_t st) {
-  if (MODE == MODE_PUSH) return launch_lepton_pass<Real, FM, MODE, PASS_MAIN>(c, a, st);
-  cudaError_t e = launch_stream<Real, FM, MODE>(c, a, st);
-  const int64_t *n1 = a.nsp > 1 ? a.sp[1].d_n : nullptr;
-  if (e == cudaSuccess) e = launch_flag_list(c, a.heavy_flags, 1, a.sp[0].d_n, n1, a.o, st);
-  if (e == cudaSuccess) e = launch_emit1<Real, FM, MODE>(c, a, st);
-  for (uint8_t cls = 2; cls <= 5 && e == cudaSuccess; ++cls) {
-    e = launch_flag_list(c, a.heavy_flags, cls, a.sp[0].d_n, n1, a.o, st);
-    if (e == cudaSuccess) e = launch_lepton_pass<Real, FM, MODE, PASS_HEAVY>(c, a, st);
-  }
+  if (MODE == MODE_PUSH) return launch_push<Real, FM>(c, a, st);
+  cudaError_t e = launch_tables_kernel<Real>(c, k_lepton_stream<Real, FM, MODE>, a, false, st);
+  if (e == cudaSuccess) e = launch_class_lists(c, a.sp[0].d_n, a.nsp > 1 ? a.sp[1].d_n : nullptr, st);
+  if (e == cudaSuccess) e = launch_tables_kernel<Real>(c, k_lepton_emit1<Real, FM, MODE>, a, a.use_mlp, st);
+  if (e == cudaSuccess) e = launch_tables_kernel<Real>(c, k_substep_count<Real, FM, MODE>, a, false, st);
+  if (e == cudaSuccess) e = launch_sub_scan(c, a.ph.d_n, a.ph.cap, st);
+  if (e == cudaSuccess) e = launch_tables_kernel<Real>(c, k_substep_write<Real, FM, MODE>, a, false, st);
   return e;
 }
 
@@ -1323,6 +1806,18 @@ cudaError_t launch_lepton(qed_ctx *c, const qed_species *s0, const qed_species *
   a.heavy_flags = c->heavy_flags;
   a.heavy_list = c->heavy_list;
   a.heavy_n = c->heavy_n;
+  a.cls_off = c->cls_off;
+  a.sub_cnt = c->sub_cnt;
+  a.sub_gf = static_cast<Real *>(c->sub_gf);
+  a.rec_e = static_cast<Real *>(c->rec_e);
+  a.rec_k = c->rec_k;
+  a.rec_cap = c->rec_cap;
+  a.stage = static_cast<Stage<Real> *>(c->stage);
+  a.stage_tag = c->stage_tag;
+  a.stage_idx = c->stage_idx;
+  a.stage_n = c->stage_n;
+  a.stage_cap = c->stage_cap;
+  a.sub_meta = c->sub_meta;
   a.mlp_frag = c->mlp_frag;
   a.mlp_w = c->mlp_w;
   a.use_mlp = c->cfg.sampler == QED_SAMPLER_MLP && c->mlp_ready;
