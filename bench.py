@@ -36,6 +36,7 @@ METRIC = "QED particle-steps/s at 64M particles (table vs MLP) and % HBM rooflin
 UNIT = "particle-steps/s"
 N_PART = 1 << 26
 DT = 0.01
+COMPACT_EVERY = 4  # dead photons (pair conversions) are removed every this many steps
 LEPTON_BYTES = 84       # R x,y,z,px,py,pz,w (28) + id (8) + E,B (24); W x,y,z,px,py,pz (24)
 PHOTON_APPEND_BYTES = 61  # x,y,z,px,py,pz,w (28) + id (8) + alive (1) + inherited E,B (24)
 PHOTON_BYTES = 85       # photon step: R 28+8+1+24, W x,y,z (12) [+ alive on pair]
@@ -45,7 +46,9 @@ def workload_desc(n):
     return {"workload": f"chi-target ensemble: {n} electrons (chi log-uniform [1e-3,1e2], gamma "
                         "log-uniform [1e2,1e4], per-particle B perp p, E=0), fused step "
                         "(gather+Boris+chi+rate+Method I+xi+recoil+append; photon push+pairs), "
-                        "table sampler, photons/pairs accumulate",
+                        "table sampler, photons/pairs accumulate; dead photons removed every "
+                        f"{COMPACT_EVERY} steps by stable compaction (qed_compact), live photons "
+                        "counted on the device each step (qed_count_alive)",
             "particles": n, "dt": DT, "precision": "fp32 state, fp64 chi where it cancels",
             "sampler": "table", "l2": "inputs larger than L2 (>= 5.4 GB read per step)"}
 
@@ -229,7 +232,7 @@ def batched_runs_bench(api, torch, mlp_weights, steps=4):
                 g.n.zero_()
             else:  # load kernels once, then restore the state
                 api.qed_step_fused(ctx, e, p, g, F, 0)
-                api.qed_compact(ctx, g)
+                api.qed_compact_fill(ctx, g)
                 torch.cuda.synchronize()
                 e.load(**host)
                 p.n.zero_()
@@ -245,7 +248,7 @@ def batched_runs_bench(api, torch, mlp_weights, steps=4):
                     cnt[k, 0].copy_(e.n[0] + p.n[0])
                     cnt[k, 1].copy_(g.n[0])
                     api.qed_step_fused(ctx, e, p, g, F, k)
-                    api.qed_compact(ctx, g)
+                    api.qed_compact_fill(ctx, g)
             b.record()
             torch.cuda.synchronize()
             ms = a.elapsed_time(b)
@@ -360,7 +363,7 @@ def main():
     n = args.particles
     total_steps = args.warmup + args.steps + args.e2e_steps
     # photon/pair capacity: ~0.25 emissions per electron per step at Dt = 0.01 at the start,
-    # falling as the ensemble cools; dead photons are compacted every step
+    # falling as the ensemble cools; dead photons are removed every step
     cap_g = int(n * 0.3 * (total_steps + 1)) + 4096
     # the photons of the hottest electrons create pairs (a cascade): room for the leptons it adds
     cap_e = 3 * n
@@ -377,9 +380,10 @@ def main():
 
     def one_step(k, s):
         counts[k, 0].copy_(e.n[0] + p.n[0])
-        counts[k, 1].copy_(g.n[0])
+        api.qed_count_alive(ctx, g, counts[k, 1:2])  # photons the step advances
         api.qed_step_fused(ctx, e, p, g, F, s)
-        api.qed_compact(ctx, g)
+        if (s + 1) % COMPACT_EVERY == 0:
+            api.qed_compact(ctx, g)
 
     # warm-up runs the exact loop body, so every kernel (ours and torch's) is loaded
     for s in range(args.warmup):
@@ -434,6 +438,7 @@ def main():
     if args.e2e_steps > 0:
         names_l = ("x", "y", "z", "px", "py", "pz", "w", "id", "ex", "ey", "ez", "bx", "by", "bz")
         names_g = names_l + ("alive",)
+        api.qed_compact(ctx, g)  # start from live photons only (each e2e step compacts)
         torch.cuda.synchronize()
         sizes = {"e": e.count(), "p": p.count(), "g": g.count()}
         pin = {}

@@ -178,6 +178,19 @@ int qed_pair(qed_ctx *ctx, const qed_species *photons, const qed_species *electr
 /* Stable in-place removal of dead particles (alive == 0). */
 int qed_compact(qed_ctx *ctx, const qed_species *s, qed_stream_t stream);
 
+/* Removal of dead particles that moves only as many particles as died.  With
+ * a live particles left, the k-th dead slot below a (in index order) receives
+ * the k-th live particle at or above a; live particles below a keep their
+ * slot.  The result is deterministic; the order of the moved particles is not
+ * their old order.  *s->d_n becomes a.  Same arguments and errors as
+ * qed_compact. */
+int qed_compact_fill(qed_ctx *ctx, const qed_species *s, qed_stream_t stream);
+
+/* Number of live particles (alive != 0) among the first *s->d_n, written to
+ * *d_count (device int64, 8-byte aligned) on `stream` without a host
+ * synchronisation -- for counting particles between compactions. */
+int qed_count_alive(qed_ctx *ctx, const qed_species *s, int64_t *d_count, qed_stream_t stream);
+
 /* One fused QED-PIC step: electrons then positrons (gather at the old
  * position, Boris push, emission with the same fields), then the photons that
  * existed when the step began (push, pair creation).  Particles created in
@@ -249,7 +262,7 @@ int qed_mlp_grad(qed_ctx *ctx, const float *x, const float *t, int64_t n, float 
 /* Batched independent runs (many ensembles of uneven size advanced together).
  * The runs are concatenated in e, p, g (per-particle fields carry each run's
  * fields; tag holds the run index, 0 .. n_runs-1).  Advances `steps` fused
- * steps (qed_step_fused, then stable compaction of dead photons) starting at
+ * steps (qed_step_fused, then qed_compact_fill of the photons) starting at
  * step index step0, as one CUDA graph: captured on the first call for a given
  * combination of species, fields and steps, cached in the context and
  * replayed by later calls.  The step index is read by the kernels from a
@@ -261,8 +274,8 @@ int qed_run_batched(qed_ctx *ctx, const qed_species *e, const qed_species *p,
                     const qed_species *g, const qed_fields *f, int64_t step0, int steps,
                     int n_runs, int64_t *d_run_photons, qed_stream_t stream);
 
-/* Autotuner of the persistent launches: times `reps` fused steps (plus photon
- * compaction) for each persistent-grid occupancy factor 1..max on the given
+/* Autotuner of the persistent launches: times `reps` fused steps (plus
+ * qed_compact_fill of the photons) for each persistent-grid occupancy factor 1..max on the given
  * species -- which it advances, so pass a disposable copy -- keeps the
  * fastest factor in the context for all later launches and returns it in
  * *best_factor; per-candidate milliseconds go to ms_out[0..max-1] if non-NULL

@@ -82,6 +82,8 @@ SIGNATURES = {
     "qed_pair": (C.c_int, [_P, C.POINTER(qed_species), C.POINTER(qed_species), C.POINTER(qed_species),
                            C.POINTER(qed_fields), C.c_int64, _P]),
     "qed_compact": (C.c_int, [_P, C.POINTER(qed_species), _P]),
+    "qed_compact_fill": (C.c_int, [_P, C.POINTER(qed_species), _P]),
+    "qed_count_alive": (C.c_int, [_P, C.POINTER(qed_species), _P, _P]),
     "qed_step_fused": (C.c_int, [_P, C.POINTER(qed_species), C.POINTER(qed_species),
                                  C.POINTER(qed_species), C.POINTER(qed_fields), C.c_int64, _P]),
     "qed_sample_xi": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int64, _P]),

@@ -220,6 +220,22 @@ def qed_compact(ctx: Context, s: Species, stream=None) -> None:
     B.check(B.lib().qed_compact(ctx.handle, C.byref(s.struct()), _stream(stream)), "qed_compact")
 
 
+def qed_count_alive(ctx: Context, s: Species, out=None, stream=None):
+    """Live particles of s, written on the device into `out` (an int64 CUDA
+    tensor element, e.g. counts[k, 1]; a new one-element tensor if None)."""
+    if out is None:
+        out = torch.zeros(1, dtype=torch.int64, device=s.x.device)
+    assert out.dtype == torch.int64 and out.is_cuda
+    B.check(B.lib().qed_count_alive(ctx.handle, C.byref(s.struct()), C.c_void_p(out.data_ptr()),
+                                    _stream(stream)), "qed_count_alive")
+    return out
+
+
+def qed_compact_fill(ctx: Context, s: Species, stream=None) -> None:
+    B.check(B.lib().qed_compact_fill(ctx.handle, C.byref(s.struct()), _stream(stream)),
+            "qed_compact_fill")
+
+
 def qed_step_fused(ctx: Context, e: Species | None, p: Species | None, g: Species, f, step: int,
                    stream=None) -> None:
     se, sp_, sg = _sp(e), _sp(p), _sp(g)

@@ -15,6 +15,8 @@ template <class Real>
 cudaError_t launch_photon(qed_ctx *, const qed_species *, const qed_species *, const qed_species *,
                           const int64_t *, const qed_fields *, int64_t, cudaStream_t);
 template <class Real> cudaError_t launch_compact(qed_ctx *, const qed_species *, cudaStream_t);
+template <class Real> cudaError_t launch_compact_fill(qed_ctx *, const qed_species *, cudaStream_t);
+cudaError_t launch_count_alive(qed_ctx *, const qed_species *, int64_t *, cudaStream_t);
 template <class Real>
 cudaError_t launch_eval(qed_ctx *, int, int, const double *, const double *, const uint32_t *,
                         double *, int64_t, cudaStream_t);
@@ -78,7 +80,7 @@ static void free_ctx(qed_ctx *c) {
                   c->P32, c->Yp32, c->tile_state, c->sync, c->snap, c->d_counters,
                   c->heavy_flags, c->heavy_list, c->heavy_n, c->cls_chunk_cnt,
                   c->cls_chunk_off, c->cls_off, c->sub_cnt, c->sub_gf, c->rec_e,
-                  c->rec_k, c->sub_meta, c->stage, c->stage_tag, c->stage_idx, c->stage_n,
+                  c->rec_k, c->sub_meta, c->fill_meta, c->stage, c->stage_tag, c->stage_idx, c->stage_n,
                   c->mlp_mem};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -226,7 +228,8 @@ extern "C" int qed_init_tables(const qed_config *cfg, qed_ctx **out, qed_stream_
       cudaMalloc(&c->stage_tag, sizeof(uint32_t) * (size_t)c->stage_cap) != cudaSuccess ||
       cudaMalloc(&c->stage_idx, sizeof(int32_t) * (size_t)c->heavy_slots) != cudaSuccess ||
       cudaMalloc(&c->stage_n, sizeof(unsigned int)) != cudaSuccess ||
-      cudaMalloc(&c->sub_meta, 2 * sizeof(int64_t)) != cudaSuccess) {
+      cudaMalloc(&c->sub_meta, 2 * sizeof(int64_t)) != cudaSuccess ||
+      cudaMalloc(&c->fill_meta, 2 * sizeof(int64_t)) != cudaSuccess) {
     free_ctx(c);
     return QED_ERR_NOMEM;
   }
@@ -327,6 +330,22 @@ extern "C" int qed_compact(qed_ctx *c, const qed_species *s, qed_stream_t stream
   cudaError_t e = c->cfg.precision == QED_FP64 ? launch_compact<double>(c, s, st)
                                                 : launch_compact<float>(c, s, st);
   return cuda_fail(e, "qed_compact");
+}
+
+extern "C" int qed_compact_fill(qed_ctx *c, const qed_species *s, qed_stream_t stream) {
+  if (!c || !species_ok(s, true)) return QED_ERR_ARG;
+  if (check_cap(c, s)) return QED_ERR_CAPACITY;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = c->cfg.precision == QED_FP64 ? launch_compact_fill<double>(c, s, st)
+                                                : launch_compact_fill<float>(c, s, st);
+  return cuda_fail(e, "qed_compact_fill");
+}
+
+extern "C" int qed_count_alive(qed_ctx *c, const qed_species *s, int64_t *d_count,
+                               qed_stream_t stream) {
+  if (!c || !d_count || !species_ok(s, true)) return QED_ERR_ARG;
+  if ((((uintptr_t)d_count) & 7) != 0) return QED_ERR_ARG;
+  return cuda_fail(launch_count_alive(c, s, d_count, (cudaStream_t)stream), "qed_count_alive");
 }
 
 extern "C" int qed_step_fused(qed_ctx *c, const qed_species *e, const qed_species *p,

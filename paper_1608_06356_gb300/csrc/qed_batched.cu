@@ -41,11 +41,12 @@ static int cu(cudaError_t e, const char *what) {
   return QED_ERR_CUDA;
 }
 
-// One step of the batched sequence: fused step, then photon compaction.
+// One step of the batched sequence: fused step, then removal of the dead
+// photons by hole filling (only the photons that died are replaced).
 static int one_step(qed_ctx *c, const qed_species *e, const qed_species *p, const qed_species *g,
                     const qed_fields *f, int64_t step, cudaStream_t st) {
   int rc = qed_step_fused(c, e, p, g, f, step, (qed_stream_t)st);
-  if (rc == QED_OK) rc = qed_compact(c, g, (qed_stream_t)st);
+  if (rc == QED_OK) rc = qed_compact_fill(c, g, (qed_stream_t)st);
   return rc;
 }
 

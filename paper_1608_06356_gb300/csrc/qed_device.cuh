@@ -58,6 +58,14 @@ __device__ __forceinline__ float m_log1p(float x) { return log1pf(x); }
 __device__ __forceinline__ double m_log1p(double x) { return log1p(x); }
 __device__ __forceinline__ float m_exp(float x) { return expf(x); }
 __device__ __forceinline__ double m_exp(double x) { return exp(x); }
+// Reduced-precision forms (a few ulp) for the rate evaluation, whose table
+// interpolation error is larger; FP64 keeps the full-precision functions.
+__device__ __forceinline__ float r_log(float x) { return __logf(x); }
+__device__ __forceinline__ double r_log(double x) { return log(x); }
+__device__ __forceinline__ float r_exp(float x) { return __expf(x); }
+__device__ __forceinline__ double r_exp(double x) { return exp(x); }
+__device__ __forceinline__ float r_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double r_div(double a, double b) { return a / b; }
 __device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float m_floor(float x) { return floorf(x); }
@@ -260,9 +268,11 @@ __device__ __forceinline__ RateOut<Real> photon_rate(const Real *R, const Real *
                                                      Real chi, Real gamma, Tally &tl) {
   RateOut<Real> o{(Real)0, (Real)-1e30, (Real)0};
   if (!(chi > (Real)0)) return o;
-  Real xi_min = sel<Real>(C.xi_min_energy, C.f_xi_min_energy) / gamma;
-  if (!(xi_min < (Real)1)) return o;
-  Real l = m_log(chi);
+  // xi_min = c / gamma (c = xi_min_energy): the cut exists for gamma > c
+  const Real c = sel<Real>(C.xi_min_energy, C.f_xi_min_energy);
+  const Real gmc = gamma - c;
+  if (!(gmc > (Real)0)) return o;
+  Real l = r_log(chi);
   Real shift = (Real)0;  // ln-rate extrapolation below chi_min: int dW ~ chi
   if (l < T.gl.lo) {
     shift = l - T.gl.lo;
@@ -277,11 +287,12 @@ __device__ __forceinline__ RateOut<Real> photon_rate(const Real *R, const Real *
   o.l = l;
   Real lnG = interp1(R, T.gl, l) + shift;
   Real wmin = (Real)0;
-  if (xi_min > (Real)0) {
-    // y = ln delta_min, delta_min = 2 xi_min / (3 chi (1 - xi_min)); chi enters
-    // through the unclamped ln chi (the delta-distribution tends to a fixed
-    // shape below chi_min)
-    Real y = m_log((Real)2 * xi_min / ((Real)3 * ((Real)1 - xi_min))) - (l + shift);
+  if (c > (Real)0) {
+    // y = ln delta_min, delta_min = 2 xi_min / (3 chi (1 - xi_min)) with
+    // xi_min / (1 - xi_min) = c / (gamma - c); chi enters through the
+    // unclamped ln chi (the delta-distribution tends to a fixed shape below
+    // chi_min)
+    Real y = r_log(r_div((Real)(2.0 / 3.0) * c, gmc)) - (l + shift);
     if (y > T.gy.hi) return o;  // cut above the spectrum: u_min = 1 - e^-(>90)
     Real kmin;
     if (y < T.gy.lo) {
@@ -292,9 +303,9 @@ __device__ __forceinline__ RateOut<Real> photon_rate(const Real *R, const Real *
       kmin = interp2(F, T.gl, l, T.gy, y);
     }
     o.kmin = kmin;
-    wmin = m_exp(kmin);
+    wmin = r_exp(kmin);
   }
-  o.W = sel<Real>(C.alpha_aS, C.f_alpha_aS) / gamma * m_exp(lnG - wmin);
+  o.W = r_div(sel<Real>(C.alpha_aS, C.f_alpha_aS), gamma) * r_exp(lnG - wmin);
   return o;
 }
 

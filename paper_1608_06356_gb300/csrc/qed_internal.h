@@ -39,6 +39,7 @@ struct qed_ctx {
   uint32_t *rec_k;    // [SUB_REC][rec_cap]
   int64_t rec_cap;
   int64_t *sub_meta;  // [2] photons of the sub-step entries, photon count before them
+  int64_t *fill_meta; // [2] count before and after a hole-filling compaction
   // staging records of the flagged leptons (streaming pass -> later passes)
   void *stage;          // Stage<Real> [stage_cap] (64 B FP32, 128 B FP64)
   uint32_t *stage_tag;  // [stage_cap]

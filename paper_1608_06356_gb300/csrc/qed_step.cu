@@ -1,17 +1,22 @@
 // qed_step.cu -- the per-macroparticle QED Monte Carlo step on sm_103a.
 //
-// Every step kernel is persistent: a grid of (SM count x resident blocks)
-// CTAs takes 256-particle tiles from a device counter in increasing order.
-// Each thread owns one particle of the tile:
+// What is computed per particle:
 //   leptons: field gather (uniform / per-particle / CIC) -> Boris push ->
 //            chi_e (Eq. 2) -> W_rad from the tables (Eq. 1 with the xi_min
 //            cut) -> N = max(1, ceil(W Dt / 0.2)) sub-steps -> Method I events
 //            with Philox draws -> xi from Eq. (7) -> recoil; photons appended.
 //   photons: ballistic push -> chi_ph (Eq. 3) -> W_pair (Eq. 6) -> Method I ->
 //            pair split xi (Eq. 6) -> e-/e+ appended, photon marked dead.
-// Appends keep particle order (and sub-step order within a particle): the
-// per-thread counts are scanned within the block and across tiles by a
-// single-pass decoupled look-back, so slot = count at launch + global prefix.
+// How the lepton step is laid out: a streaming pass reads every particle once
+// (coalesced), pushes it and decides with a cheap upper bound of the rate
+// whether it surely has N = 1 and no event; those (most) are finished there.
+// The rest are staged as 64-byte records, ordered by a class list (binned by
+// N so that lanes of a warp do similar work), and run through a counting
+// pass, a scan and a writing pass that append their photons in list order.
+// Photons: a streaming pass, then an ordered pass over the flagged ones.
+// Appends keep a deterministic order (and sub-step order within a particle);
+// ordered passes scan within the block and across tiles by a single-pass
+// decoupled look-back, so slot = count at launch + global prefix.
 // Particle state is structure-of-arrays; loads and stores of a tile are
 // coalesced 4-byte (FP32) or 8-byte (FP64) accesses.
 #include <cstdio>
@@ -368,7 +373,7 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 4 : 2) k_lepton_stre
         Tally t0;
         t0.clear();
         RateOut<Real> ro = photon_rate(sR, sF, A.T, A.C, chi, g, t0);
-        Real wdt = ro.W * dt;
+        const Real wdt = ro.W * dt;
         if (wdt > wdt_max) {
           // classes by sub-step count N = ceil(W Dt / wdt_max): 2: N <= 3, 3: N <= 7,
           // 4: N <= 15, 5: N >= 16 (lanes of a warp then do similar amounts of work)
@@ -376,7 +381,7 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 4 : 2) k_lepton_stre
           flag = q <= (Real)3 ? 2 : (q <= (Real)7 ? 3 : (q <= (Real)15 ? 4 : 5));
         } else {
           U4 r = draw(A.C.seed, pid, step_, 0, STREAM_EMIT);
-          if (wdt > unif<Real>(r.x)) flag = 1;
+          if (wdt > unif<Real>(r.x)) flag = 1;  // one sub-step with an event
         }
         if (flag == 0) {
           tl.status |= t0.status;
@@ -436,22 +441,21 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 4 : 2) k_lepton_stre
 }
 
 // ---------------------------------------------------------------------------
-// Sub-step passes over the particles that need N > 1 generator sub-steps
-// (classes 2-5 of the class list).  The work is split in two so that no
-// expensive emission chain ever waits on another:
-//   counting pass: redo the particle from its stored state (gather, push,
-//     chi, rate, N) and run its Method I chain -- per sub-step one Philox
-//     draw, on an event xi from the inverse table and the recoil -- writing
-//     only the number of photons, the final gamma and the first REC
-//     emission records (photon energy, sub-step index).  Particles are
-//     independent here: no scan, no ordering.
-//   writing pass: an exclusive scan of the counts (decoupled look-back over
-//     32-entry warp tiles; a tile's aggregate is known as soon as it has read
-//     its counts, so no tile waits on another's emission work) gives every
-//     particle its photon slots; the particle is pushed again (the same
-//     arithmetic), its photons written from the records -- or, for a particle
-//     with more than REC photons, from a replay of its chain -- and its final
-//     state stored.
+// Emission passes over the class list: every lepton the streaming pass could
+// not finish (an event possible, or N > 1 by the rate bound).  The work is
+// split so that no emission chain ever waits on another:
+//   counting pass: the exact rate (with the xi_min cut) and N, then the
+//     particle's Method I chain -- per sub-step one Philox draw, on an event
+//     kappa from r2, ln delta from the inverse table (or the learned sampler
+//     for N = 1), xi (Eq. 7) and the recoil -- writing only the number of
+//     photons, the final gamma and the first REC emission records (photon
+//     energy, sub-step index).  Particles are independent: no scan, no order.
+//   scan: an in-place exclusive scan of the counts (one pass, decoupled
+//     look-back over 4096-entry tiles of uniform cost) gives every particle
+//     its first photon slot.
+//   writing pass: the photons of each particle, from its records -- or, for a
+//     particle with more than REC photons, from a replay of its chain -- and
+//     its final momentum.
 // Within a warp the chain is split into a scan phase (each lane draws until
 // its next event) and an emission phase that the lanes with an event execute
 // together, so lanes of different event counts stay converged.
@@ -551,13 +555,19 @@ __device__ __forceinline__ int64_t substep_count(const Consts &C, Real W, Real d
   return (int64_t)nn;
 }
 
-template <class Real, int FM, int MODE>
-__global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 3 : 2) k_substep_count(LeptonArgs<Real> A) {
+template <class Real, int FM, int MODE, bool MLP>
+__global__ void __launch_bounds__(TILE, sizeof(Real) == 4 && !MLP ? 3 : 2) k_substep_count(LeptonArgs<Real> A) {
   const int64_t step_ = A.d_step ? *A.d_step : A.step;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool kSmem = sizeof(Real) == 4;
   Real *sR = kSmem ? reinterpret_cast<Real *>(smem_raw) : const_cast<Real *>(A.T.R);
   Real *sF = kSmem ? sR + A.T.gl.n : const_cast<Real *>(A.T.F);
+  // learned sampler image after the tables (FP32 contexts only)
+  uint32_t *s_frag = reinterpret_cast<uint32_t *>(
+      smem_raw + (kSmem ? (((size_t)A.T.gl.n * (1 + A.T.gy.n) * sizeof(Real) + 15) & ~(size_t)15) : 0));
+  float *s_fw = reinterpret_cast<float *>(s_frag + MLP_FRAG_WORDS);
+  constexpr bool use_mlp = kSmem && MLP;
+  if (use_mlp) mlp_stage(s_frag, s_fw, A.mlp_frag, A.mlp_w);
   __shared__ long long s_meta[4];
   __shared__ BlockTally bt;
   if (kSmem) {
@@ -567,7 +577,7 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 3 : 2) k_substep_cou
   block_tally_init(&bt);
   if (threadIdx.x == 0) {
     s_meta[0] = *(volatile int64_t *)A.sp[0].d_n;
-    s_meta[1] = A.cls_off[1];
+    s_meta[1] = 0;  // the whole class list
     s_meta[2] = A.cls_off[NCLS];
   }
   __syncthreads();
@@ -623,8 +633,24 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 3 : 2) k_substep_cou
         ++k;
       }
       if (!__any_sync(0xFFFFFFFFu, ev)) break;
-      if (ev) {  // emission, by every lane with an event
-        XiOut<Real> xo = photon_xi(A.T.Y, A.T, ro.l, chi, ro.kmin, unif<Real>(wy), unif<Real>(~wy), tl);
+      // emission, by every lane with an event: kappa from r2 (Eq. 7), then
+      // ln delta from the inverse table -- or, for a particle with N = 1 in
+      // a context with the learned sampler, from the network (a
+      // warp-collective call, made with every lane)
+      const Real kap = ev ? photon_kappa(ro.kmin, unif<Real>(wy), unif<Real>(~wy)) : (Real)0;
+      Real Y = (Real)0;
+      bool in_mlp = false;
+      if (use_mlp) {
+        const float lchi = chi > (Real)0 ? (float)m_log(chi) : MLP_L_LO - 1.0f;
+        in_mlp = ev && N == 1 && lchi >= MLP_L_LO && lchi <= MLP_L_HI && (float)kap >= MLP_K_LO &&
+                 (float)kap <= MLP_K_HI;
+        const float zz = mlp_infer_warp(s_frag, s_fw, (lchi - MLP_LC) / MLP_LS,
+                                        ((float)kap - MLP_KC) / MLP_KS);
+        Y = (Real)(zz + mlp_baseline((float)kap));
+      }
+      if (ev) {
+        if (!in_mlp) Y = photon_lndelta_table(A.T.Y, A.T, ro.l, kap, tl);
+        XiOut<Real> xo = xi_from_lndelta(chi, Y);
         Real g2 = g * xo.omxi, eph = g * xo.xi;
         if (g2 < (Real)1) { g2 = (Real)1; eph = g - (Real)1; }
         if (cnt < REC && h < rc) {
@@ -671,7 +697,7 @@ __global__ void __launch_bounds__(TILE) k_sub_scan(SubScanArgs A) {
   __shared__ uint32_t scan_sm[33];
   __shared__ long long s_meta[6];
   if (threadIdx.x == 0) {
-    s_meta[2] = A.cls_off[NCLS] - A.cls_off[1];
+    s_meta[2] = A.cls_off[NCLS];
     s_meta[3] = *(volatile int64_t *)A.ph_n;
     s_meta[4] = (long long)A.o.scan.sync[2];
   }
@@ -741,7 +767,7 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 3 : 2) k_substep_wri
   block_tally_init(&bt);
   if (threadIdx.x == 0) {
     s_meta[0] = *(volatile int64_t *)A.sp[0].d_n;
-    s_meta[1] = A.cls_off[1];
+    s_meta[1] = 0;  // the whole class list
     s_meta[2] = A.cls_off[NCLS];
     s_meta[3] = A.sub_meta[0];  // photons of all entries
     s_meta[4] = A.sub_meta[1];  // photon count before them
@@ -1083,123 +1109,6 @@ __global__ void __launch_bounds__(TILE) k_cls_scatter(ClassListArgs A) {
 }
 
 // ---------------------------------------------------------------------------
-// Single-event pass: particles whose one sub-step drew an event (class 1 of
-// the streaming pass) each emit exactly one photon, so the photon of list
-// entry h goes to slot (count at launch) + h -- no scan is needed.  The
-// particle is redone from its stored state; the streaming pass's decision is
-// taken as given.  The last CTA to finish publishes the new photon count.
-// ---------------------------------------------------------------------------
-template <class Real, int FM, int MODE>
-__global__ void __launch_bounds__(TILE) k_lepton_emit1(LeptonArgs<Real> A) {
-  const int64_t step_ = A.d_step ? *A.d_step : A.step;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr bool kSmem = sizeof(Real) == 4;
-  Real *sR = kSmem ? reinterpret_cast<Real *>(smem_raw) : const_cast<Real *>(A.T.R);
-  Real *sF = kSmem ? sR + A.T.gl.n : const_cast<Real *>(A.T.F);
-  // learned sampler image after the tables (FP32 contexts only)
-  uint32_t *s_frag = reinterpret_cast<uint32_t *>(
-      smem_raw + (kSmem ? (((size_t)A.T.gl.n * (1 + A.T.gy.n) * sizeof(Real) + 15) & ~(size_t)15) : 0));
-  float *s_fw = reinterpret_cast<float *>(s_frag + MLP_FRAG_WORDS);
-  const bool use_mlp = kSmem && A.use_mlp;
-  if (use_mlp) mlp_stage(s_frag, s_fw, A.mlp_frag, A.mlp_w);
-  __shared__ long long s_meta[8];
-  __shared__ BlockTally bt;
-  if (kSmem) {
-    load_tables_smem(sR, A.T.R, A.T.gl.n);
-    load_tables_smem(sF, A.T.F, A.T.gl.n * A.T.gy.n);
-  }
-  block_tally_init(&bt);
-  if (threadIdx.x == 0) {
-    s_meta[0] = *(volatile int64_t *)A.sp[0].d_n;
-    s_meta[1] = A.cls_off[1];  // class 1 occupies [0, cls_off[1])
-    s_meta[2] = *(volatile int64_t *)A.ph.d_n;
-    s_meta[3] = (long long)A.o.scan.sync[2];
-  }
-  __syncthreads();
-  const int64_t n0 = s_meta[0], nl = s_meta[1], base = s_meta[2];
-  const uint32_t epoch = (uint32_t)s_meta[3];
-  const int64_t T0 = (n0 + TILE - 1) / TILE;
-  const Real inv_aS = sel<Real>(A.C.inv_aS, A.C.f_inv_aS);
-  const Real dt = sel<Real>(A.C.dt, A.C.f_dt);
-  Tally tl;
-  tl.clear();
-  // warp-uniform loop (the learned sampler is a warp-collective call)
-  for (int64_t hb = blockIdx.x * (int64_t)TILE + (threadIdx.x & ~31); hb < nl;
-       hb += (int64_t)gridDim.x * TILE) {
-    const int64_t h = hb + (threadIdx.x & 31);
-    const bool active = h < nl;
-    Entry<Real> P;
-    P.x = P.y = P.z = P.px = P.py = P.w = (Real)0;
-    P.pz = P.g = (Real)1;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) { P.E[c] = (Real)0; P.B[c] = (Real)0; }
-    P.id = 0;
-    P.tag = 0;
-    if (active) load_entry<Real, FM, MODE>(A, A.heavy_list[h], T0, dt, P);
-    const Real px = P.px, py = P.py, pz = P.pz, g = P.g;
-    const Real *E = P.E, *B = P.B;
-    const uint64_t pid = P.id;
-    Real chi = chi_lepton(px, py, pz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
-    Tally t0;  // an idle lane tallies nothing
-    t0.clear();
-    RateOut<Real> ro = photon_rate(sR, sF, A.T, A.C, chi, g, t0);
-    if (active) {
-      tl.status |= t0.status;
-      tl.domain += t0.domain;
-    }
-    U4 r = draw(A.C.seed, pid, step_, 0, STREAM_EMIT);
-    const Real kap = photon_kappa(ro.kmin, unif<Real>(r.y), unif<Real>(~r.y));
-    Real Y = 0;
-    bool in_mlp = false;
-    if (use_mlp) {
-      const float lchi = (float)m_log(chi);
-      in_mlp = active && lchi >= MLP_L_LO && lchi <= MLP_L_HI && (float)kap >= MLP_K_LO &&
-               (float)kap <= MLP_K_HI;
-      const float zz = mlp_infer_warp(s_frag, s_fw, (lchi - MLP_LC) / MLP_LS,
-                                      ((float)kap - MLP_KC) / MLP_KS);
-      Y = (Real)(zz + mlp_baseline((float)kap));
-    }
-    if (!active) continue;
-    if (!in_mlp) Y = photon_lndelta_table(A.T.Y, A.T, ro.l, kap, tl);
-    XiOut<Real> xo = xi_from_lndelta(chi, Y);
-    Real g2 = g * xo.omxi, eph = g * xo.xi;
-    if (g2 < (Real)1) { g2 = (Real)1; eph = g - (Real)1; }
-    Real nx, ny, nz;
-    unit_dir(P, nx, ny, nz);
-    store_entry<Real, MODE>(A, P, g2, nx, ny, nz);
-    tl.events += 1;
-    tl.substeps += 1;
-    int b = spec_bin(A.C, eph);
-    if (b >= 0) atomicAdd(&bt.hist[b], 1ull);
-    const int64_t out = base + h;
-    if (out < A.ph.cap) {
-      U4 cid = draw(A.C.seed, pid, step_, 0, STREAM_PHOTON_ID);
-      write_child(A.ph, out, P.x, P.y, P.z, eph * nx, eph * ny, eph * nz, P.w,
-                  (uint64_t)cid.x | ((uint64_t)cid.y << 32), P.E, P.B, P.tag);
-    } else {
-      tl.dropped += 1;
-      tl.status |= QED_STATUS_CAPACITY;
-    }
-  }
-  tally_flush(&bt, tl);
-  __syncthreads();
-  block_tally_commit(&bt, A.o.cnt, 0);
-  // the last CTA to finish publishes the photon count (all CTAs have read it)
-  if (threadIdx.x == 0) {
-    __threadfence();
-    unsigned int prev = atomicAdd(&A.o.scan.sync[1], 1u);
-    if (prev == gridDim.x - 1) {
-      int64_t nn = base + nl;
-      *A.ph.d_n = nn < A.ph.cap ? nn : A.ph.cap;
-      A.o.scan.sync[0] = 0u;
-      A.o.scan.sync[1] = 0u;
-      A.o.scan.sync[2] = epoch + 1u;
-      __threadfence();
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Photon kernel: push + Breit-Wheeler pairs
 // ---------------------------------------------------------------------------
 template <class Real> struct PhotonArgs {
@@ -1467,6 +1376,195 @@ __global__ void __launch_bounds__(TILE) k_compact(CompactArgs<Real> A) {
   }
   if (threadIdx.x == 0 && status) atomicOr(&A.o.cnt->status, status);
   launch_epilogue(A.o.scan, epoch);
+}
+
+// ---------------------------------------------------------------------------
+// Hole-filling compaction.  With a live particles among n, every dead slot
+// below a (a hole) receives a live particle from [a, n) (a tail): the k-th
+// hole in index order takes the k-th tail in index order.  Only as many
+// particles move as there are holes, and every live particle below a keeps
+// its index.  Count, scan, hole-list and move passes; no CTA waits on another.
+// ---------------------------------------------------------------------------
+constexpr int FILL_ITEMS = 8;
+constexpr int FILL_CHUNK = TILE * FILL_ITEMS;
+static_assert(FILL_CHUNK == CLS_CHUNK_FLAGS, "fill chunks use the class-list scratch");
+
+template <class Real> struct FillArgs {
+  Sp<Real> s;
+  unsigned long long *chunk_alive;  // [chunks]
+  uint32_t *chunk_off;              // [chunks][NCLS]: [0] holes before, [1] tails before
+  int64_t *meta;                    // [0] n, [1] a
+  int *holes;                       // hole slots in index order
+};
+
+// live flags of this thread's 8 slots of chunk c (bit j: slot first + j)
+__device__ __forceinline__ uint32_t fill_bits(const uint8_t *alive, int64_t c, int64_t n,
+                                              int64_t &first) {
+  first = c * FILL_CHUNK + (int64_t)threadIdx.x * FILL_ITEMS;
+  uint32_t bits = 0;
+#pragma unroll
+  for (int j = 0; j < FILL_ITEMS; ++j)
+    if (first + j < n && alive[first + j]) bits |= 1u << j;
+  return bits;
+}
+
+template <class Real>
+__global__ void __launch_bounds__(TILE) k_fill_count(FillArgs<Real> A) {
+  __shared__ uint32_t scan_sm[33];
+  const int64_t n = *(volatile const int64_t *)A.s.d_n;
+  const int64_t nchunks = (n + FILL_CHUNK - 1) / FILL_CHUNK;
+  for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    int64_t first;
+    const uint32_t bits = fill_bits(A.s.alive, c, n, first);
+    block_excl_scan(__popc(bits), scan_sm);
+    if (threadIdx.x == 0) A.chunk_alive[c] = scan_sm[32];
+    __syncthreads();
+  }
+}
+
+// One CTA: a, the boundary chunk's split, and each chunk's hole and tail offsets.
+__global__ void __launch_bounds__(CLS_SCAN_THREADS) k_fill_scan(const uint8_t *alive,
+                                                                 int64_t *d_n,
+                                                                 FillArgs<float> A) {
+  __shared__ unsigned long long tot;
+  __shared__ unsigned long long sm[33];
+  __shared__ uint32_t xs;
+  const int64_t n = *(volatile const int64_t *)d_n;
+  const int64_t nchunks = (n + FILL_CHUNK - 1) / FILL_CHUNK;
+  if (threadIdx.x == 0) { tot = 0; xs = 0; }
+  __syncthreads();
+  unsigned long long mine = 0;
+  for (int64_t c = threadIdx.x; c < nchunks; c += blockDim.x) mine += A.chunk_alive[c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xFFFFFFFFu, mine, o);
+  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&tot, mine);
+  __syncthreads();
+  const int64_t a = (int64_t)tot;
+  // live particles of the boundary chunk below a
+  const int64_t cb = a / FILL_CHUNK, b0 = cb * FILL_CHUNK;
+  uint32_t xl = 0;
+  for (int64_t i = b0 + threadIdx.x; i < a; i += blockDim.x) xl += alive[i] ? 1u : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) xl += __shfl_xor_sync(0xFFFFFFFFu, xl, o);
+  if ((threadIdx.x & 31) == 0 && xl) atomicAdd(&xs, xl);
+  __syncthreads();
+  const uint32_t x = xs;
+  if (threadIdx.x == 0) {
+    A.meta[0] = n;
+    A.meta[1] = a;
+    *d_n = a;
+  }
+  int64_t carry_h = 0, carry_t = 0;
+  const int64_t per_round = (int64_t)blockDim.x * CLS_SCAN_PER_THREAD;
+  for (int64_t r0 = 0; r0 < nchunks; r0 += per_round) {
+    const int64_t c0 = r0 + (int64_t)threadIdx.x * CLS_SCAN_PER_THREAD;
+    uint32_t hv[CLS_SCAN_PER_THREAD], tv[CLS_SCAN_PER_THREAD];
+    uint32_t hs = 0, ts = 0;
+#pragma unroll
+    for (int j = 0; j < CLS_SCAN_PER_THREAD; ++j) {
+      const int64_t c = c0 + j;
+      hv[j] = tv[j] = 0;
+      if (c < nchunks) {
+        const int64_t lo = c * FILL_CHUNK, hi = lo + FILL_CHUNK < n ? lo + FILL_CHUNK : n;
+        const uint32_t al = (uint32_t)A.chunk_alive[c];
+        if (hi <= a) {
+          hv[j] = (uint32_t)(hi - lo) - al;
+        } else if (lo >= a) {
+          tv[j] = al;
+        } else {
+          hv[j] = (uint32_t)(a - lo) - x;
+          tv[j] = al - x;
+        }
+      }
+      hs += hv[j];
+      ts += tv[j];
+    }
+    const unsigned long long v = (unsigned long long)hs | ((unsigned long long)ts << 32);
+    const unsigned long long e = block_excl_scan64(v, sm), tt = sm[32];
+    uint32_t rh = (uint32_t)e, rt = (uint32_t)(e >> 32);
+#pragma unroll
+    for (int j = 0; j < CLS_SCAN_PER_THREAD; ++j) {
+      const int64_t c = c0 + j;
+      if (c < nchunks) {
+        A.chunk_off[c * NCLS + 0] = (uint32_t)(carry_h + rh);
+        A.chunk_off[c * NCLS + 1] = (uint32_t)(carry_t + rt);
+      }
+      rh += hv[j];
+      rt += tv[j];
+    }
+    carry_h += (int64_t)(uint32_t)tt;
+    carry_t += (int64_t)(uint32_t)(tt >> 32);
+  }
+}
+
+template <class Real>
+__global__ void __launch_bounds__(TILE) k_fill_holes(FillArgs<Real> A) {
+  __shared__ uint32_t scan_sm[33];
+  const int64_t n = A.meta[0], a = A.meta[1];
+  const int64_t nchunks = (a + FILL_CHUNK - 1) / FILL_CHUNK;  // chunks with slots below a
+  for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    int64_t first;
+    uint32_t bits = fill_bits(A.s.alive, c, n, first);
+    uint32_t hole = 0;
+#pragma unroll
+    for (int j = 0; j < FILL_ITEMS; ++j)
+      if (first + j < a && !(bits & (1u << j))) hole |= 1u << j;
+    uint32_t k = A.chunk_off[c * NCLS + 0] + block_excl_scan(__popc(hole), scan_sm);
+    __syncthreads();
+    while (hole) {
+      const int j = __ffs(hole) - 1;
+      hole &= hole - 1;
+      A.holes[k++] = (int)(first + j);
+    }
+  }
+}
+
+template <class Real>
+__global__ void __launch_bounds__(TILE) k_fill_move(FillArgs<Real> A) {
+  __shared__ uint32_t scan_sm[33];
+  const int64_t n = A.meta[0], a = A.meta[1];
+  const int64_t c_lo = a / FILL_CHUNK, nchunks = (n + FILL_CHUNK - 1) / FILL_CHUNK;
+  const Sp<Real> &S = A.s;
+  const bool fields = S.ex != nullptr;
+  for (int64_t c = c_lo + blockIdx.x; c < nchunks; c += gridDim.x) {
+    int64_t first;
+    const uint32_t bits = fill_bits(S.alive, c, n, first);
+    uint32_t tail = 0;
+#pragma unroll
+    for (int j = 0; j < FILL_ITEMS; ++j)
+      if (first + j >= a && (bits & (1u << j))) tail |= 1u << j;
+    uint32_t k = A.chunk_off[c * NCLS + 1] + block_excl_scan(__popc(tail), scan_sm);
+    __syncthreads();
+    while (tail) {
+      const int j = __ffs(tail) - 1;
+      tail &= tail - 1;
+      const int64_t i = first + j, d = A.holes[k++];
+      S.x[d] = S.x[i]; S.y[d] = S.y[i]; S.z[d] = S.z[i];
+      S.px[d] = S.px[i]; S.py[d] = S.py[i]; S.pz[d] = S.pz[i];
+      S.w[d] = S.w[i];
+      S.id[d] = S.id[i];
+      if (S.tag) S.tag[d] = S.tag[i];
+      if (fields) {
+        S.ex[d] = S.ex[i]; S.ey[d] = S.ey[i]; S.ez[d] = S.ez[i];
+        S.bx[d] = S.bx[i]; S.by[d] = S.by[i]; S.bz[d] = S.bz[i];
+      }
+      S.alive[d] = 1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Number of live particles (alive != 0) among the first *d_n, added to *out.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(TILE) k_count_alive(const uint8_t *alive, const int64_t *d_n,
+                                                      unsigned long long *out) {
+  const int64_t n = *(volatile const int64_t *)d_n;
+  unsigned long long c = 0;
+  for (int64_t i = blockIdx.x * (int64_t)TILE + threadIdx.x; i < n; i += (int64_t)gridDim.x * TILE)
+    c += alive[i] ? 1u : 0u;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
 // ---------------------------------------------------------------------------
@@ -1765,18 +1863,19 @@ static cudaError_t launch_sub_scan(qed_ctx *c, int64_t *ph_n, int64_t ph_cap, cu
   return cudaGetLastError();
 }
 
-// Emission: the streaming pass finishes the particles with one sub-step and
-// no event and classes the rest; the class list orders them (class 1 first,
-// each class in particle order); the single-event pass appends the class-1
-// photons; the counting and writing sub-step passes append those of classes
-// 2-5 after them.
+// Emission: the streaming pass finishes the particles that surely have one
+// sub-step and no event and classes the rest; the class list orders them
+// (class 1 first, each class in particle order); the counting pass, the scan
+// and the writing pass append their photons in that order.
 template <class Real, int FM, int MODE>
 static cudaError_t launch_lepton_t(qed_ctx *c, const LeptonArgs<Real> &a, cudaStream_t st) {
   if (MODE == MODE_PUSH) return launch_push<Real, FM>(c, a, st);
   cudaError_t e = launch_tables_kernel<Real>(c, k_lepton_stream<Real, FM, MODE>, a, false, st);
   if (e == cudaSuccess) e = launch_class_lists(c, a.sp[0].d_n, a.nsp > 1 ? a.sp[1].d_n : nullptr, st);
-  if (e == cudaSuccess) e = launch_tables_kernel<Real>(c, k_lepton_emit1<Real, FM, MODE>, a, a.use_mlp, st);
-  if (e == cudaSuccess) e = launch_tables_kernel<Real>(c, k_substep_count<Real, FM, MODE>, a, false, st);
+  if (e == cudaSuccess)
+    e = a.use_mlp && sizeof(Real) == 4
+            ? launch_tables_kernel<Real>(c, k_substep_count<Real, FM, MODE, true>, a, true, st)
+            : launch_tables_kernel<Real>(c, k_substep_count<Real, FM, MODE, false>, a, false, st);
   if (e == cudaSuccess) e = launch_sub_scan(c, a.ph.d_n, a.ph.cap, st);
   if (e == cudaSuccess) e = launch_tables_kernel<Real>(c, k_substep_write<Real, FM, MODE>, a, false, st);
   return e;
@@ -1886,6 +1985,42 @@ cudaError_t launch_compact(qed_ctx *c, const qed_species *s, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <class Real>
+cudaError_t launch_compact_fill(qed_ctx *c, const qed_species *s, cudaStream_t st) {
+  FillArgs<Real> a{};
+  a.s = to_sp<Real>(s);
+  a.chunk_alive = c->cls_chunk_cnt;
+  a.chunk_off = c->cls_chunk_off;
+  a.meta = c->fill_meta;
+  a.holes = c->heavy_list;
+  FillArgs<float> af{};  // the scan reads only the shared scratch
+  af.chunk_alive = a.chunk_alive;
+  af.chunk_off = a.chunk_off;
+  af.meta = a.meta;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fill_count<Real>, TILE, 0);
+  if (e != cudaSuccess) return e;
+  const int grid = c->num_sms * (per_sm > 0 ? per_sm : 1);
+  k_fill_count<Real><<<grid, TILE, 0, st>>>(a);
+  k_fill_scan<<<1, CLS_SCAN_THREADS, 0, st>>>(s->alive, s->d_n, af);
+  k_fill_holes<Real><<<grid, TILE, 0, st>>>(a);
+  k_fill_move<Real><<<grid, TILE, 0, st>>>(a);
+  c->launches += 4;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_count_alive(qed_ctx *c, const qed_species *s, int64_t *out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(int64_t), st);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_count_alive, TILE, 0);
+  if (e != cudaSuccess) return e;
+  k_count_alive<<<c->num_sms * (per_sm > 0 ? per_sm : 1), TILE, 0, st>>>(
+      s->alive, s->d_n, reinterpret_cast<unsigned long long *>(out));
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_snapshot(qed_ctx *c, const int64_t *src, int64_t *dst, cudaStream_t st) {
   k_snapshot<<<1, 1, 0, st>>>(src, dst);
   c->launches += 1;
@@ -1955,6 +2090,8 @@ template cudaError_t launch_photon<double>(qed_ctx *, const qed_species *, const
                                            int64_t, cudaStream_t);
 template cudaError_t launch_compact<float>(qed_ctx *, const qed_species *, cudaStream_t);
 template cudaError_t launch_compact<double>(qed_ctx *, const qed_species *, cudaStream_t);
+template cudaError_t launch_compact_fill<float>(qed_ctx *, const qed_species *, cudaStream_t);
+template cudaError_t launch_compact_fill<double>(qed_ctx *, const qed_species *, cudaStream_t);
 template cudaError_t launch_eval<float>(qed_ctx *, int, int, const double *, const double *,
                                         const uint32_t *, double *, int64_t, cudaStream_t);
 template cudaError_t launch_eval<double>(qed_ctx *, int, int, const double *, const double *,

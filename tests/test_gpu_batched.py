@@ -48,9 +48,9 @@ def test_graph_replay_equals_eager_steps(api):
     ctx_b = api.qed_init_tables(api.config(dt=0.02, seed=9))
     ea, pa, ga = _species(api, st, n)
     eb, pb, gb = _species(api, st, n)
-    for k in range(6):  # eager: fused step + photon compaction
+    for k in range(6):  # eager: fused step + photon compaction by hole filling
         api.qed_step_fused(ctx_a, ea, pa, ga, F, 10 + k)
-        api.qed_compact(ctx_a, ga)
+        api.qed_compact_fill(ctx_a, ga)
     counts = api.qed_run_batched(ctx_b, eb, pb, gb, F, 10, 3, n_runs=len(sizes))
     api.qed_run_batched(ctx_b, eb, pb, gb, F, 13, 3)  # replays the cached graph
     torch.cuda.synchronize()
