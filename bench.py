@@ -38,6 +38,10 @@ N_PART = 1 << 26
 DT = 0.01
 COMPACT_EVERY = 4  # dead photons (pair conversions) are removed every this many steps
 LEPTON_BYTES = 84       # R x,y,z,px,py,pz,w (28) + id (8) + E,B (24); W x,y,z,px,py,pz (24)
+LEPTON_STREAM_BYTES = 81  # streaming pass alone: R x..pz, id, E,B (56); W x..pz (24) + class flag (1)
+# DRAM bytes (read + write) per lepton of one lepton step, from an ncu capture of
+# the lepton-step kernels (None when the kernels changed since it was taken)
+LEPTON_TRAFFIC_PER_LEPTON = 183.0
 PHOTON_APPEND_BYTES = 61  # x,y,z,px,py,pz,w (28) + id (8) + alive (1) + inherited E,B (24)
 PHOTON_BYTES = 85       # photon step: R 28+8+1+24, W x,y,z (12) [+ alive on pair]
 
@@ -410,7 +414,9 @@ def main():
     clocks = clk.stop()
     launches = ctx.launches - launches0
     ms = t0.elapsed_time(t1)
-    lep_ms, pho_ms, nprof = api.qed_profile_end(ctx)
+    phases, nprof = api.qed_profile_end_phases(ctx)
+    lep_ms = sum(phases[k] for k in api.PROF_PHASES[:5])
+    pho_ms = phases["photon_stream"] + phases["photon_ordered"]
     c_after = api.qed_read_counters(ctx)
     cnt = counts.cpu().numpy()
     ps_local = float(cnt[:, 0].sum() + cnt[:, 1].sum())
@@ -420,17 +426,33 @@ def main():
         t_max, ps_total = reduce_over_ranks(dist, ms, ps_local, "cuda")
     value = ps_total / (t_max * 1e-3)
 
-    # roofline of the dominant (lepton) kernel: algorithmic bytes / event time
+    # roofline of the lepton step (the per-lepton unit whose algorithmic bytes
+    # are 84 B + 61 B per emitted photon): its five phases (streaming pass,
+    # class list, counting pass, scan, writing pass) are timed by CUDA events
+    # recorded on the launching stream between them
     emitted = c_after["emit_events"] - c_before["emit_events"]
-    lep_bytes = (LEPTON_BYTES * cnt[:, 0].sum() + PHOTON_APPEND_BYTES * emitted) / max(nprof, 1)
+    deferred = c_after["deferred"] - c_before["deferred"]
+    leptons = float(cnt[:, 0].sum())
+    lep_bytes = (LEPTON_BYTES * leptons + PHOTON_APPEND_BYTES * emitted) / max(nprof, 1)
     lep_t = lep_ms / max(nprof, 1) * 1e-3
     peak, peak_kind = peaks()
     achieved = lep_bytes / lep_t / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_lepton (fused gather/push/emission)",
+    traffic = None
+    if LEPTON_TRAFFIC_PER_LEPTON is not None:
+        traffic = LEPTON_TRAFFIC_PER_LEPTON * leptons / max(nprof, 1)
+    roofline = {"bound": "hbm",
+                "kernel": "lepton step: k_lepton_stream + k_cls_count/scan/scatter + "
+                          "k_substep_count + k_sub_scan + k_substep_write",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": f"{peak_kind} HBM copy", "traffic": None,
-                "bytes_per_launch": lep_bytes, "ms_per_launch": lep_t * 1e3,
+                "peak_source": f"{peak_kind} HBM copy (MEASURED_PEAKS.json hbm_gbs)",
+                "traffic": traffic, "bytes_per_launch": lep_bytes, "ms_per_launch": lep_t * 1e3,
                 "lepton_share_of_step": lep_ms / max(ms, 1e-9),
+                "phases_ms_per_step": {k: v / max(nprof, 1) for k, v in phases.items()},
+                "deferred_fraction": deferred / max(leptons, 1.0),
+                "streaming_pass": {
+                    "bytes_per_launch": LEPTON_STREAM_BYTES * leptons / max(nprof, 1),
+                    "achieved_gbs": LEPTON_STREAM_BYTES * leptons / max(nprof, 1)
+                                    / (phases["lepton_stream"] / max(nprof, 1) * 1e-3) / 1e9},
                 "photon_kernel_ms_per_launch": pho_ms / max(nprof, 1)}
 
     # e2e: the same steps with the state on the host (pinned), copied in and out
@@ -504,6 +526,7 @@ def main():
                          "pair_events": c_after["pair_events"] - c_before["pair_events"],
                          "substeps": c_after["substeps"] - c_before["substeps"],
                          "dropped": c_after["dropped"], "domain": c_after["domain"],
+                         "deferred": deferred,
                          "status": status,
                          "particles_at_end": {"leptons": int(cnt[-1, 0]), "photons": int(cnt[-1, 1])}}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

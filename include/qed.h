@@ -145,6 +145,8 @@ typedef struct {
   uint32_t status;      /* QED_STATUS_* bits */
   uint32_t pad_;
   int64_t hist[64];     /* emitted-photon energies, 64 log bins over [spec_lo, spec_hi) */
+  int64_t deferred;     /* leptons the streaming pass left to the emission passes
+                           (an event possible or N > 1) */
 } qed_counters;
 
 const char *qed_strerror(int code);
@@ -286,12 +288,19 @@ int qed_autotune(qed_ctx *ctx, const qed_species *e, const qed_species *p, const
 
 /* Measurement hooks.  qed_profile_begin creates CUDA events (call it outside
  * any timed or captured region) so that each of the next max_steps calls of
- * qed_step_fused records events on its stream around its lepton kernel and
- * its photon kernel.  qed_profile_end synchronises, returns the summed
- * milliseconds of each kernel and the number of steps recorded, and releases
- * the events. */
+ * qed_step_fused records events on its stream between its phases:
+ *   0 lepton streaming pass      1 lepton class list (3 launches)
+ *   2 lepton counting pass       3 scan of the photon counts
+ *   4 lepton writing pass        5 photon streaming pass
+ *   6 photon list + ordered pass
+ * qed_profile_end synchronises, returns the summed milliseconds of the
+ * lepton stage (phases 0-4) and of the photon stage (5-6) and the number of
+ * steps recorded, and releases the events; qed_profile_end_phases does the
+ * same with the summed milliseconds of each phase in ms[0..QED_PROF_PHASES-1]. */
+enum { QED_PROF_PHASES = 7 };
 int qed_profile_begin(qed_ctx *ctx, int max_steps);
 int qed_profile_end(qed_ctx *ctx, double *lepton_ms, double *photon_ms, int64_t *steps);
+int qed_profile_end_phases(qed_ctx *ctx, double *ms, int64_t *steps);
 
 /* Allocation-free stable compaction (no counterpart in the paper; it is a
  * service for callers that cannot allocate device memory -- an application

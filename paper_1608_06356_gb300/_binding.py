@@ -20,6 +20,7 @@ MLP_NP = 8577
 QED_FIELDS_UNIFORM, QED_FIELDS_PER_PARTICLE, QED_FIELDS_GRID = 0, 1, 2
 QED_STATUS_CAPACITY, QED_STATUS_DOMAIN, QED_STATUS_NONFINITE = 1, 2, 4
 QED_STATUS_TIMEOUT, QED_STATUS_SUBSTEPS, QED_STATUS_REPLAY = 8, 16, 32
+QED_PROF_PHASES = 7
 
 ERRORS = {-1: "QED_ERR_ARG", -2: "QED_ERR_CUDA", -3: "QED_ERR_CAPACITY", -4: "QED_ERR_DOMAIN",
           -5: "QED_ERR_TIMEOUT", -6: "QED_ERR_NOCONV", -7: "QED_ERR_NOMEM", -8: "QED_ERR_UNSUPPORTED"}
@@ -61,12 +62,12 @@ class qed_fields(C.Structure):
 class qed_counters(C.Structure):
     _fields_ = [("emit_events", C.c_int64), ("pair_events", C.c_int64), ("substeps", C.c_int64),
                 ("dropped", C.c_int64), ("domain", C.c_int64), ("status", C.c_uint32),
-                ("pad_", C.c_uint32), ("hist", C.c_int64 * 64)]
+                ("pad_", C.c_uint32), ("hist", C.c_int64 * 64), ("deferred", C.c_int64)]
 
     def as_dict(self):
         return {"emit_events": self.emit_events, "pair_events": self.pair_events,
                 "substeps": self.substeps, "dropped": self.dropped, "domain": self.domain,
-                "status": self.status, "hist": list(self.hist)}
+                "status": self.status, "hist": list(self.hist), "deferred": self.deferred}
 
 
 # name -> (restype, argtypes); the exported C ABI, one entry per declaration
@@ -109,6 +110,7 @@ SIGNATURES = {
     "qed_mlp_grad": (C.c_int, [_P, _P, _P, C.c_int64, _P, C.POINTER(C.c_double), _P]),
     "qed_profile_end": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                   C.POINTER(C.c_int64)]),
+    "qed_profile_end_phases": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
 }
 
 _lib = None

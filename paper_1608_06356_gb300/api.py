@@ -315,6 +315,18 @@ def qed_profile_end(ctx: Context) -> tuple[float, float, int]:
     return a.value, b.value, n.value
 
 
+PROF_PHASES = ("lepton_stream", "lepton_class_list", "lepton_count", "photon_count_scan",
+               "lepton_write", "photon_stream", "photon_ordered")
+
+
+def qed_profile_end_phases(ctx: Context) -> tuple[dict, int]:
+    """({phase name: summed ms}, steps recorded)."""
+    ms = (C.c_double * B.QED_PROF_PHASES)()
+    n = C.c_int64()
+    B.check(B.lib().qed_profile_end_phases(ctx.handle, ms, C.byref(n)), "qed_profile_end_phases")
+    return dict(zip(PROF_PHASES, list(ms))), n.value
+
+
 def qed_mlp_load(ctx: Context, weights) -> None:
     w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32))
     B.check(B.lib().qed_mlp_load(ctx.handle, w.ctypes.data, w.size), "qed_mlp_load")

@@ -89,7 +89,7 @@ static void free_ctx(qed_ctx *c) {
 
 static void prof_release(qed_ctx *c) {
   if (!c->prof_ev) return;
-  for (int i = 0; i < 3 * c->prof_max; ++i) cudaEventDestroy(c->prof_ev[i]);
+  for (int i = 0; i < PROF_MARKS * c->prof_max; ++i) cudaEventDestroy(c->prof_ev[i]);
   free(c->prof_ev);
   c->prof_ev = nullptr;
   c->prof_max = c->prof_n = 0;
@@ -108,13 +108,15 @@ extern "C" void qed_destroy(qed_ctx *c) {
 extern "C" int qed_profile_begin(qed_ctx *c, int max_steps) {
   if (!c || max_steps <= 0 || max_steps > 100000) return QED_ERR_ARG;
   prof_release(c);
-  c->prof_ev = (cudaEvent_t *)calloc((size_t)3 * max_steps, sizeof(cudaEvent_t));
+  c->prof_ev = (cudaEvent_t *)calloc((size_t)PROF_MARKS * max_steps, sizeof(cudaEvent_t));
   if (!c->prof_ev) return QED_ERR_NOMEM;
-  for (int i = 0; i < 3 * max_steps; ++i) {
+  for (int i = 0; i < PROF_MARKS * max_steps; ++i) {
     cudaError_t e = cudaEventCreate(&c->prof_ev[i]);
     if (e != cudaSuccess) {
-      c->prof_max = i / 3;
-      prof_release(c);
+      for (int j = 0; j < i; ++j) cudaEventDestroy(c->prof_ev[j]);
+      free(c->prof_ev);
+      c->prof_ev = nullptr;
+      c->prof_max = c->prof_n = 0;
       return cuda_fail(e, "qed_profile_begin");
     }
   }
@@ -123,22 +125,30 @@ extern "C" int qed_profile_begin(qed_ctx *c, int max_steps) {
   return QED_OK;
 }
 
-extern "C" int qed_profile_end(qed_ctx *c, double *lepton_ms, double *photon_ms, int64_t *steps) {
-  if (!c || !c->prof_ev) return QED_ERR_ARG;
-  double tl = 0.0, tp = 0.0;
+extern "C" int qed_profile_end_phases(qed_ctx *c, double *ms, int64_t *steps) {
+  if (!c || !c->prof_ev || !ms) return QED_ERR_ARG;
+  for (int q = 0; q < QED_PROF_PHASES; ++q) ms[q] = 0.0;
   for (int k = 0; k < c->prof_n; ++k) {
-    float a = 0.f, b = 0.f;
-    cudaError_t e = cudaEventSynchronize(c->prof_ev[3 * k + 2]);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&a, c->prof_ev[3 * k], c->prof_ev[3 * k + 1]);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, c->prof_ev[3 * k + 1], c->prof_ev[3 * k + 2]);
+    cudaEvent_t *ev = c->prof_ev + PROF_MARKS * k;
+    cudaError_t e = cudaEventSynchronize(ev[QED_PROF_PHASES]);
+    for (int q = 0; q < QED_PROF_PHASES && e == cudaSuccess; ++q) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, ev[q], ev[q + 1]);
+      ms[q] += t;
+    }
     if (e != cudaSuccess) { prof_release(c); return cuda_fail(e, "qed_profile_end"); }
-    tl += a;
-    tp += b;
   }
-  if (lepton_ms) *lepton_ms = tl;
-  if (photon_ms) *photon_ms = tp;
   if (steps) *steps = c->prof_n;
   prof_release(c);
+  return QED_OK;
+}
+
+extern "C" int qed_profile_end(qed_ctx *c, double *lepton_ms, double *photon_ms, int64_t *steps) {
+  double ms[QED_PROF_PHASES];
+  int rc = qed_profile_end_phases(c, ms, steps);
+  if (rc != QED_OK) return rc;
+  if (lepton_ms) *lepton_ms = ms[0] + ms[1] + ms[2] + ms[3] + ms[4];
+  if (photon_ms) *photon_ms = ms[5] + ms[6];
   return QED_OK;
 }
 
@@ -358,20 +368,18 @@ extern "C" int qed_step_fused(qed_ctx *c, const qed_species *e, const qed_specie
   cudaStream_t st = (cudaStream_t)stream;
   const bool f64 = c->cfg.precision == QED_FP64;
   const bool prof = c->prof_ev && c->prof_n < c->prof_max;
-  cudaEvent_t *ev = prof ? c->prof_ev + 3 * c->prof_n : nullptr;
+  c->prof_cur = prof ? c->prof_ev + PROF_MARKS * c->prof_n : nullptr;
   cudaError_t err = launch_snapshot(c, g->d_n, c->snap, st);
-  if (err == cudaSuccess && prof) err = cudaEventRecord(ev[0], st);
-  if (err == cudaSuccess)
+  if (err == cudaSuccess) err = prof_mark(c, 0, st);
+  if (err == cudaSuccess)  // marks 1-5 inside
     err = f64 ? launch_lepton<double>(c, e, p, g, f, step, MODE_FUSED_, st)
               : launch_lepton<float>(c, e, p, g, f, step, MODE_FUSED_, st);
-  if (err == cudaSuccess && prof) err = cudaEventRecord(ev[1], st);
-  if (err == cudaSuccess)
+  if (err == cudaSuccess)  // mark 6 inside
     err = f64 ? launch_photon<double>(c, g, e, p, c->snap, f, step, st)
               : launch_photon<float>(c, g, e, p, c->snap, f, step, st);
-  if (err == cudaSuccess && prof) {
-    err = cudaEventRecord(ev[2], st);
-    c->prof_n += 1;
-  }
+  if (err == cudaSuccess) err = prof_mark(c, QED_PROF_PHASES, st);
+  if (err == cudaSuccess && prof) c->prof_n += 1;
+  c->prof_cur = nullptr;
   return cuda_fail(err, "qed_step_fused");
 }
 

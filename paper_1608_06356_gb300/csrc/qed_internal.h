@@ -67,8 +67,9 @@ struct qed_ctx {
   // persistent-grid occupancy factor (0 = as many CTAs per SM as fit)
   int grid_factor;
   // measurement hooks (qed_profile_begin/end): 3 events per profiled step
-  cudaEvent_t *prof_ev;
+  cudaEvent_t *prof_ev;   // QED_PROF_MARKS events per profiled step
   int prof_max, prof_n;
+  cudaEvent_t *prof_cur;  // the current fused step's events while it is launched, else null
 };
 
 namespace qed {
@@ -80,6 +81,14 @@ inline int persistent_blocks_per_sm(const qed_ctx *c, int occupancy) {
   int b = occupancy < 1 ? 1 : occupancy;
   if (c->grid_factor > 0 && c->grid_factor < b) b = c->grid_factor;
   return b;
+}
+// Event marks of a profiled fused step: 0 start, 1 after the lepton
+// streaming pass, 2 after the class list, 3 after the counting pass, 4 after
+// the scan, 5 after the writing pass (lepton stage done), 6 after the photon
+// streaming pass, 7 after the photon stage.
+constexpr int PROF_MARKS = QED_PROF_PHASES + 1;
+inline cudaError_t prof_mark(qed_ctx *c, int k, cudaStream_t st) {
+  return c->prof_cur ? cudaEventRecord(c->prof_cur[k], st) : cudaSuccess;
 }
 constexpr int TILE = 256;  // particles per tile = threads per block in the step kernels
 constexpr int SUB_REC = 4; // emission records kept per particle by the sub-step counting pass

@@ -640,7 +640,8 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 && !MLP ? 3 : 2) k_sub
       const Real kap = ev ? photon_kappa(ro.kmin, unif<Real>(wy), unif<Real>(~wy)) : (Real)0;
       Real Y = (Real)0;
       bool in_mlp = false;
-      if (use_mlp) {
+      // (only rounds in which some lane has N = 1 run the network)
+      if (use_mlp && __any_sync(0xFFFFFFFFu, ev && N == 1)) {
         const float lchi = chi > (Real)0 ? (float)m_log(chi) : MLP_L_LO - 1.0f;
         in_mlp = ev && N == 1 && lchi >= MLP_L_LO && lchi <= MLP_L_HI && (float)kap >= MLP_K_LO &&
                  (float)kap <= MLP_K_HI;
@@ -937,6 +938,7 @@ struct ClassListArgs {
   int64_t *off;                   // [NCLS + 1]
   const int32_t *stage_idx;       // [slot] staging record of a flagged slot (-1: none)
   unsigned int *stage_n;          // staging counter, reset by the scan for the next step
+  qed_counters *cnt;              // deferred += list length
 };
 
 __device__ __forceinline__ int64_t cls_nslots(const ClassListArgs &A) {
@@ -1037,6 +1039,7 @@ __global__ void __launch_bounds__(CLS_SCAN_THREADS) k_cls_scan(ClassListArgs A) 
       b += (int64_t)tot[k];
     }
     A.off[NCLS] = b;
+    if (b) atomicAdd(reinterpret_cast<unsigned long long *>(&A.cnt->deferred), (unsigned long long)b);
   }
   __syncthreads();
   // per-class running prefix over chunks; each round a thread takes
@@ -1835,6 +1838,7 @@ static cudaError_t launch_class_lists(qed_ctx *c, const int64_t *n0, const int64
   a.off = c->cls_off;
   a.stage_idx = c->stage_idx;
   a.stage_n = c->stage_n;
+  a.cnt = c->d_counters;
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cls_count, TILE, 0);
   if (e != cudaSuccess) return e;
@@ -1871,13 +1875,18 @@ template <class Real, int FM, int MODE>
 static cudaError_t launch_lepton_t(qed_ctx *c, const LeptonArgs<Real> &a, cudaStream_t st) {
   if (MODE == MODE_PUSH) return launch_push<Real, FM>(c, a, st);
   cudaError_t e = launch_tables_kernel<Real>(c, k_lepton_stream<Real, FM, MODE>, a, false, st);
+  if (e == cudaSuccess) e = prof_mark(c, 1, st);
   if (e == cudaSuccess) e = launch_class_lists(c, a.sp[0].d_n, a.nsp > 1 ? a.sp[1].d_n : nullptr, st);
+  if (e == cudaSuccess) e = prof_mark(c, 2, st);
   if (e == cudaSuccess)
     e = a.use_mlp && sizeof(Real) == 4
             ? launch_tables_kernel<Real>(c, k_substep_count<Real, FM, MODE, true>, a, true, st)
             : launch_tables_kernel<Real>(c, k_substep_count<Real, FM, MODE, false>, a, false, st);
+  if (e == cudaSuccess) e = prof_mark(c, 3, st);
   if (e == cudaSuccess) e = launch_sub_scan(c, a.ph.d_n, a.ph.cap, st);
+  if (e == cudaSuccess) e = prof_mark(c, 4, st);
   if (e == cudaSuccess) e = launch_tables_kernel<Real>(c, k_substep_write<Real, FM, MODE>, a, false, st);
+  if (e == cudaSuccess) e = prof_mark(c, 5, st);
   return e;
 }
 
@@ -1937,6 +1946,7 @@ static cudaError_t launch_photon_t(qed_ctx *c, const PhotonArgs<Real> &a, cudaSt
   k_photon_stream<Real, FM><<<c->num_sms * per_sm, TILE, sm, st>>>(a);
   c->launches += 1;
   e = cudaGetLastError();
+  if (e == cudaSuccess) e = prof_mark(c, 6, st);
   if (e == cudaSuccess) e = launch_flag_list(c, a.flags, 1, a.n_active, nullptr, a.o, st);
   if (e != cudaSuccess) return e;
   auto kern = k_photon<Real, FM, 1>;
