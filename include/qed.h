@@ -90,7 +90,7 @@ typedef struct {
   uint64_t seed;        /* Philox4x32-10 key */
   double spec_lo, spec_hi; /* photon-energy histogram: 64 log bins over [spec_lo, spec_hi) m c^2 */
   int64_t max_particles;   /* largest per-species capacity any call will use (sizes scan
-                              state and the sub-step scratch, about 70 (FP32) or 110
+                              state and the sub-step scratch, about 80 (FP32) or 120
                               (FP64) bytes per particle); default 2^24, at most
                               2^30 - 4096 */
   int64_t max_substeps;    /* cap on N per particle per step (status bit when hit) */

@@ -80,7 +80,8 @@ static void free_ctx(qed_ctx *c) {
                   c->P32, c->Yp32, c->tile_state, c->sync, c->snap, c->d_counters,
                   c->heavy_flags, c->heavy_list, c->heavy_n, c->cls_chunk_cnt,
                   c->cls_chunk_off, c->cls_off, c->sub_cnt, c->sub_gf, c->rec_e,
-                  c->rec_k, c->sub_meta, c->fill_meta, c->stage, c->stage_tag, c->stage_idx, c->stage_n,
+                  c->rec_k, c->sub_meta, c->fill_meta, c->replay_n, c->stage, c->stage_tag,
+                  c->stage_idx, c->stage_n,
                   c->mlp_mem};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -239,7 +240,8 @@ extern "C" int qed_init_tables(const qed_config *cfg, qed_ctx **out, qed_stream_
       cudaMalloc(&c->stage_idx, sizeof(int32_t) * (size_t)c->heavy_slots) != cudaSuccess ||
       cudaMalloc(&c->stage_n, sizeof(unsigned int)) != cudaSuccess ||
       cudaMalloc(&c->sub_meta, 2 * sizeof(int64_t)) != cudaSuccess ||
-      cudaMalloc(&c->fill_meta, 2 * sizeof(int64_t)) != cudaSuccess) {
+      cudaMalloc(&c->fill_meta, 2 * sizeof(int64_t)) != cudaSuccess ||
+      cudaMalloc(&c->replay_n, sizeof(unsigned int)) != cudaSuccess) {
     free_ctx(c);
     return QED_ERR_NOMEM;
   }

@@ -40,6 +40,7 @@ struct qed_ctx {
   int64_t rec_cap;
   int64_t *sub_meta;  // [2] photons of the sub-step entries, photon count before them
   int64_t *fill_meta; // [2] count before and after a hole-filling compaction
+  unsigned int *replay_n;  // entries the writing pass leaves to its replay launch
   // staging records of the flagged leptons (streaming pass -> later passes)
   void *stage;          // Stage<Real> [stage_cap] (64 B FP32, 128 B FP64)
   uint32_t *stage_tag;  // [stage_cap]
@@ -91,6 +92,6 @@ inline cudaError_t prof_mark(qed_ctx *c, int k, cudaStream_t st) {
   return c->prof_cur ? cudaEventRecord(c->prof_cur[k], st) : cudaSuccess;
 }
 constexpr int TILE = 256;  // particles per tile = threads per block in the step kernels
-constexpr int SUB_REC = 4; // emission records kept per particle by the sub-step counting pass
+constexpr int SUB_REC = 8; // emission records kept per particle by the sub-step counting pass
 constexpr int CLS_CHUNK_FLAGS = 2048;  // flags per chunk of the class-list passes
 }  // namespace qed

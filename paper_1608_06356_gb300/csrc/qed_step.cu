@@ -223,6 +223,8 @@ template <class Real> struct LeptonArgs {
   uint32_t *rec_k;          // [REC][rec_cap] their sub-step indices
   int64_t rec_cap;
   const int64_t *sub_meta;  // [0] photons of the sub-step entries, [1] photon count before them
+  int32_t *replay_list;     // entries whose chains the replay launch redoes
+  unsigned int *replay_n;   // their number (reset by the scan)
   const uint32_t *mlp_frag; // learned inverse CDF (used when use_mlp)
   const float *mlp_w;
   int use_mlp;
@@ -686,6 +688,7 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 && !MLP ? 3 : 2) k_sub
 // the new photon count.
 struct SubScanArgs {
   uint32_t *cnt;
+  unsigned int *replay_n;  // reset here for the writing pass
   const int64_t *cls_off;
   int64_t *sub_meta;
   int64_t *ph_n;
@@ -708,9 +711,12 @@ __global__ void __launch_bounds__(TILE) k_sub_scan(SubScanArgs A) {
   const int64_t per_tile = (int64_t)TILE * SCAN_ITEMS;
   const int64_t ntiles = (nh + per_tile - 1) / per_tile;
   uint32_t status = 0;
-  if (ntiles == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
-    A.sub_meta[0] = 0;
-    A.sub_meta[1] = nph;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *A.replay_n = 0u;
+    if (ntiles == 0) {
+      A.sub_meta[0] = 0;
+      A.sub_meta[1] = nph;
+    }
   }
   for (;;) {
     if (threadIdx.x == 0) s_meta[0] = (long long)atomicAdd(&A.o.scan.sync[0], 1u);
@@ -752,16 +758,21 @@ __global__ void __launch_bounds__(TILE) k_sub_scan(SubScanArgs A) {
   launch_epilogue(A.o.scan, epoch);
 }
 
-template <class Real, int FM, int MODE>
-__global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 3 : 2) k_substep_write(LeptonArgs<Real> A) {
+// REPLAY = false: every particle whose photons are all in its records; it
+// lists the others (more than REC photons, or past the record capacity, both
+// rare), whose chains the REPLAY = true launch redoes -- separately, so that
+// the common case carries neither the tables nor the chain's registers, and
+// densely, so that the rare long replays share warps.
+template <class Real, int FM, int MODE, bool REPLAY>
+__global__ void __launch_bounds__(TILE, REPLAY || sizeof(Real) == 8 ? 2 : 4) k_substep_write(LeptonArgs<Real> A) {
   const int64_t step_ = A.d_step ? *A.d_step : A.step;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr bool kSmem = sizeof(Real) == 4;
+  constexpr bool kSmem = sizeof(Real) == 4 && REPLAY;
   Real *sR = kSmem ? reinterpret_cast<Real *>(smem_raw) : const_cast<Real *>(A.T.R);
   Real *sF = kSmem ? sR + A.T.gl.n : const_cast<Real *>(A.T.F);
   __shared__ long long s_meta[5];
   __shared__ BlockTally bt;
-  if (kSmem) {  // for replays
+  if (kSmem) {
     load_tables_smem(sR, A.T.R, A.T.gl.n);
     load_tables_smem(sF, A.T.F, A.T.gl.n * A.T.gy.n);
   }
@@ -782,12 +793,19 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 3 : 2) k_substep_wri
   const Real dt = sel<Real>(A.C.dt, A.C.f_dt);
   const Real wdt_max = sel<Real>(A.C.wdt_max, A.C.f_wdt_max);
   const int64_t rc = A.rec_cap;
+  // the replay launch runs over the entries the first launch listed
+  const int64_t n_iter = REPLAY ? (int64_t)*(volatile unsigned int *)A.replay_n : nh;
   Tally tl;
   tl.clear();
-  for (int64_t h = blockIdx.x * (int64_t)TILE + threadIdx.x; h < nh; h += (int64_t)gridDim.x * TILE) {
+  for (int64_t q = blockIdx.x * (int64_t)TILE + threadIdx.x; q < n_iter; q += (int64_t)gridDim.x * TILE) {
+    const int64_t h = REPLAY ? (int64_t)A.replay_list[q] : q;
     // sub_cnt holds the exclusive prefix of the counts now
     const uint32_t off = A.sub_cnt[h];
     const uint32_t cnt = (h + 1 < nh ? A.sub_cnt[h + 1] : total) - off;
+    if (!REPLAY && cnt > 0 && (cnt > REC || h >= rc)) {  // its photons are not all recorded
+      A.replay_list[atomicAdd(A.replay_n, 1u)] = (int32_t)h;
+      continue;
+    }
     const int32_t e = A.heavy_list[begin + h];
     if (cnt == 0 && e >= 0) continue;  // staged, no photon: the streaming pass stored it
     const int64_t out0 = nph + (int64_t)off;
@@ -811,7 +829,7 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 3 : 2) k_substep_wri
       write_child(A.ph, out, P.x, P.y, P.z, eph * nx, eph * ny, eph * nz, P.w,
                   (uint64_t)cid.x | ((uint64_t)cid.y << 32), P.E, P.B, P.tag);
     };
-    if (cnt <= REC && h < rc) {
+    if (!REPLAY) {
       for (uint32_t j = 0; j < cnt; ++j) put(j, A.rec_e[j * rc + h], (int64_t)A.rec_k[j * rc + h]);
       g = A.sub_gf[h];
     } else {
@@ -855,6 +873,7 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 3 : 2) k_substep_wri
 struct HeavyListArgs {
   const uint8_t *flags;
   uint8_t want;  // flag value to collect
+  const int32_t *stage_idx;  // if set: list the staging record (or -(slot + 1))
   int *list;
   int64_t *count;
   const int64_t *n0, *n1;  // species counts (sizes the main pass's slot range)
@@ -908,7 +927,12 @@ __global__ void __launch_bounds__(TILE) k_heavy_list(HeavyListArgs A) {
     while (mask) {
       int j = __ffs(mask) - 1;
       mask &= mask - 1;
-      A.list[out++] = (int)(first + j);
+      int v = (int)(first + j);
+      if (A.stage_idx) {
+        const int32_t sidx = A.stage_idx[first + j];
+        v = sidx >= 0 ? sidx : -v - 1;
+      }
+      A.list[out++] = v;
     }
   }
   if (threadIdx.x == 0 && status) atomicOr(&A.o.cnt->status, status);
@@ -1123,7 +1147,12 @@ template <class Real> struct PhotonArgs {
   Out o;
   int64_t step;
   uint8_t *flags;       // streaming pass: 1 = redo in the ordered pass
-  const int *list;      // ordered pass: photon indices to process
+  const int *list;      // ordered pass: staging record (>= 0) or -(index + 1)
+  Stage<Real> *stage;   // pushed state of the flagged photons (streaming pass)
+  uint32_t *stage_tag;
+  int32_t *stage_idx;   // [index] staging record of a flagged photon, -1 if not staged
+  unsigned int *stage_n;
+  int64_t stage_cap;
   const int64_t *list_n;
   const int64_t *d_step;  // if set, the step index is read here (graph replay)
 };
@@ -1135,7 +1164,7 @@ template <class Real> struct PhotonArgs {
 // from their stored state by the ordered pass (k_photon over the list).
 // ---------------------------------------------------------------------------
 template <class Real, int FM>
-__global__ void __launch_bounds__(TILE) k_photon_stream(PhotonArgs<Real> A) {
+__global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 4 : 2) k_photon_stream(PhotonArgs<Real> A) {
   const int64_t step_ = A.d_step ? *A.d_step : A.step;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real *sP = reinterpret_cast<Real *>(smem_raw);
@@ -1149,15 +1178,20 @@ __global__ void __launch_bounds__(TILE) k_photon_stream(PhotonArgs<Real> A) {
   const int64_t nslots = (n + TILE - 1) / TILE * TILE;
   const Real inv_aS = sel<Real>(A.C.inv_aS, A.C.f_inv_aS);
   const Real dt = sel<Real>(A.C.dt, A.C.f_dt), wdt_max = sel<Real>(A.C.wdt_max, A.C.f_wdt_max);
+  const int lane = threadIdx.x & 31;
+  uint32_t batch_base = 0, batch_used = STAGE_BATCH;  // this warp's staging batch
   Tally tl;
   tl.clear();
+  // nslots is a multiple of TILE: every lane of a warp runs the same iterations
   for (int64_t i = blockIdx.x * (int64_t)TILE + threadIdx.x; i < nslots;
        i += (int64_t)gridDim.x * TILE) {
     uint8_t flag = 0;
+    Real x = 0, y = 0, z = 0, px = 0, py = 0, pz = 0;
+    Real E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
+    uint64_t pid = 0;
     if (i < n && A.ph.alive[i]) {
-      Real x = A.ph.x[i], y = A.ph.y[i], z = A.ph.z[i];
-      Real px = A.ph.px[i], py = A.ph.py[i], pz = A.ph.pz[i];
-      Real E[3], B[3];
+      x = A.ph.x[i]; y = A.ph.y[i]; z = A.ph.z[i];
+      px = A.ph.px[i]; py = A.ph.py[i]; pz = A.ph.pz[i];
       get_fields<Real, FM>(A.ph, A.f, i, x, y, z, E, B);
       Real k = m_sqrt(px * px + py * py + pz * pz);
       Real chi = chi_photon(px, py, pz, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
@@ -1167,21 +1201,59 @@ __global__ void __launch_bounds__(TILE) k_photon_stream(PhotonArgs<Real> A) {
       Real wdt = ro.W * dt;
       if (wdt > wdt_max) {
         flag = 1;
-      } else if (ro.W > (Real)0) {
-        U4 r = draw(A.C.seed, A.ph.id[i], step_, 0, STREAM_PAIR);
+        pid = A.ph.id[i];
+      } else if (ro.W > (Real)0) {  // (most soft photons have W = 0: no id read)
+        pid = A.ph.id[i];
+        U4 r = draw(A.C.seed, pid, step_, 0, STREAM_PAIR);
         if (wdt > unif<Real>(r.x)) flag = 1;
+      }
+      if (k > (Real)0) {
+        Real ik = dt / k;
+        x += px * ik; y += py * ik; z += pz * ik;
       }
       if (!flag) {
         tl.substeps += 1;
         tl.status |= t0.status;
         tl.domain += t0.domain;
-        if (k > (Real)0) {
-          Real ik = dt / k;
-          A.ph.x[i] = x + px * ik; A.ph.y[i] = y + py * ik; A.ph.z[i] = z + pz * ik;
-        }
+        if (k > (Real)0) { A.ph.x[i] = x; A.ph.y[i] = y; A.ph.z[i] = z; }
       }
     }
     A.flags[i] = flag;
+    // stage the flagged photons (warp-collective)
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, flag != 0);
+    if (m) {
+      const uint32_t cm = __popc(m);
+      if (batch_used + cm > STAGE_BATCH) {
+        uint32_t nb = 0;
+        if (lane == 0) nb = atomicAdd(A.stage_n, STAGE_BATCH);
+        batch_base = __shfl_sync(0xFFFFFFFFu, nb, 0);
+        batch_used = 0;
+      }
+      if (flag) {
+        const uint64_t pos = (uint64_t)batch_base + batch_used + __popc(m & ((1u << lane) - 1u));
+        int32_t sidx = -1;
+        if (pos < (uint64_t)A.stage_cap) {
+          sidx = (int32_t)pos;
+          Stage<Real> r;
+          r.p[0] = px; r.p[1] = py; r.p[2] = pz;
+          r.e[0] = E[0]; r.e[1] = E[1]; r.e[2] = E[2];
+          r.b[0] = B[0]; r.b[1] = B[1]; r.b[2] = B[2];
+          r.id_lo = (uint32_t)pid; r.id_hi = (uint32_t)(pid >> 32);
+          r.w = A.ph.w[i];
+          r.x[0] = x; r.x[1] = y; r.x[2] = z;
+          r.slot = (uint32_t)i;
+          const uint4 *src = reinterpret_cast<const uint4 *>(&r);
+          uint4 *dst = reinterpret_cast<uint4 *>(A.stage + pos);
+#pragma unroll
+          for (int q = 0; q < (int)(sizeof(Stage<Real>) / 16); ++q) dst[q] = src[q];
+          if (A.ph.tag) A.stage_tag[pos] = A.ph.tag[i];
+          // the pushed position does not depend on the pair decision
+          A.ph.x[i] = x; A.ph.y[i] = y; A.ph.z[i] = z;
+        }
+        A.stage_idx[i] = sidx;
+      }
+      batch_used += cm;
+    }
   }
   tally_flush(&bt, tl);
   __syncthreads();
@@ -1220,23 +1292,46 @@ __global__ void __launch_bounds__(TILE) k_photon(PhotonArgs<Real> A) {
     if (t >= ntiles) break;
     const int64_t h = t * TILE + threadIdx.x;
     bool active = h < n;
-    const int64_t i = LIST ? (active ? (int64_t)A.list[h] : 0) : h;
-    if (active && A.ph.alive) active = A.ph.alive[i] != 0;
+    // list entry: staging record e >= 0 (pushed state, position already
+    // stored), or -(index + 1) for a photon the staging area had no room for
+    const int32_t e = (LIST && active) ? A.list[h] : -1;
+    const bool staged = LIST && active && e >= 0;
+    int64_t i = LIST ? 0 : h;
     Real x = 0, y = 0, z = 0, px = 0, py = 0, pz = 0, wt = 0, k = 0;
     Real E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
     uint64_t pid = 0;
     uint32_t ptag = 0;
+    if (staged) {
+      Stage<Real> r;
+      const uint4 *src = reinterpret_cast<const uint4 *>(A.stage + e);
+      uint4 *dst = reinterpret_cast<uint4 *>(&r);
+#pragma unroll
+      for (int q = 0; q < (int)(sizeof(Stage<Real>) / 16); ++q) dst[q] = __ldcs(src + q);
+      px = r.p[0]; py = r.p[1]; pz = r.p[2];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) { E[c] = r.e[c]; B[c] = r.b[c]; }
+      pid = (uint64_t)r.id_lo | ((uint64_t)r.id_hi << 32);
+      wt = r.w;
+      x = r.x[0]; y = r.x[1]; z = r.x[2];
+      i = r.slot;
+      if (A.ph.tag) ptag = A.stage_tag[e];
+    } else if (LIST && active) {
+      i = -(int64_t)e - 1;
+    }
+    if (active && !staged && A.ph.alive) active = A.ph.alive[i] != 0;
     uint32_t cnt = 0;
     Real ge = 0, gp = 0;
     int64_t ks = 0;
     if (active) {
-      x = A.ph.x[i]; y = A.ph.y[i]; z = A.ph.z[i];
-      px = A.ph.px[i]; py = A.ph.py[i]; pz = A.ph.pz[i];
-      wt = A.ph.w[i]; pid = A.ph.id[i];
-      if (A.ph.tag) ptag = A.ph.tag[i];
-      get_fields<Real, FM>(A.ph, A.f, i, x, y, z, E, B);
+      if (!staged) {
+        x = A.ph.x[i]; y = A.ph.y[i]; z = A.ph.z[i];
+        px = A.ph.px[i]; py = A.ph.py[i]; pz = A.ph.pz[i];
+        wt = A.ph.w[i]; pid = A.ph.id[i];
+        if (A.ph.tag) ptag = A.ph.tag[i];
+        get_fields<Real, FM>(A.ph, A.f, i, x, y, z, E, B);
+      }
       k = m_sqrt(px * px + py * py + pz * pz);
-      if (k > (Real)0) {
+      if (!staged && k > (Real)0) {
         Real ik = dt / k;
         x += px * ik; y += py * ik; z += pz * ik;
         A.ph.x[i] = x; A.ph.y[i] = y; A.ph.z[i] = z;
@@ -1778,10 +1873,12 @@ template <class Real> size_t lepton_smem(const qed_ctx *c) {
 }
 
 static cudaError_t launch_flag_list(qed_ctx *c, const uint8_t *flags, uint8_t want, const int64_t *n0,
-                                    const int64_t *n1, const Out &o, cudaStream_t st) {
+                                    const int64_t *n1, const Out &o, const int32_t *stage_idx,
+                                    cudaStream_t st) {
   HeavyListArgs h{};
   h.flags = flags;
   h.want = want;
+  h.stage_idx = stage_idx;
   h.list = c->heavy_list;
   h.count = c->heavy_n;
   h.n0 = n0;
@@ -1825,6 +1922,19 @@ static cudaError_t launch_tables_kernel(qed_ctx *c, Kern kern, const LeptonArgs<
   return cudaGetLastError();
 }
 
+// A persistent launch of a kernel without dynamic shared memory.
+template <class Real, class Kern>
+static cudaError_t launch_plain_kernel(qed_ctx *c, Kern kern, const LeptonArgs<Real> &a,
+                                       cudaStream_t st) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE, 0);
+  if (e != cudaSuccess) return e;
+  per_sm = persistent_blocks_per_sm(c, per_sm);
+  kern<<<c->num_sms * per_sm, TILE, 0, st>>>(a);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
 // The class list of the streaming pass's flags (three launches).
 static cudaError_t launch_class_lists(qed_ctx *c, const int64_t *n0, const int64_t *n1,
                                       cudaStream_t st) {
@@ -1853,6 +1963,7 @@ static cudaError_t launch_class_lists(qed_ctx *c, const int64_t *n0, const int64
 static cudaError_t launch_sub_scan(qed_ctx *c, int64_t *ph_n, int64_t ph_cap, cudaStream_t st) {
   SubScanArgs a{};
   a.cnt = c->sub_cnt;
+  a.replay_n = c->replay_n;
   a.cls_off = c->cls_off;
   a.sub_meta = c->sub_meta;
   a.ph_n = ph_n;
@@ -1885,7 +1996,8 @@ static cudaError_t launch_lepton_t(qed_ctx *c, const LeptonArgs<Real> &a, cudaSt
   if (e == cudaSuccess) e = prof_mark(c, 3, st);
   if (e == cudaSuccess) e = launch_sub_scan(c, a.ph.d_n, a.ph.cap, st);
   if (e == cudaSuccess) e = prof_mark(c, 4, st);
-  if (e == cudaSuccess) e = launch_tables_kernel<Real>(c, k_substep_write<Real, FM, MODE>, a, false, st);
+  if (e == cudaSuccess) e = launch_plain_kernel<Real>(c, k_substep_write<Real, FM, MODE, false>, a, st);
+  if (e == cudaSuccess) e = launch_tables_kernel<Real>(c, k_substep_write<Real, FM, MODE, true>, a, false, st);
   if (e == cudaSuccess) e = prof_mark(c, 5, st);
   return e;
 }
@@ -1926,6 +2038,8 @@ cudaError_t launch_lepton(qed_ctx *c, const qed_species *s0, const qed_species *
   a.stage_n = c->stage_n;
   a.stage_cap = c->stage_cap;
   a.sub_meta = c->sub_meta;
+  a.replay_list = c->stage_idx;  // free once the class list is built
+  a.replay_n = c->replay_n;
   a.mlp_frag = c->mlp_frag;
   a.mlp_w = c->mlp_w;
   a.use_mlp = c->cfg.sampler == QED_SAMPLER_MLP && c->mlp_ready;
@@ -1939,15 +2053,16 @@ template <class Real, int FM>
 static cudaError_t launch_photon_t(qed_ctx *c, const PhotonArgs<Real> &a, cudaStream_t st) {
   size_t sm = sizeof(Real) * (size_t)c->glp.n;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_photon_stream<Real, FM>,
-                                                                TILE, sm);
+  cudaError_t e = cudaMemsetAsync(a.stage_n, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_photon_stream<Real, FM>, TILE, sm);
   if (e != cudaSuccess) return e;
   per_sm = persistent_blocks_per_sm(c, per_sm);
   k_photon_stream<Real, FM><<<c->num_sms * per_sm, TILE, sm, st>>>(a);
   c->launches += 1;
   e = cudaGetLastError();
   if (e == cudaSuccess) e = prof_mark(c, 6, st);
-  if (e == cudaSuccess) e = launch_flag_list(c, a.flags, 1, a.n_active, nullptr, a.o, st);
+  if (e == cudaSuccess) e = launch_flag_list(c, a.flags, 1, a.n_active, nullptr, a.o, a.stage_idx, st);
   if (e != cudaSuccess) return e;
   auto kern = k_photon<Real, FM, 1>;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE, sm);
@@ -1975,6 +2090,11 @@ cudaError_t launch_photon(qed_ctx *c, const qed_species *g, const qed_species *e
   a.flags = c->heavy_flags;
   a.list = c->heavy_list;
   a.list_n = c->heavy_n;
+  a.stage = static_cast<Stage<Real> *>(c->stage);
+  a.stage_tag = c->stage_tag;
+  a.stage_idx = c->stage_idx;
+  a.stage_n = c->stage_n;
+  a.stage_cap = c->stage_cap;
   a.d_step = c->use_dstep ? c->d_step : nullptr;
   if (f->mode == QED_FIELDS_UNIFORM) return launch_photon_t<Real, FM_UNIFORM>(c, a, st);
   if (f->mode == QED_FIELDS_PER_PARTICLE) return launch_photon_t<Real, FM_PER_PARTICLE>(c, a, st);
