@@ -66,6 +66,8 @@ __device__ __forceinline__ float r_exp(float x) { return __expf(x); }
 __device__ __forceinline__ double r_exp(double x) { return exp(x); }
 __device__ __forceinline__ float r_div(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double r_div(double a, double b) { return a / b; }
+__device__ __forceinline__ float r_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double r_rsqrt(double x) { return 1.0 / sqrt(x); }
 __device__ __forceinline__ float m_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double m_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float m_floor(float x) { return floorf(x); }
@@ -109,6 +111,28 @@ __device__ __forceinline__ Real interp1(const Real *tab, const GridR<Real> &g, R
   Real w[4];
   int i = lag4(g, x, w);
   return w[0] * tab[i - 1] + w[1] * tab[i] + w[2] * tab[i + 1] + w[3] * tab[i + 2];
+}
+
+// interp1 with the weights and base index from lag4
+template <class Real>
+__device__ __forceinline__ Real interp1w(const Real *tab, int i, const Real w[4]) {
+  return w[0] * tab[i - 1] + w[1] * tab[i] + w[2] * tab[i + 1] + w[3] * tab[i + 2];
+}
+
+// interp2 along ga with the row weights and base index from lag4
+template <class Real>
+__device__ __forceinline__ Real interp2w(const Real *tab, int i, const Real wa[4],
+                                         const GridR<Real> &gb, Real b) {
+  Real wb[4];
+  int j = lag4(gb, b, wb);
+  const Real *r = tab + (i - 1) * gb.n + (j - 1);
+  Real acc = (Real)0;
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const Real *q = r + p * gb.n;
+    acc += wa[p] * (wb[0] * q[0] + wb[1] * q[1] + wb[2] * q[2] + wb[3] * q[3]);
+  }
+  return acc;
 }
 
 // tab[(row = index along ga) * gb.n + col]
@@ -199,7 +223,7 @@ __device__ __forceinline__ Real chi_lepton(Real px, Real py, Real pz, Real g, Re
   }
   Real p2 = px * px + py * py + pz * pz;
   if (!(p2 > (Real)0)) return m_sqrt(ex * ex + ey * ey + ez * ez) * inv_aS;
-  Real ip = (Real)1 / m_sqrt(p2);
+  Real ip = r_rsqrt(p2);
   Real nx = px * ip, ny = py * ip, nz = pz * ip;
   Real epar = nx * ex + ny * ey + nz * ez;
   Real eqx = ex - epar * nx, eqy = ey - epar * ny, eqz = ez - epar * nz;
@@ -285,7 +309,9 @@ __device__ __forceinline__ RateOut<Real> photon_rate(const Real *R, const Real *
     tl.status |= QED_STATUS_DOMAIN;
   }
   o.l = l;
-  Real lnG = interp1(R, T.gl, l) + shift;
+  Real wl[4];  // ln chi weights, shared by the rate and forward tables (same grid)
+  const int il = lag4(T.gl, l, wl);
+  Real lnG = interp1w(R, il, wl) + shift;
   Real wmin = (Real)0;
   if (c > (Real)0) {
     // y = ln delta_min, delta_min = 2 xi_min / (3 chi (1 - xi_min)) with
@@ -296,11 +322,11 @@ __device__ __forceinline__ RateOut<Real> photon_rate(const Real *R, const Real *
     if (y > T.gy.hi) return o;  // cut above the spectrum: u_min = 1 - e^-(>90)
     Real kmin;
     if (y < T.gy.lo) {
-      kmin = interp2(F, T.gl, l, T.gy, T.gy.lo) + (y - T.gy.lo) * (Real)(1.0 / 3.0);
+      kmin = interp2w(F, il, wl, T.gy, T.gy.lo) + (y - T.gy.lo) * (Real)(1.0 / 3.0);
       tl.domain += 1;
       tl.status |= QED_STATUS_DOMAIN;
     } else {
-      kmin = interp2(F, T.gl, l, T.gy, y);
+      kmin = interp2w(F, il, wl, T.gy, y);
     }
     o.kmin = kmin;
     wmin = r_exp(kmin);

@@ -92,11 +92,10 @@ __device__ __forceinline__ Real boris(Real &px, Real &py, Real &pz, const Real E
                                       const Real B[3], Real q, Real dt) {
   Real h = (Real)0.5 * q * dt;
   Real ux = px + h * E[0], uy = py + h * E[1], uz = pz + h * E[2];
-  Real gm = m_sqrt((Real)1 + ux * ux + uy * uy + uz * uz);
-  Real ig = h / gm;
+  Real ig = h * r_rsqrt((Real)1 + ux * ux + uy * uy + uz * uz);  // h / gamma-
   Real tx = B[0] * ig, ty = B[1] * ig, tz = B[2] * ig;
   Real t2 = tx * tx + ty * ty + tz * tz;
-  Real s = (Real)2 / ((Real)1 + t2);
+  Real s = r_div((Real)2, (Real)1 + t2);
   Real sx = tx * s, sy = ty * s, sz = tz * s;
   Real vx = ux + (uy * tz - uz * ty), vy = uy + (uz * tx - ux * tz), vz = uz + (ux * ty - uy * tx);
   ux += vy * sz - vz * sy;
@@ -174,6 +173,20 @@ __device__ __forceinline__ void launch_epilogue(const ScanState &S, uint32_t epo
       __threadfence();
     }
   }
+}
+
+// Asynchronous global -> shared copies of one thread's own words (cp.async):
+// the data of the next particle is in flight while the current one computes.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
 }
 
 template <class Real>
@@ -298,7 +311,7 @@ __global__ void __launch_bounds__(TILE) k_lepton_push(LeptonArgs<Real> A) {
       status |= QED_STATUS_NONFINITE;
       continue;
     }
-    const Real ig = dt / gm;
+    const Real ig = r_div(dt, gm);
     S.x[i] = x + px * ig; S.y[i] = y + py * ig; S.z[i] = z + pz * ig;
     S.px[i] = px; S.py[i] = py; S.pz[i] = pz;
   }
@@ -315,13 +328,25 @@ __global__ void __launch_bounds__(TILE) k_lepton_push(LeptonArgs<Real> A) {
 // event, 2: more than one sub-step -- and are redone, from their unchanged
 // stored state, by the ordered passes that append photons.
 // ---------------------------------------------------------------------------
+// Words a thread prefetches per particle: x, y, z, px, py, pz (+ E, B when the
+// fields are per particle); the id goes to its own 8-byte slot.
+template <int FM> __host__ __device__ constexpr int stream_words() { return FM == FM_PER_PARTICLE ? 12 : 6; }
+template <class Real, int FM> __host__ __device__ constexpr size_t stream_prefetch_bytes() {
+  return 2 * TILE * ((size_t)stream_words<FM>() * sizeof(Real) + sizeof(uint64_t));
+}
+
 template <class Real, int FM, int MODE>
-__global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 4 : 2) k_lepton_stream(LeptonArgs<Real> A) {
+__global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 3 : 2) k_lepton_stream(LeptonArgs<Real> A) {
   const int64_t step_ = A.d_step ? *A.d_step : A.step;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr bool kSmem = sizeof(Real) == 4;
+  constexpr int NV = stream_words<FM>();
   Real *sR = kSmem ? reinterpret_cast<Real *>(smem_raw) : const_cast<Real *>(A.T.R);
   Real *sF = kSmem ? sR + A.T.gl.n : const_cast<Real *>(A.T.F);
+  // prefetch buffers after the tables: [2][NV][TILE] words, then [2][TILE] ids
+  const size_t tab_bytes = kSmem ? (((size_t)A.T.gl.n * (1 + A.T.gy.n) * sizeof(Real) + 15) & ~(size_t)15) : 0;
+  Real *pf = reinterpret_cast<Real *>(smem_raw + tab_bytes);
+  uint64_t *pf_id = reinterpret_cast<uint64_t *>(pf + 2 * NV * TILE);
   __shared__ long long s_meta[4];
   __shared__ BlockTally bt;
   if (kSmem) {
@@ -340,13 +365,34 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 4 : 2) k_lepton_stre
   const Real inv_aS = sel<Real>(A.C.inv_aS, A.C.f_inv_aS);
   const Real dt = sel<Real>(A.C.dt, A.C.f_dt), wdt_max = sel<Real>(A.C.wdt_max, A.C.f_wdt_max);
   const int lane = threadIdx.x & 31;
+  const int t = threadIdx.x;
   // this warp's current batch of staging records (warp-uniform)
   uint32_t batch_base = 0, batch_used = STAGE_BATCH;
   Tally tl;
   tl.clear();
+  // issue the copies of slot `sl`'s particle into buffer b
+  auto prefetch = [&](int64_t sl, int b) {
+    const int64_t tile = sl / TILE;
+    const int si = tile < T0 ? 0 : 1;
+    const Sp<Real> &S = A.sp[si];
+    const int64_t i = (tile - (si ? T0 : 0)) * TILE + (sl % TILE);
+    if (i >= (si ? n1 : n0)) return;
+    Real *d = pf + (size_t)b * NV * TILE + t;
+    const Real *src[12] = {S.x, S.y, S.z, S.px, S.py, S.pz, S.ex, S.ey, S.ez, S.bx, S.by, S.bz};
+#pragma unroll
+    for (int c = 0; c < NV; ++c) cp_async<sizeof(Real)>(d + c * TILE, src[c] + i);
+    cp_async<8>(pf_id + b * TILE + t, S.id + i);
+  };
+  const int64_t stride = (int64_t)gridDim.x * TILE;
+  int buf = 0;
+  int64_t slot = blockIdx.x * (int64_t)TILE + threadIdx.x;
+  if (slot < nslots) prefetch(slot, 0);
+  cp_async_commit();
   // nslots is a multiple of TILE: every lane of a warp runs the same iterations
-  for (int64_t slot = blockIdx.x * (int64_t)TILE + threadIdx.x; slot < nslots;
-       slot += (int64_t)gridDim.x * TILE) {
+  for (; slot < nslots; slot += stride, buf ^= 1) {
+    if (slot + stride < nslots) prefetch(slot + stride, buf ^ 1);
+    cp_async_commit();
+    cp_async_wait<1>();  // this slot's copies have landed
     const int64_t tile = slot / TILE;
     const int si = tile < T0 ? 0 : 1;
     const Sp<Real> &S = A.sp[si];
@@ -356,14 +402,20 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 4 : 2) k_lepton_stre
     Real E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
     uint64_t pid = 0;
     if (i < (si ? n1 : n0)) {
-      x = S.x[i]; y = S.y[i]; z = S.z[i];
-      px = S.px[i]; py = S.py[i]; pz = S.pz[i];
-      get_fields<Real, FM>(S, A.f, i, x, y, z, E, B);
-      pid = S.id[i];
+      const Real *v = pf + (size_t)buf * NV * TILE + t;
+      x = v[0]; y = v[TILE]; z = v[2 * TILE];
+      px = v[3 * TILE]; py = v[4 * TILE]; pz = v[5 * TILE];
+      if (FM == FM_PER_PARTICLE) {
+        E[0] = v[6 * TILE]; E[1] = v[7 * TILE]; E[2] = v[8 * TILE];
+        B[0] = v[9 * TILE]; B[1] = v[10 * TILE]; B[2] = v[11 * TILE];
+      } else {
+        get_fields<Real, FM>(S, A.f, i, x, y, z, E, B);
+      }
+      pid = pf_id[buf * TILE + t];
       Real g;
       if (MODE != MODE_EMIT) {
         g = boris(px, py, pz, E, B, S.q, dt);
-        Real ig = dt / g;
+        Real ig = r_div(dt, g);
         x += px * ig; y += py * ig; z += pz * ig;
       } else {
         g = m_sqrt((Real)1 + px * px + py * py + pz * pz);
@@ -379,7 +431,7 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 4 : 2) k_lepton_stre
         if (wdt > wdt_max) {
           // classes by sub-step count N = ceil(W Dt / wdt_max): 2: N <= 3, 3: N <= 7,
           // 4: N <= 15, 5: N >= 16 (lanes of a warp then do similar amounts of work)
-          const Real q = wdt / wdt_max;
+          const Real q = r_div(wdt, wdt_max);
           flag = q <= (Real)3 ? 2 : (q <= (Real)7 ? 3 : (q <= (Real)15 ? 4 : 5));
         } else {
           U4 r = draw(A.C.seed, pid, step_, 0, STREAM_EMIT);
@@ -437,6 +489,7 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 4 : 2) k_lepton_stre
       batch_used += cm;
     }
   }
+  cp_async_wait<0>();
   tally_flush(&bt, tl);
   __syncthreads();
   block_tally_commit(&bt, A.o.cnt, 0);
@@ -463,6 +516,13 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 4 : 2) k_lepton_stre
 // together, so lanes of different event counts stay converged.
 // ---------------------------------------------------------------------------
 constexpr int REC = SUB_REC;
+// Work scheduling of the counting pass: a lane is idle (no particle), scanning
+// (drawing sub-steps) or pending (an event found, its emission not yet done).
+enum { LS_IDLE = 0, LS_SCAN = 1, LS_PEND = 2 };
+constexpr int CNT_CHUNK = 64;       // entries per queue chunk of a warp
+constexpr int CNT_MIN_EMIT = 16;    // an emission round waits for this many lanes ...
+constexpr int CNT_MIN_INIT = 12;    // ... a refill round for this many idle lanes
+constexpr int CNT_SCAN_DRAWS = 4;   // draws per lane per scanning round
 
 // A class-list entry's particle after the push.  Entry e >= 0 is staging
 // record e (written by the streaming pass, which has also stored the pushed
@@ -517,7 +577,7 @@ __device__ __forceinline__ void load_entry(const LeptonArgs<Real> &A, int32_t e,
   P.tag = S.tag ? S.tag[i] : 0u;
   if (MODE != MODE_EMIT) {
     P.g = boris(P.px, P.py, P.pz, P.E, P.B, S.q, dt);
-    Real ig = dt / P.g;
+    Real ig = r_div(dt, P.g);
     P.x += P.px * ig; P.y += P.py * ig; P.z += P.pz * ig;
   } else {
     P.g = m_sqrt((Real)1 + P.px * P.px + P.py * P.py + P.pz * P.pz);
@@ -585,64 +645,93 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 && !MLP ? 3 : 2) k_sub
   __syncthreads();
   const int64_t T0 = (s_meta[0] + TILE - 1) / TILE;
   const int64_t begin = s_meta[1], nh = s_meta[2] - s_meta[1];
-  const int64_t nwt = (nh + 31) / 32;
   const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
   const Real inv_aS = sel<Real>(A.C.inv_aS, A.C.f_inv_aS);
   const Real dt = sel<Real>(A.C.dt, A.C.f_dt);
   const Real wdt_max = sel<Real>(A.C.wdt_max, A.C.f_wdt_max);
   const int64_t rc = A.rec_cap;
   Tally tl;
   tl.clear();
-  // warp tiles of 32 entries, strided over the grid's warps; the heaviest
-  // classes sit at the end of the list and are taken first
-  const int64_t nwarps = (int64_t)gridDim.x * (TILE / 32);
-  for (int64_t f = blockIdx.x * (int64_t)(TILE / 32) + (threadIdx.x >> 5); f < nwt; f += nwarps) {
-    const int64_t h = (nwt - 1 - f) * 32 + lane;
-    const bool active = h < nh;
-    Entry<Real> P;
-    P.x = P.y = P.z = P.px = P.py = (Real)0;
-    P.pz = P.g = (Real)1;
+  // This warp's queue: chunks w, w + W, w + 2W, ... of CNT_CHUNK entries,
+  // counted from the end of the list (the heaviest classes first).
+  const int64_t W = (int64_t)gridDim.x * (TILE / 32);
+  const int64_t w = blockIdx.x * (int64_t)(TILE / 32) + (threadIdx.x >> 5);
+  const int64_t nchunks = (nh + CNT_CHUNK - 1) / CNT_CHUNK;
+  const int64_t qend = w < nchunks ? ((nchunks - 1 - w) / W + 1) * CNT_CHUNK : 0;
+  int64_t next = 0;  // queue position (warp-uniform)
+  // lane state
+  int state = LS_IDLE;
+  int64_t h = 0, N = 0, k = 0;
+  uint32_t cnt = 0, wy = 0;
+  Real px = 0, py = 0, pz = 1, g = 1, chi = 0, dts = 0, nx = 0, ny = 0, nz = 0;
+  Real E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
+  uint64_t pid = 0;
+  RateOut<Real> ro{(Real)0, (Real)-1e30, (Real)0};
+  auto finish = [&]() {
+    tl.events += cnt;
+    A.sub_cnt[h] = cnt;
+    if (h < rc) A.sub_gf[h] = g;
+    state = LS_IDLE;
+  };
+  for (;;) {
+    const unsigned idle = __ballot_sync(0xFFFFFFFFu, state == LS_IDLE);
+    const unsigned pend = __ballot_sync(0xFFFFFFFFu, state == LS_PEND);
+    const unsigned scan = __ballot_sync(0xFFFFFFFFu, state == LS_SCAN);
+    const bool more = next < qend;
+    // one phase per round, run by every lane in that state: emission once
+    // enough lanes wait for it, refills once enough lanes are idle, else
+    // draws; the fall-backs guarantee progress
+    int phase;
+    if (__popc(pend) >= CNT_MIN_EMIT) phase = LS_PEND;
+    else if (more && __popc(idle) >= CNT_MIN_INIT) phase = LS_IDLE;
+    else if (scan) phase = LS_SCAN;
+    else if (pend) phase = LS_PEND;
+    else if (more && idle) phase = LS_IDLE;
+    else break;
+    if (phase == LS_IDLE) {
+      // refill: the idle lanes take the next queue positions, in lane order
+      if (state == LS_IDLE) {
+        const int64_t q = next + __popc(idle & lt_mask);
+        const int64_t hr = q < qend ? (w + (q / CNT_CHUNK) * W) * CNT_CHUNK + (q % CNT_CHUNK) : nh;
+        if (hr < nh) {
+          h = nh - 1 - hr;
+          Entry<Real> P;
+          load_entry<Real, FM, MODE>(A, A.heavy_list[begin + h], T0, dt, P);
+          px = P.px; py = P.py; pz = P.pz; g = P.g;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) { P.E[c] = (Real)0; P.B[c] = (Real)0; }
-    P.id = 0;
-    if (active) load_entry<Real, FM, MODE>(A, A.heavy_list[begin + h], T0, dt, P);
-    Real px = P.px, py = P.py, pz = P.pz, g = P.g;
-    const Real *E = P.E, *B = P.B;
-    const uint64_t pid = P.id;
-    Real chi = chi_lepton(px, py, pz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
-    Tally t0;  // an idle lane tallies nothing
-    t0.clear();
-    RateOut<Real> ro = photon_rate(sR, sF, A.T, A.C, chi, g, t0);
-    int64_t N = substep_count(A.C, ro.W, dt, wdt_max, t0.status);
-    if (active) {
-      tl.status |= t0.status;
-      tl.domain += t0.domain;
-      tl.substeps += N;
-    } else {
-      N = 0;
-    }
-    const Real dts = dt / (Real)(N > 0 ? N : 1);
-    Real nx, ny, nz;
-    unit_dir(P, nx, ny, nz);
-    uint32_t cnt = 0;
-    int64_t k = 0;
-    for (;;) {
-      bool ev = false;  // scan: draw until this lane's next event
-      uint32_t wy = 0;
-      while (k < N) {
-        U4 r = draw(A.C.seed, pid, step_, k, STREAM_EMIT);
-        if (ro.W * dts > unif<Real>(r.x)) { ev = true; wy = r.y; break; }
-        ++k;
+          for (int c = 0; c < 3; ++c) { E[c] = P.E[c]; B[c] = P.B[c]; }
+          pid = P.id;
+          unit_dir(P, nx, ny, nz);
+          chi = chi_lepton(px, py, pz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
+          ro = photon_rate(sR, sF, A.T, A.C, chi, g, tl);
+          N = substep_count(A.C, ro.W, dt, wdt_max, tl.status);
+          tl.substeps += N;
+          dts = dt / (Real)N;
+          k = 0;
+          cnt = 0;
+          state = LS_SCAN;
+        }
       }
-      if (!__any_sync(0xFFFFFFFFu, ev)) break;
+      next += __popc(idle);
+    } else if (phase == LS_SCAN) {
+      // Method I draws until an event or the last sub-step
+      if (state == LS_SCAN) {
+        for (int s = 0; s < CNT_SCAN_DRAWS; ++s) {
+          const U4 r = draw(A.C.seed, pid, step_, k, STREAM_EMIT);
+          if (ro.W * dts > unif<Real>(r.x)) { wy = r.y; state = LS_PEND; break; }
+          if (++k >= N) { finish(); break; }
+        }
+      }
+    } else {
       // emission, by every lane with an event: kappa from r2 (Eq. 7), then
-      // ln delta from the inverse table -- or, for a particle with N = 1 in
-      // a context with the learned sampler, from the network (a
-      // warp-collective call, made with every lane)
+      // ln delta from the inverse table -- or, for a particle with N = 1 in a
+      // context with the learned sampler, from the network (a warp-collective
+      // call, made by every lane, only in rounds where some lane needs it)
+      const bool ev = state == LS_PEND;
       const Real kap = ev ? photon_kappa(ro.kmin, unif<Real>(wy), unif<Real>(~wy)) : (Real)0;
       Real Y = (Real)0;
       bool in_mlp = false;
-      // (only rounds in which some lane has N = 1 run the network)
       if (use_mlp && __any_sync(0xFFFFFFFFu, ev && N == 1)) {
         const float lchi = chi > (Real)0 ? (float)m_log(chi) : MLP_L_LO - 1.0f;
         in_mlp = ev && N == 1 && lchi >= MLP_L_LO && lchi <= MLP_L_HI && (float)kap >= MLP_K_LO &&
@@ -666,15 +755,14 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 && !MLP ? 3 : 2) k_sub
         Real pm2 = m_sqrt((g2 - (Real)1) * (g2 + (Real)1));
         px = pm2 * nx; py = pm2 * ny; pz = pm2 * nz;
         g = g2;
-        chi = chi_lepton(px, py, pz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
-        ro = photon_rate(sR, sF, A.T, A.C, chi, g, tl);
-        ++k;
+        if (++k >= N) {
+          finish();
+        } else {  // the rate for the remaining sub-steps
+          chi = chi_lepton(px, py, pz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
+          ro = photon_rate(sR, sF, A.T, A.C, chi, g, tl);
+          state = LS_SCAN;
+        }
       }
-    }
-    if (active) {
-      tl.events += cnt;
-      A.sub_cnt[h] = cnt;
-      if (h < rc) A.sub_gf[h] = g;
     }
   }
   tally_flush(&bt, tl);
@@ -1908,9 +1996,10 @@ static cudaError_t launch_push(qed_ctx *c, const LeptonArgs<Real> &a, cudaStream
 // forward tables (and, when `mlp` is set, the learned sampler) in shared memory.
 template <class Real, class Kern>
 static cudaError_t launch_tables_kernel(qed_ctx *c, Kern kern, const LeptonArgs<Real> &a, bool mlp,
-                                        cudaStream_t st) {
+                                        cudaStream_t st, size_t extra = 0) {
   size_t sm = sizeof(Real) == 8 ? 0 : lepton_smem<Real>(c);
   if (sm && mlp) sm = ((sm + 15) & ~(size_t)15) + MLP_SMEM_BYTES;
+  if (extra) sm = ((sm + 15) & ~(size_t)15) + extra;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -1985,7 +2074,8 @@ static cudaError_t launch_sub_scan(qed_ctx *c, int64_t *ph_n, int64_t ph_cap, cu
 template <class Real, int FM, int MODE>
 static cudaError_t launch_lepton_t(qed_ctx *c, const LeptonArgs<Real> &a, cudaStream_t st) {
   if (MODE == MODE_PUSH) return launch_push<Real, FM>(c, a, st);
-  cudaError_t e = launch_tables_kernel<Real>(c, k_lepton_stream<Real, FM, MODE>, a, false, st);
+  cudaError_t e = launch_tables_kernel<Real>(c, k_lepton_stream<Real, FM, MODE>, a, false, st,
+                                             stream_prefetch_bytes<Real, FM>());
   if (e == cudaSuccess) e = prof_mark(c, 1, st);
   if (e == cudaSuccess) e = launch_class_lists(c, a.sp[0].d_n, a.nsp > 1 ? a.sp[1].d_n : nullptr, st);
   if (e == cudaSuccess) e = prof_mark(c, 2, st);
