@@ -239,7 +239,7 @@ extern "C" int qed_init_tables(const qed_config *cfg, qed_ctx **out, qed_stream_
       cudaMalloc(&c->stage_tag, sizeof(uint32_t) * (size_t)c->stage_cap) != cudaSuccess ||
       cudaMalloc(&c->stage_idx, sizeof(int32_t) * (size_t)c->heavy_slots) != cudaSuccess ||
       cudaMalloc(&c->stage_n, sizeof(unsigned int)) != cudaSuccess ||
-      cudaMalloc(&c->sub_meta, 2 * sizeof(int64_t)) != cudaSuccess ||
+      cudaMalloc(&c->sub_meta, 4 * sizeof(int64_t)) != cudaSuccess ||
       cudaMalloc(&c->fill_meta, 2 * sizeof(int64_t)) != cudaSuccess ||
       cudaMalloc(&c->replay_n, sizeof(unsigned int)) != cudaSuccess) {
     free_ctx(c);

@@ -38,7 +38,7 @@ struct qed_ctx {
   void *rec_e;        // Real [SUB_REC][rec_cap]
   uint32_t *rec_k;    // [SUB_REC][rec_cap]
   int64_t rec_cap;
-  int64_t *sub_meta;  // [2] photons of the sub-step entries, photon count before them
+  int64_t *sub_meta;  // [4] appends of the emission (or pair) entries, counts before them
   int64_t *fill_meta; // [2] count before and after a hole-filling compaction
   unsigned int *replay_n;  // entries the writing pass leaves to its replay launch
   // staging records of the flagged leptons (streaming pass -> later passes)

@@ -777,10 +777,10 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 && !MLP ? 3 : 2) k_sub
 struct SubScanArgs {
   uint32_t *cnt;
   unsigned int *replay_n;  // reset here for the writing pass
-  const int64_t *cls_off;
-  int64_t *sub_meta;
-  int64_t *ph_n;
-  int64_t ph_cap;
+  const int64_t *n_entries;
+  int64_t *sub_meta;       // [0] total, [1] count of out1 before, [2] count of out2 before
+  int64_t *out1_n, *out2_n;  // species counts to advance by the total (out2 optional)
+  int64_t out1_cap, out2_cap;
   Out o;
 };
 constexpr int SCAN_ITEMS = 16;
@@ -789,12 +789,13 @@ __global__ void __launch_bounds__(TILE) k_sub_scan(SubScanArgs A) {
   __shared__ uint32_t scan_sm[33];
   __shared__ long long s_meta[6];
   if (threadIdx.x == 0) {
-    s_meta[2] = A.cls_off[NCLS];
-    s_meta[3] = *(volatile int64_t *)A.ph_n;
+    s_meta[2] = *(volatile const int64_t *)A.n_entries;
+    s_meta[3] = *(volatile int64_t *)A.out1_n;
     s_meta[4] = (long long)A.o.scan.sync[2];
+    s_meta[5] = A.out2_n ? *(volatile int64_t *)A.out2_n : 0;
   }
   __syncthreads();
-  const int64_t nh = s_meta[2], nph = s_meta[3];
+  const int64_t nh = s_meta[2], nph = s_meta[3], n2 = s_meta[5];
   const uint32_t epoch = (uint32_t)s_meta[4];
   const int64_t per_tile = (int64_t)TILE * SCAN_ITEMS;
   const int64_t ntiles = (nh + per_tile - 1) / per_tile;
@@ -804,6 +805,7 @@ __global__ void __launch_bounds__(TILE) k_sub_scan(SubScanArgs A) {
     if (ntiles == 0) {
       A.sub_meta[0] = 0;
       A.sub_meta[1] = nph;
+      A.sub_meta[2] = n2;
     }
   }
   for (;;) {
@@ -830,7 +832,9 @@ __global__ void __launch_bounds__(TILE) k_sub_scan(SubScanArgs A) {
           const int64_t tot = (int64_t)pre + agg;
           A.sub_meta[0] = tot;
           A.sub_meta[1] = nph;
-          *A.ph_n = nph + tot < A.ph_cap ? nph + tot : A.ph_cap;
+          A.sub_meta[2] = n2;
+          *A.out1_n = nph + tot < A.out1_cap ? nph + tot : A.out1_cap;
+          if (A.out2_n) *A.out2_n = n2 + tot < A.out2_cap ? n2 + tot : A.out2_cap;
         }
       }
     }
@@ -860,6 +864,8 @@ __global__ void __launch_bounds__(TILE, REPLAY || sizeof(Real) == 8 ? 2 : 4) k_s
   Real *sF = kSmem ? sR + A.T.gl.n : const_cast<Real *>(A.T.F);
   __shared__ long long s_meta[5];
   __shared__ BlockTally bt;
+  // a replay block with nothing to replay leaves before staging the tables
+  if (REPLAY && (int64_t)blockIdx.x * TILE >= (int64_t)*(volatile unsigned int *)A.replay_n) return;
   if (kSmem) {
     load_tables_smem(sR, A.T.R, A.T.gl.n);
     load_tables_smem(sF, A.T.F, A.T.gl.n * A.T.gy.n);
@@ -1243,6 +1249,11 @@ template <class Real> struct PhotonArgs {
   int64_t stage_cap;
   const int64_t *list_n;
   const int64_t *d_step;  // if set, the step index is read here (graph replay)
+  uint32_t *sub_cnt;      // pairs per list entry, then their exclusive prefix
+  const int64_t *sub_meta;  // [0] pairs in all, [1] electrons before, [2] positrons before
+  Real *rec_e;            // [0][h] gamma_e, [1][h] gamma_p of entry h's pair (h < rec_cap)
+  uint32_t *rec_k;        // [h] its sub-step
+  int64_t rec_cap;
 };
 
 // ---------------------------------------------------------------------------
@@ -1348,146 +1359,193 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 4 : 2) k_photon_stre
   block_tally_commit(&bt, A.o.cnt, 1);
 }
 
-template <class Real, int FM, int LIST>
-__global__ void __launch_bounds__(TILE) k_photon(PhotonArgs<Real> A) {
+// ---------------------------------------------------------------------------
+// Pair passes over the list of flagged photons (list order = photon index
+// order), split like the lepton emission passes: a counting pass with no
+// ordering (the photon's Method I chain: at most one pair, after which the
+// photon is dead), the in-place scan of the counts, and a writing pass that
+// appends the e-/e+ of each pair at its scanned slot.
+// ---------------------------------------------------------------------------
+template <class Real> struct PhotonEntry {
+  Real x, y, z, px, py, pz, k, w;
+  Real E[3], B[3];
+  uint64_t id;
+  uint32_t tag;
+  int64_t i;  // photon index
+};
+
+// List entry e >= 0: staging record e (pushed position already stored);
+// e < 0: photon -e-1, which the counting pass (COUNT) pushes and stores and
+// the writing pass reads back already pushed.
+template <class Real, int FM, bool COUNT>
+__device__ __forceinline__ void load_photon(const PhotonArgs<Real> &A, int32_t e, Real dt,
+                                            PhotonEntry<Real> &P) {
+  if (e >= 0) {
+    Stage<Real> r;
+    const uint4 *src = reinterpret_cast<const uint4 *>(A.stage + e);
+    uint4 *dst = reinterpret_cast<uint4 *>(&r);
+#pragma unroll
+    for (int q = 0; q < (int)(sizeof(Stage<Real>) / 16); ++q) dst[q] = src[q];
+    P.px = r.p[0]; P.py = r.p[1]; P.pz = r.p[2];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { P.E[c] = r.e[c]; P.B[c] = r.b[c]; }
+    P.id = (uint64_t)r.id_lo | ((uint64_t)r.id_hi << 32);
+    P.w = r.w;
+    P.x = r.x[0]; P.y = r.x[1]; P.z = r.x[2];
+    P.i = r.slot;
+    P.tag = A.ph.tag ? A.stage_tag[e] : 0u;
+    P.k = m_sqrt(P.px * P.px + P.py * P.py + P.pz * P.pz);
+    return;
+  }
+  const int64_t i = -(int64_t)e - 1;
+  P.i = i;
+  P.x = A.ph.x[i]; P.y = A.ph.y[i]; P.z = A.ph.z[i];
+  P.px = A.ph.px[i]; P.py = A.ph.py[i]; P.pz = A.ph.pz[i];
+  P.w = A.ph.w[i];
+  P.id = A.ph.id[i];
+  P.tag = A.ph.tag ? A.ph.tag[i] : 0u;
+  get_fields<Real, FM>(A.ph, A.f, i, P.x, P.y, P.z, P.E, P.B);  // at the position before the push
+  P.k = m_sqrt(P.px * P.px + P.py * P.py + P.pz * P.pz);
+  if (COUNT && P.k > (Real)0) {
+    Real ik = dt / P.k;
+    P.x += P.px * ik; P.y += P.py * ik; P.z += P.pz * ik;
+    A.ph.x[i] = P.x; A.ph.y[i] = P.y; A.ph.z[i] = P.z;
+  }
+}
+
+// Method I for one photon (Eqs. 3, 6): 1 and the pair's (gamma_e, gamma_p,
+// sub-step) on an event, else 0.
+template <class Real>
+__device__ __forceinline__ uint32_t pair_chain(const PhotonArgs<Real> &A, const Real *sP,
+                                               const PhotonEntry<Real> &P, int64_t step_, Real dt,
+                                               Tally &tl, int64_t &N, Real &ge, Real &gp,
+                                               int64_t &ks) {
+  const Real inv_aS = sel<Real>(A.C.inv_aS, A.C.f_inv_aS);
+  const Real wdt_max = sel<Real>(A.C.wdt_max, A.C.f_wdt_max);
+  Real chi = chi_photon(P.px, P.py, P.pz, P.E[0], P.E[1], P.E[2], P.B[0], P.B[1], P.B[2], inv_aS);
+  RateOut<Real> ro = pair_rate(sP, A.T, A.C, chi, P.k, tl);
+  N = 1;
+  const Real wdt = ro.W * dt;
+  if (wdt > wdt_max) {
+    Real nn = m_ceil(wdt / wdt_max);
+    if (nn > (Real)A.C.max_substeps) { nn = (Real)A.C.max_substeps; tl.status |= QED_STATUS_SUBSTEPS; }
+    N = (int64_t)nn;
+  }
+  const Real dts = dt / (Real)N;
+  for (int64_t s = 0; s < N; ++s) {
+    U4 r = draw(A.C.seed, P.id, step_, s, STREAM_PAIR);
+    if (!(ro.W * dts > unif<Real>(r.x))) continue;
+    XiOut<Real> xo = pair_xi(A.T.Yp, A.T, ro.l, unif<Real>(r.y), unif<Real>(~r.y));
+    ge = xo.xi * P.k;
+    gp = xo.omxi * P.k;
+    if (ge < (Real)1) { ge = (Real)1; gp = P.k - (Real)1; }
+    if (gp < (Real)1) { gp = (Real)1; ge = P.k - (Real)1; }
+    ks = s;
+    return 1u;
+  }
+  return 0u;
+}
+
+template <class Real, int FM>
+__global__ void __launch_bounds__(TILE) k_pair_count(PhotonArgs<Real> A) {
   const int64_t step_ = A.d_step ? *A.d_step : A.step;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Real *sP = reinterpret_cast<Real *>(smem_raw);
-  __shared__ uint32_t scan_sm[33];
-  __shared__ long long s_meta[8];
+  __shared__ long long s_meta[1];
   __shared__ BlockTally bt;
   load_tables_smem(sP, A.T.P, A.T.glp.n);
   block_tally_init(&bt);
-  if (threadIdx.x == 0) {
-    s_meta[2] = LIST ? *(volatile const int64_t *)A.list_n : *(volatile const int64_t *)A.n_active;
-    s_meta[3] = *(volatile int64_t *)A.el.d_n;
-    s_meta[4] = *(volatile int64_t *)A.po.d_n;
-    s_meta[5] = (long long)A.o.scan.sync[2];
-  }
+  if (threadIdx.x == 0) s_meta[0] = *(volatile const int64_t *)A.list_n;
   __syncthreads();
-  const int64_t n = s_meta[2], ne = s_meta[3], np = s_meta[4];
-  const uint32_t epoch = (uint32_t)s_meta[5];
-  const int64_t ntiles = (n + TILE - 1) / TILE;
-  const Real inv_aS = sel<Real>(A.C.inv_aS, A.C.f_inv_aS);
+  const int64_t nl = s_meta[0];
   const Real dt = sel<Real>(A.C.dt, A.C.f_dt);
+  const int64_t rc = A.rec_cap;
   Tally tl;
   tl.clear();
-  for (;;) {
-    if (threadIdx.x == 0) s_meta[0] = (long long)atomicAdd(&A.o.scan.sync[0], 1u);
-    __syncthreads();
-    const int64_t t = s_meta[0];
-    __syncthreads();
-    if (t >= ntiles) break;
-    const int64_t h = t * TILE + threadIdx.x;
-    bool active = h < n;
-    // list entry: staging record e >= 0 (pushed state, position already
-    // stored), or -(index + 1) for a photon the staging area had no room for
-    const int32_t e = (LIST && active) ? A.list[h] : -1;
-    const bool staged = LIST && active && e >= 0;
-    int64_t i = LIST ? 0 : h;
-    Real x = 0, y = 0, z = 0, px = 0, py = 0, pz = 0, wt = 0, k = 0;
-    Real E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
-    uint64_t pid = 0;
-    uint32_t ptag = 0;
-    if (staged) {
-      Stage<Real> r;
-      const uint4 *src = reinterpret_cast<const uint4 *>(A.stage + e);
-      uint4 *dst = reinterpret_cast<uint4 *>(&r);
-#pragma unroll
-      for (int q = 0; q < (int)(sizeof(Stage<Real>) / 16); ++q) dst[q] = __ldcs(src + q);
-      px = r.p[0]; py = r.p[1]; pz = r.p[2];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) { E[c] = r.e[c]; B[c] = r.b[c]; }
-      pid = (uint64_t)r.id_lo | ((uint64_t)r.id_hi << 32);
-      wt = r.w;
-      x = r.x[0]; y = r.x[1]; z = r.x[2];
-      i = r.slot;
-      if (A.ph.tag) ptag = A.stage_tag[e];
-    } else if (LIST && active) {
-      i = -(int64_t)e - 1;
-    }
-    if (active && !staged && A.ph.alive) active = A.ph.alive[i] != 0;
-    uint32_t cnt = 0;
+  for (int64_t h = blockIdx.x * (int64_t)TILE + threadIdx.x; h < nl; h += (int64_t)gridDim.x * TILE) {
+    PhotonEntry<Real> P;
+    load_photon<Real, FM, true>(A, A.list[h], dt, P);
+    int64_t N = 1, ks = 0;
     Real ge = 0, gp = 0;
-    int64_t ks = 0;
-    if (active) {
-      if (!staged) {
-        x = A.ph.x[i]; y = A.ph.y[i]; z = A.ph.z[i];
-        px = A.ph.px[i]; py = A.ph.py[i]; pz = A.ph.pz[i];
-        wt = A.ph.w[i]; pid = A.ph.id[i];
-        if (A.ph.tag) ptag = A.ph.tag[i];
-        get_fields<Real, FM>(A.ph, A.f, i, x, y, z, E, B);
-      }
-      k = m_sqrt(px * px + py * py + pz * pz);
-      if (!staged && k > (Real)0) {
-        Real ik = dt / k;
-        x += px * ik; y += py * ik; z += pz * ik;
-        A.ph.x[i] = x; A.ph.y[i] = y; A.ph.z[i] = z;
-      }
-      Real chi = chi_photon(px, py, pz, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
-      RateOut<Real> ro = pair_rate(sP, A.T, A.C, chi, k, tl);
-      int64_t N = 1;
-      Real wdt = ro.W * dt;
-      const Real wdt_max = sel<Real>(A.C.wdt_max, A.C.f_wdt_max);
-      if (wdt > wdt_max) {
-        Real nn = m_ceil(wdt / wdt_max);
-        if (nn > (Real)A.C.max_substeps) { nn = (Real)A.C.max_substeps; tl.status |= QED_STATUS_SUBSTEPS; }
-        N = (int64_t)nn;
-      }
-      const Real dts = dt / (Real)N;
-      tl.substeps += N;
-      for (int64_t s = 0; s < N; ++s) {
-        U4 r = draw(A.C.seed, pid, step_, s, STREAM_PAIR);
-        if (!(ro.W * dts > unif<Real>(r.x))) continue;
-        XiOut<Real> xo = pair_xi(A.T.Yp, A.T, ro.l, unif<Real>(r.y), unif<Real>(~r.y));
-        ge = xo.xi * k;
-        gp = xo.omxi * k;
-        if (ge < (Real)1) { ge = (Real)1; gp = k - (Real)1; }
-        if (gp < (Real)1) { gp = (Real)1; ge = k - (Real)1; }
-        ks = s;
-        cnt = 1;
-        A.ph.alive[i] = 0;
-        break;
-      }
-      tl.events += cnt;
-    }
-    uint32_t excl = block_excl_scan(cnt, scan_sm);
-    uint32_t agg = scan_sm[32];
-    if (threadIdx.x < 32) {
-      uint32_t st = 0;
-      uint32_t pre = lookback_warp(A.o.scan, t, epoch, agg, st);
-      if (threadIdx.x == 0) {
-        s_meta[1] = pre;
-        if (st) tl.status |= st;
-        if (t == ntiles - 1) {
-          int64_t tot = (int64_t)pre + agg;
-          *A.el.d_n = ne + tot < A.el.cap ? ne + tot : A.el.cap;
-          *A.po.d_n = np + tot < A.po.cap ? np + tot : A.po.cap;
-        }
-      }
-    }
-    __syncthreads();
+    const uint32_t cnt = pair_chain(A, sP, P, step_, dt, tl, N, ge, gp, ks);
+    tl.substeps += N;
+    tl.events += cnt;
+    A.sub_cnt[h] = cnt;
     if (cnt) {
-      const int64_t off = s_meta[1] + excl;
-      Real ik = (Real)1 / k;
-      Real nx = px * ik, ny = py * ik, nz = pz * ik;
-      U4 cid = draw(A.C.seed, pid, step_, ks, STREAM_PAIR_ID);
-      Real pe = m_sqrt((ge - (Real)1) * (ge + (Real)1));
-      Real pp = m_sqrt((gp - (Real)1) * (gp + (Real)1));
-      if (ne + off < A.el.cap)
-        write_child(A.el, ne + off, x, y, z, pe * nx, pe * ny, pe * nz, wt,
-                    (uint64_t)cid.x | ((uint64_t)cid.y << 32), E, B, ptag);
-      else { tl.dropped += 1; tl.status |= QED_STATUS_CAPACITY; }
-      if (np + off < A.po.cap)
-        write_child(A.po, np + off, x, y, z, pp * nx, pp * ny, pp * nz, wt,
-                    (uint64_t)cid.z | ((uint64_t)cid.w << 32), E, B, ptag);
-      else { tl.dropped += 1; tl.status |= QED_STATUS_CAPACITY; }
+      A.ph.alive[P.i] = 0;
+      if (h < rc) {
+        A.rec_e[h] = ge;
+        A.rec_e[rc + h] = gp;
+        A.rec_k[h] = (uint32_t)ks;
+      }
     }
   }
   tally_flush(&bt, tl);
   __syncthreads();
   block_tally_commit(&bt, A.o.cnt, 1);
-  launch_epilogue(A.o.scan, epoch);
+}
+
+template <class Real, int FM>
+__global__ void __launch_bounds__(TILE) k_pair_write(PhotonArgs<Real> A) {
+  const int64_t step_ = A.d_step ? *A.d_step : A.step;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Real *sP = reinterpret_cast<Real *>(smem_raw);
+  __shared__ long long s_meta[4];
+  __shared__ BlockTally bt;
+  load_tables_smem(sP, A.T.P, A.T.glp.n);  // for entries past the record capacity
+  block_tally_init(&bt);
+  if (threadIdx.x == 0) {
+    s_meta[0] = *(volatile const int64_t *)A.list_n;
+    s_meta[1] = A.sub_meta[0];  // pairs of all entries
+    s_meta[2] = A.sub_meta[1];  // electron count before them
+    s_meta[3] = A.sub_meta[2];  // positron count before them
+  }
+  __syncthreads();
+  const int64_t nl = s_meta[0];
+  const uint32_t total = (uint32_t)s_meta[1];
+  const int64_t ne = s_meta[2], np = s_meta[3];
+  const Real dt = sel<Real>(A.C.dt, A.C.f_dt);
+  const int64_t rc = A.rec_cap;
+  Tally tl;
+  tl.clear();
+  for (int64_t h = blockIdx.x * (int64_t)TILE + threadIdx.x; h < nl; h += (int64_t)gridDim.x * TILE) {
+    const uint32_t off = A.sub_cnt[h];  // exclusive prefix of the counts now
+    const uint32_t cnt = (h + 1 < nl ? A.sub_cnt[h + 1] : total) - off;
+    if (!cnt) continue;
+    PhotonEntry<Real> P;
+    load_photon<Real, FM, false>(A, A.list[h], dt, P);
+    Real ge = 0, gp = 0;
+    int64_t ks = 0;
+    if (h < rc) {
+      ge = A.rec_e[h];
+      gp = A.rec_e[rc + h];
+      ks = A.rec_k[h];
+    } else {  // past the record capacity: redo the chain (same draws, same table)
+      Tally dummy;
+      dummy.clear();
+      int64_t N = 1;
+      if (!pair_chain(A, sP, P, step_, dt, dummy, N, ge, gp, ks)) {
+        tl.status |= QED_STATUS_REPLAY;  // should not happen: write a pair at rest
+        ge = gp = (Real)1;
+      }
+    }
+    const Real ik = (Real)1 / P.k;
+    const Real nx = P.px * ik, ny = P.py * ik, nz = P.pz * ik;
+    const U4 cid = draw(A.C.seed, P.id, step_, ks, STREAM_PAIR_ID);
+    const Real pe = m_sqrt((ge - (Real)1) * (ge + (Real)1));
+    const Real pp = m_sqrt((gp - (Real)1) * (gp + (Real)1));
+    if (ne + off < A.el.cap)
+      write_child(A.el, ne + off, P.x, P.y, P.z, pe * nx, pe * ny, pe * nz, P.w,
+                  (uint64_t)cid.x | ((uint64_t)cid.y << 32), P.E, P.B, P.tag);
+    else { tl.dropped += 1; tl.status |= QED_STATUS_CAPACITY; }
+    if (np + off < A.po.cap)
+      write_child(A.po, np + off, P.x, P.y, P.z, pp * nx, pp * ny, pp * nz, P.w,
+                  (uint64_t)cid.z | ((uint64_t)cid.w << 32), P.E, P.B, P.tag);
+    else { tl.dropped += 1; tl.status |= QED_STATUS_CAPACITY; }
+  }
+  tally_flush(&bt, tl);
+  __syncthreads();
+  block_tally_commit(&bt, A.o.cnt, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -2049,14 +2107,18 @@ static cudaError_t launch_class_lists(qed_ctx *c, const int64_t *n0, const int64
   return cudaGetLastError();
 }
 
-static cudaError_t launch_sub_scan(qed_ctx *c, int64_t *ph_n, int64_t ph_cap, cudaStream_t st) {
+static cudaError_t launch_sub_scan(qed_ctx *c, const int64_t *n_entries, int64_t *out1_n,
+                                   int64_t out1_cap, int64_t *out2_n, int64_t out2_cap,
+                                   cudaStream_t st) {
   SubScanArgs a{};
   a.cnt = c->sub_cnt;
   a.replay_n = c->replay_n;
-  a.cls_off = c->cls_off;
+  a.n_entries = n_entries;
   a.sub_meta = c->sub_meta;
-  a.ph_n = ph_n;
-  a.ph_cap = ph_cap;
+  a.out1_n = out1_n;
+  a.out1_cap = out1_cap;
+  a.out2_n = out2_n;
+  a.out2_cap = out2_cap;
   a.o = out_of(c);
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sub_scan, TILE, 0);
@@ -2084,7 +2146,7 @@ static cudaError_t launch_lepton_t(qed_ctx *c, const LeptonArgs<Real> &a, cudaSt
             ? launch_tables_kernel<Real>(c, k_substep_count<Real, FM, MODE, true>, a, true, st)
             : launch_tables_kernel<Real>(c, k_substep_count<Real, FM, MODE, false>, a, false, st);
   if (e == cudaSuccess) e = prof_mark(c, 3, st);
-  if (e == cudaSuccess) e = launch_sub_scan(c, a.ph.d_n, a.ph.cap, st);
+  if (e == cudaSuccess) e = launch_sub_scan(c, c->cls_off + NCLS, a.ph.d_n, a.ph.cap, nullptr, 0, st);
   if (e == cudaSuccess) e = prof_mark(c, 4, st);
   if (e == cudaSuccess) e = launch_plain_kernel<Real>(c, k_substep_write<Real, FM, MODE, false>, a, st);
   if (e == cudaSuccess) e = launch_tables_kernel<Real>(c, k_substep_write<Real, FM, MODE, true>, a, false, st);
@@ -2154,11 +2216,19 @@ static cudaError_t launch_photon_t(qed_ctx *c, const PhotonArgs<Real> &a, cudaSt
   if (e == cudaSuccess) e = prof_mark(c, 6, st);
   if (e == cudaSuccess) e = launch_flag_list(c, a.flags, 1, a.n_active, nullptr, a.o, a.stage_idx, st);
   if (e != cudaSuccess) return e;
-  auto kern = k_photon<Real, FM, 1>;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE, sm);
+  // pairs: counting pass, scan (advances both lepton counts), writing pass
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair_count<Real, FM>, TILE, sm);
   if (e != cudaSuccess) return e;
   per_sm = persistent_blocks_per_sm(c, per_sm);
-  kern<<<c->num_sms * per_sm, TILE, sm, st>>>(a);
+  k_pair_count<Real, FM><<<c->num_sms * per_sm, TILE, sm, st>>>(a);
+  c->launches += 1;
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = launch_sub_scan(c, a.list_n, a.el.d_n, a.el.cap, a.po.d_n, a.po.cap, st);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair_write<Real, FM>, TILE, sm);
+  if (e != cudaSuccess) return e;
+  per_sm = persistent_blocks_per_sm(c, per_sm);
+  k_pair_write<Real, FM><<<c->num_sms * per_sm, TILE, sm, st>>>(a);
   c->launches += 1;
   return cudaGetLastError();
 }
@@ -2185,6 +2255,11 @@ cudaError_t launch_photon(qed_ctx *c, const qed_species *g, const qed_species *e
   a.stage_idx = c->stage_idx;
   a.stage_n = c->stage_n;
   a.stage_cap = c->stage_cap;
+  a.sub_cnt = c->sub_cnt;
+  a.sub_meta = c->sub_meta;
+  a.rec_e = static_cast<Real *>(c->rec_e);
+  a.rec_k = c->rec_k;
+  a.rec_cap = c->rec_cap;
   a.d_step = c->use_dstep ? c->d_step : nullptr;
   if (f->mode == QED_FIELDS_UNIFORM) return launch_photon_t<Real, FM_UNIFORM>(c, a, st);
   if (f->mode == QED_FIELDS_PER_PARTICLE) return launch_photon_t<Real, FM_PER_PARTICLE>(c, a, st);
