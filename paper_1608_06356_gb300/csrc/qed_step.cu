@@ -521,7 +521,7 @@ constexpr int REC = SUB_REC;
 enum { LS_IDLE = 0, LS_SCAN = 1, LS_PEND = 2 };
 constexpr int CNT_CHUNK = 64;       // entries per queue chunk of a warp
 constexpr int CNT_MIN_EMIT = 16;    // an emission round waits for this many lanes ...
-constexpr int CNT_MIN_INIT = 12;    // ... a refill round for this many idle lanes
+constexpr int CNT_MIN_INIT = 20;    // ... a refill round for this many idle lanes
 constexpr int CNT_SCAN_DRAWS = 4;   // draws per lane per scanning round
 
 // A class-list entry's particle after the push.  Entry e >= 0 is staging
@@ -1554,13 +1554,18 @@ __global__ void __launch_bounds__(TILE) k_pair_write(PhotonArgs<Real> A) {
 // writes only below the end of its own range, after every earlier tile has
 // published -- so no data is overwritten before it has been read.
 // ---------------------------------------------------------------------------
+// Compaction tiles are 1024 particles (one per thread of a 1024-thread CTA),
+// so a call takes a quarter of the tile-counter atomics and look-backs that
+// 256-particle tiles would.
+constexpr int COMPACT_TILE = 1024;
+
 template <class Real> struct CompactArgs {
   Sp<Real> s;
   Out o;
 };
 
 template <class Real>
-__global__ void __launch_bounds__(TILE) k_compact(CompactArgs<Real> A) {
+__global__ void __launch_bounds__(COMPACT_TILE) k_compact(CompactArgs<Real> A) {
   __shared__ uint32_t scan_sm[33];
   __shared__ long long s_meta[8];
   if (threadIdx.x == 0) {
@@ -1570,7 +1575,7 @@ __global__ void __launch_bounds__(TILE) k_compact(CompactArgs<Real> A) {
   __syncthreads();
   const int64_t n = s_meta[2];
   const uint32_t epoch = (uint32_t)s_meta[5];
-  const int64_t ntiles = (n + TILE - 1) / TILE;
+  const int64_t ntiles = (n + COMPACT_TILE - 1) / COMPACT_TILE;
   const bool fields = A.s.ex != nullptr;
   uint32_t status = 0;
   for (;;) {
@@ -1579,7 +1584,7 @@ __global__ void __launch_bounds__(TILE) k_compact(CompactArgs<Real> A) {
     const int64_t t = s_meta[0];
     __syncthreads();
     if (t >= ntiles) break;
-    const int64_t i = t * TILE + threadIdx.x;
+    const int64_t i = t * COMPACT_TILE + threadIdx.x;
     uint32_t keep = 0;
     Real v[13];
     uint64_t id = 0;
@@ -2272,10 +2277,10 @@ cudaError_t launch_compact(qed_ctx *c, const qed_species *s, cudaStream_t st) {
   a.s = to_sp<Real>(s);
   a.o = out_of(c);
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_compact<Real>, TILE, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_compact<Real>, COMPACT_TILE, 0);
   if (e != cudaSuccess) return e;
   per_sm = persistent_blocks_per_sm(c, per_sm);
-  k_compact<Real><<<c->num_sms * per_sm, TILE, 0, st>>>(a);
+  k_compact<Real><<<c->num_sms * per_sm, COMPACT_TILE, 0, st>>>(a);
   c->launches += 1;
   return cudaGetLastError();
 }
