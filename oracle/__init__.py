@@ -47,13 +47,18 @@ def build(force: bool = False) -> str:
 class Config(C.Structure):
     _fields_ = [("a_S", C.c_double), ("alpha", C.c_double), ("dt", C.c_double),
                 ("wdt_max", C.c_double), ("xi_min_energy", C.c_double),
-                ("pair_sign", C.c_int), ("pad_", C.c_int), ("seed", C.c_uint64),
+                ("pair_sign", C.c_int), ("generator", C.c_int), ("seed", C.c_uint64),
                 ("spec_lo", C.c_double), ("spec_hi", C.c_double)]
 
 
+GEN_METHOD_I, GEN_METHOD_II, GEN_METHOD_III = 0, 1, 2
+
+
 def make_config(dt=0.01, a_S=A_S_1UM, alpha=ALPHA, wdt_max=0.2, xi_min_energy=2.0,
-                pair_sign=1, seed=0, spec_lo=2.0, spec_hi=1000.0) -> Config:
-    return Config(a_S, alpha, dt, wdt_max, xi_min_energy, pair_sign, 0, seed, spec_lo, spec_hi)
+                pair_sign=1, seed=0, spec_lo=2.0, spec_hi=1000.0, generator=GEN_METHOD_I) -> Config:
+    """generator: photon event generator, Method I (default), II or III."""
+    return Config(a_S, alpha, dt, wdt_max, xi_min_energy, pair_sign, generator, seed, spec_lo,
+                  spec_hi)
 
 
 class Fields(C.Structure):
@@ -72,7 +77,7 @@ class _Species(C.Structure):
                 ("w", _PD), ("id", C.POINTER(C.c_uint64)), ("alive", C.POINTER(C.c_uint8)),
                 ("ex", _PD), ("ey", _PD), ("ez", _PD), ("bx", _PD), ("by", _PD), ("bz", _PD),
                 ("n", C.c_int64), ("capacity", C.c_int64), ("q", C.c_double),
-                ("tag", C.POINTER(C.c_uint32))]
+                ("tag", C.POINTER(C.c_uint32)), ("od_p", _PD), ("od_r", _PD)]
 
 
 class Counters(C.Structure):
@@ -315,7 +320,7 @@ class Species:
     """FP64 SoA particle buffers owned by numpy, with capacity for appends."""
 
     def __init__(self, capacity: int, q: float, per_particle_fields: bool = False,
-                 with_alive: bool = False, with_tag: bool = False):
+                 with_alive: bool = False, with_tag: bool = False, with_od: bool = False):
         self.capacity = int(capacity)
         self.q = float(q)
         cap = max(self.capacity, 1)
@@ -327,6 +332,9 @@ class Species:
         for nm in _FIELD_NAMES:
             setattr(self, nm, np.zeros(cap) if per_particle_fields else None)
         self.tag = np.zeros(cap, dtype=np.uint32) if with_tag else None
+        # Methods II/III state: cumulative probability and r3 (0 = not drawn yet)
+        self.od_p = np.zeros(cap) if with_od else None
+        self.od_r = np.zeros(cap) if with_od else None
         self.n = 0
 
     def load(self, **arrays):
@@ -358,6 +366,8 @@ class Species:
         s.n, s.capacity, s.q = self.n, self.capacity, self.q
         s.tag = (self.tag.ctypes.data_as(C.POINTER(C.c_uint32)) if self.tag is not None
                  else C.POINTER(C.c_uint32)())
+        s.od_p = _dp(self.od_p) if self.od_p is not None else _PD()
+        s.od_r = _dp(self.od_r) if self.od_r is not None else _PD()
         return s
 
 

@@ -326,7 +326,7 @@ typedef struct {
   double wdt_max;       /* sub-step threshold: W*Dt/N <= wdt_max (0.2) */
   double xi_min_energy; /* infrared cut: xi_min * eps_e = xi_min_energy (2 m c^2) */
   int pair_sign;        /* sign of the int K_{1/3} term of Eq. (6) */
-  int pad_;
+  int generator;        /* photon event generator: 0 Method I, 1 Method II, 2 Method III */
   uint64_t seed;        /* Philox key */
   double spec_lo, spec_hi; /* photon-energy histogram range (m c^2), 64 log bins */
 } orc_config;
@@ -551,6 +551,8 @@ typedef struct {
   int64_t n, capacity;
   double q; /* -1 electron, +1 positron, 0 photon */
   uint32_t *tag; /* optional user tag, inherited by children (NULL = none) */
+  double *od_p, *od_r; /* Methods II/III: cumulative probability P_cum and its
+                          random number r3 (0 = not drawn yet); NULL = Method I */
 } orc_species;
 
 typedef struct {
@@ -591,8 +593,43 @@ static void get_fields(const orc_fields *f, const orc_species *s, int64_t i, dou
   }
 }
 
-/* One lepton: gather, Boris push, then Method I with sub-steps.  Emitted
- * photons go to *out in emission order. */
+/* One photon emission (Eq. 7 with r2, recoil, child appended), sub-step k.
+ * p and g are updated to the recoiled lepton. */
+static void emit_photon(const orc_config *cfg, const orc_species *s, int64_t i, int64_t step,
+                        int64_t k, double chi, double r2, double c2, const double E[3],
+                        const double B[3], double p[3], double *g, orc_childlist *out) {
+  double xi = orc_sample_photon(cfg, chi, *g, r2, c2);
+  if (xi > 1.0 - 1.0 / *g) xi = 1.0 - 1.0 / *g; /* lepton keeps gamma >= 1 */
+  double pm = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+  double n[3] = {p[0] / pm, p[1] / pm, p[2] / pm};
+  double eph = xi * *g;
+  double g2 = *g - eph; /* = gamma (1 - xi) */
+  double pm2 = sqrt(fmax(g2 * g2 - 1.0, 0.0));
+  orc_child c;
+  c.x = s->x[i]; c.y = s->y[i]; c.z = s->z[i];
+  c.px = eph * n[0]; c.py = eph * n[1]; c.pz = eph * n[2];
+  c.w = s->w[i];
+  c.tag = s->tag ? s->tag[i] : 0u;
+  uint32_t cid[4];
+  orc_draw(cfg->seed, s->id[i], step, k, ORC_STREAM_PHOTON_ID, cid);
+  c.id = (uint64_t)cid[0] | ((uint64_t)cid[1] << 32);
+  for (int q = 0; q < 3; ++q) { c.f[q] = E[q]; c.f[3 + q] = B[q]; }
+  child_push(out, &c);
+  p[0] = pm2 * n[0]; p[1] = pm2 * n[1]; p[2] = pm2 * n[2];
+  *g = sqrt(1.0 + p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+}
+
+/* One lepton: gather, Boris push, then the photon event generator.  Emitted
+ * photons go to *out in emission order.
+ * Method I (default): W_rad with sub-steps N = max(1, ceil(W Dt / 0.2)); in
+ *   sub-step k a photon is emitted if W Dt/N > r1.
+ * Methods II and III (the paper's alternatives, text around Fig. 2): the
+ *   particle carries a cumulative probability P_cum and a random number r3
+ *   taken when it first needs one (Philox word 3 of its emission draw).  Each
+ *   step P_cum = P_cum + W_rad Dt; a photon is emitted if 1 - exp(-P_cum) > r3
+ *   (Method II) or P_cum > r3 (Method III), after which P_cum restarts at 0
+ *   with a fresh r3 (word 2 of the same draw).  No sub-steps: at most one
+ *   photon per step.  1 - exp(-P) is evaluated as -expm1(-P). */
 static void lepton_one(const orc_config *cfg, const orc_fields *f, orc_species *s, int64_t i,
                        int64_t step, orc_childlist *out, int64_t *substeps) {
   double E[3], B[3];
@@ -605,6 +642,22 @@ static void lepton_one(const orc_config *cfg, const orc_fields *f, orc_species *
 
   double chi = orc_chi_lepton(p, E, B, cfg->a_S);
   double W = orc_rate_photon(cfg, chi, g);
+  if (cfg->generator != 0 && s->od_p && s->od_r) {
+    uint32_t r[4];
+    orc_draw(cfg->seed, s->id[i], step, 0, ORC_STREAM_EMIT, r);
+    if (!(s->od_r[i] > 0.0)) s->od_r[i] = orc_u(r[3]);
+    s->od_p[i] += W * cfg->dt;
+    *substeps += 1;
+    int emit = cfg->generator == 1 ? (-expm1(-s->od_p[i]) > s->od_r[i])
+                                   : (s->od_p[i] > s->od_r[i]);
+    if (emit) {
+      emit_photon(cfg, s, i, step, 0, chi, orc_u(r[1]), orc_uc(r[1]), E, B, p, &g, out);
+      s->od_p[i] = 0.0;
+      s->od_r[i] = orc_u(r[2]);
+    }
+    s->px[i] = p[0]; s->py[i] = p[1]; s->pz[i] = p[2];
+    return;
+  }
   int64_t N = 1;
   if (W * cfg->dt > cfg->wdt_max) N = (int64_t)ceil(W * cfg->dt / cfg->wdt_max);
   double dts = cfg->dt / (double)N;
@@ -613,25 +666,7 @@ static void lepton_one(const orc_config *cfg, const orc_fields *f, orc_species *
     uint32_t r[4];
     orc_draw(cfg->seed, s->id[i], step, k, ORC_STREAM_EMIT, r);
     if (!(W * dts > orc_u(r[0]))) continue;
-    double xi = orc_sample_photon(cfg, chi, g, orc_u(r[1]), orc_uc(r[1]));
-    if (xi > 1.0 - 1.0 / g) xi = 1.0 - 1.0 / g; /* lepton keeps gamma >= 1 */
-    double pm = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
-    double n[3] = {p[0] / pm, p[1] / pm, p[2] / pm};
-    double eph = xi * g;
-    double g2 = g - eph; /* = gamma (1 - xi) */
-    double pm2 = sqrt(fmax(g2 * g2 - 1.0, 0.0));
-    orc_child c;
-    c.x = s->x[i]; c.y = s->y[i]; c.z = s->z[i];
-    c.px = eph * n[0]; c.py = eph * n[1]; c.pz = eph * n[2];
-    c.w = s->w[i];
-    c.tag = s->tag ? s->tag[i] : 0u;
-    uint32_t cid[4];
-    orc_draw(cfg->seed, s->id[i], step, k, ORC_STREAM_PHOTON_ID, cid);
-    c.id = (uint64_t)cid[0] | ((uint64_t)cid[1] << 32);
-    for (int q = 0; q < 3; ++q) { c.f[q] = E[q]; c.f[3 + q] = B[q]; }
-    child_push(out, &c);
-    p[0] = pm2 * n[0]; p[1] = pm2 * n[1]; p[2] = pm2 * n[2];
-    g = sqrt(1.0 + p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+    emit_photon(cfg, s, i, step, k, chi, orc_u(r[1]), orc_uc(r[1]), E, B, p, &g, out);
     chi = orc_chi_lepton(p, E, B, cfg->a_S);
     W = orc_rate_photon(cfg, chi, g);
   }
@@ -706,6 +741,8 @@ static void append_children(orc_species *s, const orc_childlist *l, int64_t *dro
     s->w[k] = c->w; s->id[k] = c->id;
     if (s->tag) s->tag[k] = c->tag;
     if (s->alive) s->alive[k] = 1;
+    if (s->od_p) s->od_p[k] = 0.0; /* a new lepton starts with P_cum = 0 ... */
+    if (s->od_r) s->od_r[k] = 0.0; /* ... and takes its r3 when it first needs one */
     if (s->ex) {
       s->ex[k] = c->f[0]; s->ey[k] = c->f[1]; s->ez[k] = c->f[2];
       s->bx[k] = c->f[3]; s->by[k] = c->f[4]; s->bz[k] = c->f[5];
