@@ -72,6 +72,10 @@ enum {
 
 enum { QED_FP32 = 0, QED_FP64 = 1 };
 enum { QED_SAMPLER_TABLE = 0, QED_SAMPLER_MLP = 1 };
+/* photon event generators (text around Fig. 2): Method I (default; W Dt/N > r1
+ * with sub-steps), Method II (cumulative probability P_cum += W Dt, emit when
+ * 1 - exp(-P_cum) > r3), Method III (emit when P_cum > r3, as printed). */
+enum { QED_GEN_METHOD_I = 0, QED_GEN_METHOD_II = 1, QED_GEN_METHOD_III = 2 };
 enum { QED_FIELDS_UNIFORM = 0, QED_FIELDS_PER_PARTICLE = 1, QED_FIELDS_GRID = 2 };
 
 /* ---- configuration ---------------------------------------------------- */
@@ -95,7 +99,8 @@ typedef struct {
                               2^30 - 4096 */
   int64_t max_substeps;    /* cap on N per particle per step (status bit when hit) */
   int sampler;             /* QED_SAMPLER_TABLE (default) or QED_SAMPLER_MLP (FP32 contexts) */
-  int pad2_;
+  int generator;           /* QED_GEN_METHOD_I (default), _II or _III: photon event generator;
+                              II and III need od_p, od_r on every lepton species */
 } qed_config;
 
 /* Fill *cfg with the paper-derived defaults (FP32, dt = 0.01, seed 0). */
@@ -110,7 +115,10 @@ void qed_config_default(qed_config *cfg);
  * d_n: device int64 holding the current count; appends beyond `capacity` are
  * dropped and counted.  q: -1 electron, +1 positron, 0 photon.
  * tag: optional user tag (e.g. the index of an independent run), copied to the
- * particles a particle creates and moved by compaction; NULL if unused.      */
+ * particles a particle creates and moved by compaction; NULL if unused.
+ * od_p, od_r: the state of event generators II and III (leptons; element type
+ * as x): the cumulative probability P_cum and its random number r3, 0 meaning
+ * "not drawn yet" (new leptons start at 0, 0).  NULL under Method I.        */
 typedef struct {
   void *x, *y, *z, *px, *py, *pz, *w;
   uint64_t *id;
@@ -121,6 +129,7 @@ typedef struct {
   int q;
   int pad_;
   uint32_t *tag;
+  void *od_p, *od_r;
 } qed_species;
 
 /* ---- fields -------------------------------------------------------------

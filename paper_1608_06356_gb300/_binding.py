@@ -21,6 +21,7 @@ QED_FIELDS_UNIFORM, QED_FIELDS_PER_PARTICLE, QED_FIELDS_GRID = 0, 1, 2
 QED_STATUS_CAPACITY, QED_STATUS_DOMAIN, QED_STATUS_NONFINITE = 1, 2, 4
 QED_STATUS_TIMEOUT, QED_STATUS_SUBSTEPS, QED_STATUS_REPLAY = 8, 16, 32
 QED_PROF_PHASES = 7
+QED_GEN_METHOD_I, QED_GEN_METHOD_II, QED_GEN_METHOD_III = 0, 1, 2
 
 ERRORS = {-1: "QED_ERR_ARG", -2: "QED_ERR_CUDA", -3: "QED_ERR_CAPACITY", -4: "QED_ERR_DOMAIN",
           -5: "QED_ERR_TIMEOUT", -6: "QED_ERR_NOCONV", -7: "QED_ERR_NOMEM", -8: "QED_ERR_UNSUPPORTED"}
@@ -41,7 +42,7 @@ class qed_config(C.Structure):
                 ("fwd_per_unit", C.c_double), ("inv_per_unit", C.c_double),
                 ("seed", C.c_uint64), ("spec_lo", C.c_double), ("spec_hi", C.c_double),
                 ("max_particles", C.c_int64), ("max_substeps", C.c_int64),
-                ("sampler", C.c_int), ("pad2_", C.c_int)]
+                ("sampler", C.c_int), ("generator", C.c_int)]
 
 
 class qed_species(C.Structure):
@@ -49,7 +50,7 @@ class qed_species(C.Structure):
                [("id", C.c_void_p), ("alive", C.c_void_p)] + \
                [(n, C.c_void_p) for n in ("ex", "ey", "ez", "bx", "by", "bz")] + \
                [("d_n", C.c_void_p), ("capacity", C.c_int64), ("q", C.c_int), ("pad_", C.c_int),
-                ("tag", C.c_void_p)]
+                ("tag", C.c_void_p), ("od_p", C.c_void_p), ("od_r", C.c_void_p)]
 
 
 class qed_fields(C.Structure):

@@ -95,6 +95,8 @@ class Species:
     by: torch.Tensor | None = None
     bz: torch.Tensor | None = None
     tag: torch.Tensor | None = None   # int32 storage of the uint32 tags
+    od_p: torch.Tensor | None = None  # event generators II/III: cumulative probability
+    od_r: torch.Tensor | None = None  # ... and its random number r3 (0 = not drawn yet)
 
     @property
     def capacity(self) -> int:
@@ -102,7 +104,7 @@ class Species:
 
     @staticmethod
     def empty(capacity: int, q: int, dtype=torch.float32, device="cuda", fields=False,
-              alive=None, tag=False) -> "Species":
+              alive=None, tag=False, od=False) -> "Species":
         cap = max(int(capacity), 0)
         mk = lambda: torch.zeros(cap, dtype=dtype, device=device)
         kw = {k: mk() for k in STATE}
@@ -114,6 +116,7 @@ class Species:
                        n=torch.zeros(1, dtype=torch.int64, device=device), q=q,
                        alive=torch.zeros(cap, dtype=torch.uint8, device=device) if alive else None,
                        tag=torch.zeros(cap, dtype=torch.int32, device=device) if tag else None,
+                       od_p=mk() if od else None, od_r=mk() if od else None,
                        **kw)
 
     def load(self, **arrays) -> "Species":
@@ -137,7 +140,7 @@ class Species:
 
     def host(self, names=None) -> dict:
         n = self.count()
-        names = names or [k for k in STATE + ("id", "alive", "tag") + FIELD_NAMES
+        names = names or [k for k in STATE + ("id", "alive", "tag", "od_p", "od_r") + FIELD_NAMES
                           if getattr(self, k) is not None]
         out = {}
         for k in names:
@@ -150,7 +153,7 @@ class Species:
 
     def struct(self) -> B.qed_species:
         s = B.qed_species()
-        for k in STATE + FIELD_NAMES + ("id", "alive", "tag"):
+        for k in STATE + FIELD_NAMES + ("id", "alive", "tag", "od_p", "od_r"):
             t = getattr(self, k)
             setattr(s, k, t.data_ptr() if t is not None and t.numel() else None)
         s.d_n = self.n.data_ptr()

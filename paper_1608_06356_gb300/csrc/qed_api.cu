@@ -161,7 +161,9 @@ static bool cfg_valid(const qed_config *c) {
          c->spec_lo > 0 && c->spec_hi > c->spec_lo && c->max_particles > 0 &&
          c->max_particles <= ((int64_t)1 << 30) - 4096 && c->max_substeps >= 1 &&
          (c->sampler == QED_SAMPLER_TABLE ||
-          (c->sampler == QED_SAMPLER_MLP && c->precision == QED_FP32));
+          (c->sampler == QED_SAMPLER_MLP && c->precision == QED_FP32)) &&
+         (c->generator == QED_GEN_METHOD_I || c->generator == QED_GEN_METHOD_II ||
+          c->generator == QED_GEN_METHOD_III);
 }
 
 extern "C" int qed_init_tables(const qed_config *cfg, qed_ctx **out, qed_stream_t stream) {
@@ -308,10 +310,15 @@ extern "C" int qed_gather_push(qed_ctx *c, const qed_species *s, const qed_field
   return cuda_fail(e, "qed_gather_push");
 }
 
+// Event generators II and III keep per-lepton state (od_p, od_r).
+static bool od_ok(const qed_ctx *c, const qed_species *s) {
+  return c->cfg.generator == QED_GEN_METHOD_I || !s || s->capacity == 0 || (s->od_p && s->od_r);
+}
+
 extern "C" int qed_emit(qed_ctx *c, const qed_species *l, const qed_species *g, const qed_fields *f,
                         int64_t step, qed_stream_t stream) {
   if (!c || !species_ok(l, false) || !species_ok(g, true) || !fields_ok(f) || !pp_fields_ok(l, f) ||
-      l->q == 0)
+      l->q == 0 || !od_ok(c, l))
     return QED_ERR_ARG;
   if (check_cap(c, l) || check_cap(c, g)) return QED_ERR_CAPACITY;
   cudaStream_t st = (cudaStream_t)stream;
@@ -364,7 +371,8 @@ extern "C" int qed_step_fused(qed_ctx *c, const qed_species *e, const qed_specie
                               const qed_species *g, const qed_fields *f, int64_t step,
                               qed_stream_t stream) {
   if (!c || !species_ok(e, false) || !species_ok(p, false) || !species_ok(g, true) ||
-      !fields_ok(f) || !pp_fields_ok(e, f) || !pp_fields_ok(p, f) || !pp_fields_ok(g, f))
+      !fields_ok(f) || !pp_fields_ok(e, f) || !pp_fields_ok(p, f) || !pp_fields_ok(g, f) ||
+      !od_ok(c, e) || !od_ok(c, p))
     return QED_ERR_ARG;
   if (check_cap(c, e) || check_cap(c, p) || check_cap(c, g)) return QED_ERR_CAPACITY;
   cudaStream_t st = (cudaStream_t)stream;

@@ -54,6 +54,8 @@ template <> __device__ __forceinline__ float unif<float>(uint32_t w) {
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float m_log(float x) { return logf(x); }
 __device__ __forceinline__ double m_log(double x) { return log(x); }
+__device__ __forceinline__ float m_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double m_expm1(double x) { return expm1(x); }
 __device__ __forceinline__ float m_log1p(float x) { return log1pf(x); }
 __device__ __forceinline__ double m_log1p(double x) { return log1p(x); }
 __device__ __forceinline__ float m_exp(float x) { return expf(x); }
@@ -173,6 +175,7 @@ struct Consts {
   uint64_t seed;
   int64_t max_substeps;
   int pair_sign;
+  int generator;            // photon event generator: 0 Method I, 1 Method II, 2 Method III
   double inv_aS, alpha_aS;  // 1/a_S and alpha a_S
   // the same constants in single precision, so that the FP32 path does no FP64 work
   float f_dt, f_wdt_max, f_xi_min_energy, f_chi_pair_min, f_spec_lo, f_spec_scale, f_inv_aS,

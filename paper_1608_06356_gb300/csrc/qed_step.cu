@@ -35,6 +35,7 @@ template <class Real> struct Sp {
   int64_t cap;
   Real q;
   uint32_t *tag;  // optional, inherited by children
+  Real *od_p, *od_r;  // event generators II/III: P_cum and r3 (0 = not drawn yet)
 };
 
 template <class Real> struct Fld {
@@ -45,6 +46,7 @@ template <class Real> struct Fld {
 };
 
 enum { FM_UNIFORM = 0, FM_PER_PARTICLE = 1, FM_GRID = 2 };
+enum { GEN_METHOD_I = 0, GEN_METHOD_II = 1, GEN_METHOD_III = 2 };
 enum { MODE_PUSH = 0, MODE_EMIT = 1, MODE_FUSED = 2 };
 // classes of the streaming lepton pass: 1 one sub-step with an event; 2-5 more
 // than one sub-step, binned by N (<= 3, <= 7, <= 15, >= 16)
@@ -276,6 +278,7 @@ __device__ __forceinline__ void write_child(const Sp<Real> &d, int64_t slot, Rea
   d.id[slot] = id;
   if (d.tag) d.tag[slot] = tag;
   if (d.alive) d.alive[slot] = 1;
+  if (d.od_p) { d.od_p[slot] = (Real)0; d.od_r[slot] = (Real)0; }
   if (d.ex) {
     d.ex[slot] = E[0]; d.ey[slot] = E[1]; d.ez[slot] = E[2];
     d.bx[slot] = B[0]; d.by[slot] = B[1]; d.bz[slot] = B[2];
@@ -428,7 +431,24 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 3 : 2) k_lepton_stre
         t0.clear();
         RateOut<Real> ro = photon_rate(sR, sF, A.T, A.C, chi, g, t0);
         const Real wdt = ro.W * dt;
-        if (wdt > wdt_max) {
+        if (A.C.generator != GEN_METHOD_I) {
+          // Methods II/III: P_cum += W Dt; an event when 1 - exp(-P_cum) > r3
+          // (II) or P_cum > r3 (III); r3 is word 3 of the emission draw when
+          // not drawn yet.  The emission itself (and the new P_cum, r3) is the
+          // counting pass's, as a one-sub-step particle with an event.
+          const U4 r = draw(A.C.seed, pid, step_, 0, STREAM_EMIT);
+          Real r3 = S.od_r[i];
+          const bool fresh = !(r3 > (Real)0);
+          if (fresh) r3 = unif<Real>(r.w);
+          const Real P = S.od_p[i] + wdt;
+          const bool ev = A.C.generator == GEN_METHOD_II ? -m_expm1(-P) > r3 : P > r3;
+          if (ev) {
+            flag = 1;
+          } else {
+            S.od_p[i] = P;
+            if (fresh) S.od_r[i] = r3;
+          }
+        } else if (wdt > wdt_max) {
           // classes by sub-step count N = ceil(W Dt / wdt_max): 2: N <= 3, 3: N <= 7,
           // 4: N <= 15, 5: N >= 16 (lanes of a warp then do similar amounts of work)
           const Real q = r_div(wdt, wdt_max);
@@ -668,10 +688,18 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 && !MLP ? 3 : 2) k_sub
   Real E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
   uint64_t pid = 0;
   RateOut<Real> ro{(Real)0, (Real)-1e30, (Real)0};
+  // Methods II/III: the particle's species, index and the word for its next r3
+  int psi = 0;
+  int64_t pi = 0;
+  uint32_t w3 = 0;
   auto finish = [&]() {
     tl.events += cnt;
     A.sub_cnt[h] = cnt;
     if (h < rc) A.sub_gf[h] = g;
+    if (A.C.generator != GEN_METHOD_I) {  // P_cum restarts with a fresh r3 (word 2)
+      A.sp[psi].od_p[pi] = (Real)0;
+      A.sp[psi].od_r[pi] = unif<Real>(w3);
+    }
     state = LS_IDLE;
   };
   for (;;) {
@@ -705,12 +733,26 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 && !MLP ? 3 : 2) k_sub
           unit_dir(P, nx, ny, nz);
           chi = chi_lepton(px, py, pz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
           ro = photon_rate(sR, sF, A.T, A.C, chi, g, tl);
-          N = substep_count(A.C, ro.W, dt, wdt_max, tl.status);
-          tl.substeps += N;
-          dts = dt / (Real)N;
           k = 0;
           cnt = 0;
-          state = LS_SCAN;
+          if (A.C.generator != GEN_METHOD_I) {
+            // Methods II/III: the streaming pass found the event; one photon,
+            // its xi from word 1 of the step's emission draw
+            const U4 r = draw(A.C.seed, pid, step_, 0, STREAM_EMIT);
+            N = 1;
+            dts = dt;
+            wy = r.y;
+            w3 = r.z;
+            psi = P.si;
+            pi = P.i;
+            tl.substeps += 1;
+            state = LS_PEND;
+          } else {
+            N = substep_count(A.C, ro.W, dt, wdt_max, tl.status);
+            tl.substeps += N;
+            dts = dt / (Real)N;
+            state = LS_SCAN;
+          }
         }
       }
       next += __popc(idle);
@@ -933,12 +975,13 @@ __global__ void __launch_bounds__(TILE, REPLAY || sizeof(Real) == 8 ? 2 : 4) k_s
       const Real *E = P.E, *B = P.B;
       Real chi = chi_lepton(P.px, P.py, P.pz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
       RateOut<Real> ro = photon_rate(sR, sF, A.T, A.C, chi, g, dummy);
-      const int64_t N = substep_count(A.C, ro.W, dt, wdt_max, dummy.status);
+      const bool forced = A.C.generator != GEN_METHOD_I;  // Methods II/III: one photon at k = 0
+      const int64_t N = forced ? 1 : substep_count(A.C, ro.W, dt, wdt_max, dummy.status);
       const Real dts = dt / (Real)N;
       uint32_t j = 0;
       for (int64_t kk = 0; kk < N && j < cnt; ++kk) {
         U4 r = draw(A.C.seed, P.id, step_, kk, STREAM_EMIT);
-        if (!(ro.W * dts > unif<Real>(r.x))) continue;
+        if (!forced && !(ro.W * dts > unif<Real>(r.x))) continue;
         XiOut<Real> xo = photon_xi(A.T.Y, A.T, ro.l, chi, ro.kmin, unif<Real>(r.y), unif<Real>(~r.y), dummy);
         Real g2 = g * xo.omxi, eph = g * xo.xi;
         if (g2 < (Real)1) { g2 = (Real)1; eph = g - (Real)1; }
@@ -1962,6 +2005,7 @@ template <class Real> Sp<Real> to_sp(const qed_species *s) {
   d.bx = (Real *)s->bx; d.by = (Real *)s->by; d.bz = (Real *)s->bz;
   d.d_n = s->d_n; d.cap = s->capacity; d.q = (Real)s->q;
   d.tag = s->tag;
+  d.od_p = (Real *)s->od_p; d.od_r = (Real *)s->od_r;
   return d;
 }
 
@@ -1996,6 +2040,7 @@ Consts consts_of(const qed_ctx *c) {
   k.dt = c->cfg.dt;
   k.wdt_max = c->cfg.wdt_max;
   k.xi_min_energy = c->cfg.xi_min_energy;
+  k.generator = c->cfg.generator;
   k.chi_pair_min = c->cfg.chi_pair_min;
   k.spec_lo = c->cfg.spec_lo;
   k.spec_scale = 64.0 / log(c->cfg.spec_hi / c->cfg.spec_lo);

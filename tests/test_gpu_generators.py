@@ -1,0 +1,122 @@
+"""Event generators II and III (the paper's alternatives to Method I, text
+around Fig. 2) on the GPU: the first-emission survival law at 2^20 identical
+electrons, and element-wise parity with the oracle over two steps.
+
+Survival: with W Dt = a fixed until the first emission, P(no emission after n
+steps) = exp(-n a) for Method II and 1 - n a for Method III; a is the GPU's own
+rate (qed_rates) at the electrons' chi and gamma; tolerance 5 binomial sigma.
+Parity (push + emission, i.e. qed_gather_push then qed_emit against the
+oracle's lepton pass): momenta 2e-5 relative, P_cum 1e-4 relative (the rate
+tables' accuracy), r3 to FP32 rounding, photons by id; electrons whose
+decision value lies within 1e-4 (relative) of r3 in either step are excluded
+and counted."""
+import numpy as np
+import pytest
+import torch
+
+from _parity import by_id, to32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1608_06356_gb300 import api as A
+    return A
+
+
+@pytest.mark.parametrize("gen", [1, 2])
+def test_first_emission_survival(api, orc, gen):
+    n, steps, dt, gamma0, chi0 = 1 << 20, 20, 0.04, 1000.0, 0.5
+    ctx = api.qed_init_tables(api.config(dt=dt, seed=5, generator=gen))
+    bz = np.float32(chi0 * orc.A_S_1UM / gamma0)
+    F = api.Fields.uniform((0, 0, 0), (0, 0, float(bz)))
+    p0 = np.float32(np.sqrt(gamma0 ** 2 - 1.0))
+    z = np.zeros(n, np.float32)
+    e = api.Species.empty(n, -1, od=True).load(
+        x=z, y=z, z=z, px=np.full(n, p0, np.float32), py=z, pz=z, w=np.ones(n, np.float32),
+        id=np.arange(n, dtype=np.uint64))
+    g = api.Species.empty(2 * n, 0)
+    chi = orc.chi_lepton([float(p0), 0, 0], [0, 0, 0], [0, 0, float(bz)])
+    gam = float(np.sqrt(1.0 + float(p0) ** 2))
+    a = float(api.qed_rates(ctx, 0, torch.tensor([chi], device="cuda"),
+                            torch.tensor([gam], device="cuda"))[0]) * dt
+    assert 0.03 < a < 0.1
+    first = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    for s in range(steps):
+        api.qed_emit(ctx, e, g, F, s)  # no push: chi and W stay fixed until an emission
+        first[(first < 0) & (e.od_p[:n] == 0)] = s
+    torch.cuda.synchronize()
+    first = first.cpu().numpy()
+    if gen == 1:
+        law = lambda k: np.exp(-k * a)
+    else:
+        law = lambda k: max(0.0, 1.0 - k * a)
+    for k in range(1, steps + 1):
+        s_meas = np.mean((first < 0) | (first >= k))
+        s_exp = law(k)
+        sigma = np.sqrt(max(s_exp * (1 - s_exp), 1e-6) / n)
+        assert abs(s_meas - s_exp) < 5 * sigma + 2e-4, (k, s_meas, s_exp)
+    assert api.qed_read_counters(ctx)["status"] == 0
+
+
+@pytest.mark.parametrize("gen", [1, 2])
+def test_generator_matches_oracle(api, orc, gen):
+    from paper_1608_06356_gb300 import workloads as W
+    n, dt, seed = 3000, 0.02, 11
+    st, _, _ = W.chi_target(n, seed=41, chi_lo=0.05, chi_hi=20.0, g_lo=200, g_hi=5e3)
+    st = to32(st)
+    ctx = api.qed_init_tables(api.config(dt=dt, seed=seed, generator=gen))
+    e = api.Species.empty(n, -1, fields=True, od=True).load(**st)
+    cfg = orc.make_config(dt=dt, seed=seed, generator=gen)
+    oe = orc.Species(n, -1.0, per_particle_fields=True, with_od=True).load(**st)
+    F, OF = api.Fields.per_particle(), orc.per_particle_fields()
+    ambiguous = np.zeros(n, bool)
+    gpu_ph, orc_ph = [], []
+    for s in (3, 4):
+        og = orc.Species(4 * n, 0.0, per_particle_fields=True, with_alive=True)
+        orc.step(cfg, OF, oe, None, og, s)
+        g = api.Species.empty(4 * n, 0, fields=True)
+        api.qed_gather_push(ctx, e, F, s)
+        api.qed_emit(ctx, e, g, F, s)
+        gpu_ph.append(g.host())
+        orc_ph.append({k: og.view(k).copy() for k in ("id", "px", "py", "pz")})
+        # decision value against r3 (non-emitters: the accumulated P_cum; for an
+        # emitter the value crossed r3, which the oracle then replaced)
+        emitted = oe.view("od_p") == 0.0
+        P = oe.view("od_p")
+        val = -np.expm1(-P) if gen == 1 else P
+        r3 = oe.view("od_r")
+        ambiguous |= ~emitted & (np.abs(val - r3) <= 1e-4 * r3 + 1e-7)
+        # (an emitter barely above its old r3 flips on the other side at most
+        # as often; such flips are bounded below and left out of the comparison)
+    torch.cuda.synchronize()
+    h = e.host()
+    ok = ~ambiguous
+    assert ambiguous.sum() <= 0.01 * n
+    emit_g, emit_o = h["od_p"] == 0, oe.view("od_p") == 0
+    assert (emit_g[ok] != emit_o[ok]).sum() <= 0.002 * n + 2
+    both = ok & (emit_g == emit_o)
+    np.testing.assert_allclose(h["od_r"][both], oe.view("od_r")[both], rtol=2e-7)
+    np.testing.assert_allclose(h["od_p"][both], oe.view("od_p")[both], rtol=1e-4, atol=1e-9)
+    for k in ("px", "py", "pz"):
+        np.testing.assert_allclose(h[k][both], oe.view(k)[both], rtol=2e-5, atol=1e-3)
+    for gh, oh in zip(gpu_ph, orc_ph):
+        gi, gs = by_id(gh)
+        oi, os_ = by_id(oh)
+        common, ig, io = np.intersect1d(gi, oi, return_indices=True)
+        assert len(common) > 50
+        assert len(gi) + len(oi) - 2 * len(common) <= 0.004 * n + 4
+        eg = np.sqrt(gs["px"][ig].astype(float) ** 2 + gs["py"][ig] ** 2 + gs["pz"][ig] ** 2)
+        eo = np.sqrt(os_["px"][io] ** 2 + os_["py"][io] ** 2 + os_["pz"][io] ** 2)
+        np.testing.assert_allclose(eg, eo, rtol=2e-5)
+
+
+def test_generator_state_required(api):
+    ctx = api.qed_init_tables(api.config(generator=1))
+    e = api.Species.empty(16, -1).load(x=np.zeros(4, np.float32))
+    g = api.Species.empty(16, 0)
+    with pytest.raises(Exception):
+        api.qed_emit(ctx, e, g, api.Fields.uniform((0, 0, 0), (0, 0, 1)), 0)
