@@ -270,6 +270,38 @@ def batched_runs_bench(api, torch, mlp_weights, steps=4):
     return out
 
 
+def generator_rates(api, torch, steps=480, dt=0.01):
+    """The paper's Fig. 2 setting: one electron per cell of 128 x 192 cells,
+    gamma = 206, B giving chi_e = 0.1, 480 steps; the average photon
+    generation rate with event generators I, II and III against W_rad at the
+    initial state (Eq. 1 with the xi_min cut, from the GPU's tables)."""
+    n, gamma0, bz = 128 * 192, 206.0, 200.0
+    p0 = np.float32(np.sqrt(gamma0 ** 2 - 1.0))
+    chi = float(p0) * bz / api.config().a_S  # |p x B| / a_S for p along x, B along z, E = 0
+    out = {"electrons": n, "gamma0": gamma0, "chi0": chi, "steps": steps, "dt": dt}
+    for gen, name in ((0, "I"), (1, "II"), (2, "III")):
+        ctx = api.qed_init_tables(api.config(dt=dt, seed=17, generator=gen))
+        z = np.zeros(n, np.float32)
+        e = api.Species.empty(n, -1, od=gen != 0).load(
+            x=z, y=z, z=z, px=np.full(n, p0, np.float32), py=z, pz=z, w=np.ones(n, np.float32),
+            id=np.arange(n, dtype=np.uint64))
+        g = api.Species.empty(n * 16, 0)
+        F = api.Fields.uniform((0, 0, 0), (0, 0, bz))
+        per_step = torch.zeros(steps, dtype=torch.int64, device="cuda")
+        for s in range(steps):
+            api.qed_gather_push(ctx, e, F, s)
+            api.qed_emit(ctx, e, g, F, s)
+            per_step[s].copy_(g.n[0])
+        torch.cuda.synchronize()
+        cum = per_step.cpu().numpy()
+        W0 = float(api.qed_rates(ctx, 0, torch.tensor([chi], device="cuda"),
+                                 torch.tensor([float(np.sqrt(1 + float(p0) ** 2))], device="cuda"))[0])
+        out["W_rad_initial"] = W0
+        out[name] = {"rate_first_48_steps": float(cum[47]) / (n * 48 * dt),
+                     "rate_all_steps": float(cum[-1]) / (n * steps * dt)}
+    return out
+
+
 def cpu_baseline(sample_n=12288, steps=2, seed=0):
     """The FP64 oracle as it stands on a bounded sample of the same workload."""
     import oracle as O
@@ -342,6 +374,7 @@ def main():
     ap.add_argument("--sampler-bench", type=int, default=1)
     ap.add_argument("--batched-bench", type=int, default=1)
     ap.add_argument("--mlp-train-samples", type=float, default=4e9)
+    ap.add_argument("--generator-bench", type=int, default=1)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -522,6 +555,7 @@ def main():
             "config": workload_desc(n), "roofline": roofline, "e2e": e2e,
             "gpu_launches": launches, "clocks": clocks, "sampler_table_vs_mlp": sampler,
             "batched_runs": batched,
+            "event_generators_fig2": generator_rates(api, torch) if args.generator_bench else None,
             "counters": {"emit_events": emitted,
                          "pair_events": c_after["pair_events"] - c_before["pair_events"],
                          "substeps": c_after["substeps"] - c_before["substeps"],

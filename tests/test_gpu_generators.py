@@ -120,3 +120,40 @@ def test_generator_state_required(api):
     g = api.Species.empty(16, 0)
     with pytest.raises(Exception):
         api.qed_emit(ctx, e, g, api.Fields.uniform((0, 0, 0), (0, 0, 1)), 0)
+
+
+def test_fig2_rate_equivalence(api, orc):
+    """The paper's Fig. 2 setting: one electron per cell of a 128 x 192 grid
+    (24576 electrons), gamma = 206, a field giving chi_e = 0.1 (Fig. 1's
+    parameters); the average photon-generation rate over the first 48 steps
+    with each generator against W_rad of Eq. (1) at the initial state.
+    Methods I and II give W_rad (Method II: (1 - e^-a)/Dt per fresh step).
+    Method III as printed is a renewal process with uniform waiting depth, so
+    from a fresh start it emits e^D - 1 photons over optical depth D <= 1
+    instead of D -- and 2 W_rad in the long run."""
+    n, dt, gamma0, steps = 128 * 192, 0.01, 206.0, 48
+    bz = 200.0
+    p0 = np.float32(np.sqrt(gamma0 ** 2 - 1.0))
+    chi = orc.chi_lepton([float(p0), 0, 0], [0, 0, 0], [0, 0, bz])
+    rates = {}
+    for gen in (0, 1, 2):
+        ctx = api.qed_init_tables(api.config(dt=dt, seed=17, generator=gen))
+        z = np.zeros(n, np.float32)
+        e = api.Species.empty(n, -1, od=gen != 0).load(
+            x=z, y=z, z=z, px=np.full(n, p0, np.float32), py=z, pz=z, w=np.ones(n, np.float32),
+            id=np.arange(n, dtype=np.uint64))
+        g = api.Species.empty(n * steps, 0)
+        F = api.Fields.uniform((0, 0, 0), (0, 0, bz))
+        for s in range(steps):
+            api.qed_gather_push(ctx, e, F, s)
+            api.qed_emit(ctx, e, g, F, s)
+        torch.cuda.synchronize()
+        rates[gen] = g.count() / (n * steps * dt)
+        W = float(api.qed_rates(ctx, 0, torch.tensor([chi], device="cuda"),
+                                torch.tensor([float(np.sqrt(1 + float(p0) ** 2))], device="cuda"))[0])
+    tol = 5 / np.sqrt(W * n * steps * dt)  # 5 sigma of the Poisson count
+    D = W * dt * steps
+    # recoil moves W by about 1% over 48 steps
+    assert abs(rates[0] / W - 1) < tol + 0.02, (rates, W)
+    assert abs(rates[1] / W - 1) < tol + 0.02, (rates, W)
+    assert abs(rates[2] / (W * np.expm1(D) / D) - 1) < tol + 0.03, (rates, W, D)
