@@ -190,7 +190,10 @@ extern "C" int qed_init_tables(const qed_config *cfg, qed_ctx **out, qed_stream_
       return g;
     };
     c->gl = mk(log(cfg->chi_min), log(cfg->chi_max), hf);
-    c->gy = mk(-18.0, 4.5, hf);
+    // y = ln delta_min ~ ln(4 / (3 gamma chi)) falls with chi: the lower end
+    // moves down with chi_max beyond 1e3 (gamma chi up to ~1e11 at chi = 1e5)
+    const double y_lo = -18.0 - 1.5 * fmax(0.0, log(cfg->chi_max / 1e3));
+    c->gy = mk(y_lo, 4.5, hf);
     c->gk = mk(-24.0, 4.75, hk);
     c->glp = mk(log(cfg->chi_pair_min), log(cfg->chi_pair_max), hf);
     c->gkp = mk(-23.0, 3.5, hk);
