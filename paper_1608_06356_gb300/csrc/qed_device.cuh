@@ -342,8 +342,10 @@ __device__ __forceinline__ RateOut<Real> photon_rate(const Real *R, const Real *
 // -ln(1 - u) = -ln(1 - r2) - ln(1 - u_min) and wmin = e^kmin = -ln(1 - u_min).
 template <class Real>
 __device__ __forceinline__ Real photon_kappa(Real kmin, Real r2, Real c2) {
-  Real wc = r2 < (Real)0.5 ? -m_log1p(-r2) : -m_log(c2);
-  return m_log(wc + m_exp(kmin));
+  // -ln(1 - r2) keeps its relative accuracy for small r2 (log1p); kappa
+  // itself needs only a small absolute error (reduced-precision log and exp)
+  Real wc = r2 < (Real)0.5 ? -m_log1p(-r2) : -r_log(c2);
+  return r_log(wc + r_exp(kmin));
 }
 
 // ln delta from the inverse table at (l, kappa) (linear asymptotes outside).
@@ -363,8 +365,8 @@ __device__ __forceinline__ Real photon_lndelta_table(const Real *Yt, const Table
 template <class Real> struct XiOut { Real xi, omxi; };
 template <class Real>
 __device__ __forceinline__ XiOut<Real> xi_from_lndelta(Real chi, Real Y) {
-  Real a = (Real)1.5 * chi * m_exp(Y);
-  Real inv = (Real)1 / ((Real)1 + a);
+  Real a = (Real)1.5 * chi * r_exp(Y);
+  Real inv = r_div((Real)1, (Real)1 + a);
   return XiOut<Real>{a * inv, inv};
 }
 

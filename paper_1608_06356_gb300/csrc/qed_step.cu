@@ -793,7 +793,11 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 && !MLP ? 3 : 2) k_sub
         }
         ++cnt;
         int b = spec_bin(A.C, eph);
-        if (b >= 0) atomicAdd(&bt.hist[b], 1ull);
+        {  // one shared atomic per distinct bin among the emitting lanes
+          const unsigned em = __activemask();
+          const unsigned same = __match_any_sync(em, b);
+          if (b >= 0 && lane == __ffs(same) - 1) atomicAdd(&bt.hist[b], (unsigned long long)__popc(same));
+        }
         Real pm2 = m_sqrt((g2 - (Real)1) * (g2 + (Real)1));
         px = pm2 * nx; py = pm2 * ny; pz = pm2 * nz;
         g = g2;
@@ -938,13 +942,22 @@ __global__ void __launch_bounds__(TILE, REPLAY || sizeof(Real) == 8 ? 2 : 4) k_s
     // sub_cnt holds the exclusive prefix of the counts now
     const uint32_t off = A.sub_cnt[h];
     const uint32_t cnt = (h + 1 < nh ? A.sub_cnt[h + 1] : total) - off;
+    const int32_t e = A.heavy_list[begin + h];
     if (!REPLAY && cnt > 0 && (cnt > REC || h >= rc)) {  // its photons are not all recorded
       A.replay_list[atomicAdd(A.replay_n, 1u)] = (int32_t)h;
       continue;
     }
-    const int32_t e = A.heavy_list[begin + h];
     if (cnt == 0 && e >= 0) continue;  // staged, no photon: the streaming pass stored it
     const int64_t out0 = nph + (int64_t)off;
+    // the first record and the final gamma are loaded with the entry itself
+    // (one round trip to memory instead of three in a row)
+    Real rec0 = 0, gfin = 0;
+    uint32_t krec0 = 0;
+    if (!REPLAY && cnt > 0) {
+      rec0 = A.rec_e[h];
+      krec0 = A.rec_k[h];
+      gfin = A.sub_gf[h];
+    }
     Entry<Real> P;
     load_entry<Real, FM, MODE>(A, e, T0, dt, P);
     Real nx, ny, nz;
@@ -966,8 +979,9 @@ __global__ void __launch_bounds__(TILE, REPLAY || sizeof(Real) == 8 ? 2 : 4) k_s
                   (uint64_t)cid.x | ((uint64_t)cid.y << 32), P.E, P.B, P.tag);
     };
     if (!REPLAY) {
-      for (uint32_t j = 0; j < cnt; ++j) put(j, A.rec_e[j * rc + h], (int64_t)A.rec_k[j * rc + h]);
-      g = A.sub_gf[h];
+      put(0, rec0, (int64_t)krec0);
+      for (uint32_t j = 1; j < cnt; ++j) put(j, A.rec_e[j * rc + h], (int64_t)A.rec_k[j * rc + h]);
+      g = gfin;
     } else {
       // more photons than records: replay the chain (same draws, same tables)
       Tally dummy;
