@@ -48,17 +48,24 @@ class Config(C.Structure):
     _fields_ = [("a_S", C.c_double), ("alpha", C.c_double), ("dt", C.c_double),
                 ("wdt_max", C.c_double), ("xi_min_energy", C.c_double),
                 ("pair_sign", C.c_int), ("generator", C.c_int), ("seed", C.c_uint64),
-                ("spec_lo", C.c_double), ("spec_hi", C.c_double)]
+                ("spec_lo", C.c_double), ("spec_hi", C.c_double), ("model", C.c_int),
+                ("pad_", C.c_int)]
 
 
 GEN_METHOD_I, GEN_METHOD_II, GEN_METHOD_III = 0, 1, 2
 
 
+MODEL_FORMULA_I, MODEL_CLASSIC = 0, 1
+
+
 def make_config(dt=0.01, a_S=A_S_1UM, alpha=ALPHA, wdt_max=0.2, xi_min_energy=2.0,
-                pair_sign=1, seed=0, spec_lo=2.0, spec_hi=1000.0, generator=GEN_METHOD_I) -> Config:
-    """generator: photon event generator, Method I (default), II or III."""
+                pair_sign=1, seed=0, spec_lo=2.0, spec_hi=1000.0, generator=GEN_METHOD_I,
+                model=MODEL_FORMULA_I) -> Config:
+    """generator: photon event generator, Method I (default), II or III.
+    model: photon spectrum, formula I (Eq. 1, default) or the classic limit
+    (Eq. 5) restricted to 0 < xi < 1."""
     return Config(a_S, alpha, dt, wdt_max, xi_min_energy, pair_sign, generator, seed, spec_lo,
-                  spec_hi)
+                  spec_hi, model, 0)
 
 
 class Fields(C.Structure):
@@ -103,6 +110,7 @@ def lib():
             "orc_spec_pair": (d, [d, d, C.c_int]),
             "orc_J": (d, [C.c_int, d]),
             "orc_cum_photon": (d, [d, d, d]),
+            "orc_cum_photon_m": (d, [d, d, d, C.c_int]),
             "orc_cum_pair": (d, [d, d, d, C.c_int]),
             "orc_rate_photon": (d, [P(Config), d, d]),
             "orc_rate_pair": (d, [P(Config), d, d]),
@@ -169,8 +177,8 @@ def spec_pair(xi, chi, sign=1):
     return lib().orc_spec_pair(float(xi), float(chi), int(sign))
 
 
-def cum_photon(a, b, chi):
-    return lib().orc_cum_photon(float(a), float(b), float(chi))
+def cum_photon(a, b, chi, model=MODEL_FORMULA_I):
+    return lib().orc_cum_photon_m(float(a), float(b), float(chi), int(model))
 
 
 def cum_pair(a, b, chi, sign=1):

@@ -286,17 +286,26 @@ double orc_spec_pair(double xi, double chi, int sign) {
 /* int_a^b spec_I(xi) dxi, computed in tau = xi^(1/3) (dxi = 3 tau^2 dtau)
  * so that the xi^(-2/3) behaviour at xi -> 0 becomes a bounded integrand. */
 typedef struct { double chi; int sign; } orc_spec_ctx;
-static double photon_tau_integrand(double tau, const void *c) {
-  double xi = tau * tau * tau;
-  return 3.0 * tau * tau * orc_spec_I(xi, ((const orc_spec_ctx *)c)->chi);
+/* The photon spectrum of the chosen model: formula I (Eq. 1), or the classic
+ * limit (Eq. 5) restricted, like formula I, to photons below the lepton's
+ * energy (0 < xi < 1). */
+static double spec_photon(double xi, double chi, int model) {
+  return model == 1 ? (xi < 1.0 ? orc_spec_classic(xi, chi) : 0.0) : orc_spec_I(xi, chi);
 }
-double orc_cum_photon(double a, double b, double chi) {
+static double photon_tau_integrand(double tau, const void *c) {
+  const orc_spec_ctx *s = (const orc_spec_ctx *)c;
+  double xi = tau * tau * tau;
+  return 3.0 * tau * tau * spec_photon(xi, s->chi, s->sign);
+}
+/* int_a^b of the photon spectrum of `model` (sign field carries the model) */
+double orc_cum_photon_m(double a, double b, double chi, int model) {
   if (a < 0.0) a = 0.0;
   if (b > 1.0) b = 1.0;
   if (!(b > a)) return 0.0;
-  orc_spec_ctx c = {chi, 1};
+  orc_spec_ctx c = {chi, model};
   return orc_integrate(photon_tau_integrand, &c, cbrt(a), cbrt(b), 8, 1e-12, 0.0);
 }
+double orc_cum_photon(double a, double b, double chi) { return orc_cum_photon_m(a, b, chi, 0); }
 
 static double pair_integrand(double xi, const void *c) {
   const orc_spec_ctx *s = (const orc_spec_ctx *)c;
@@ -329,6 +338,8 @@ typedef struct {
   int generator;        /* photon event generator: 0 Method I, 1 Method II, 2 Method III */
   uint64_t seed;        /* Philox key */
   double spec_lo, spec_hi; /* photon-energy histogram range (m c^2), 64 log bins */
+  int model;            /* photon spectrum: 0 formula I (Eq. 1), 1 classic limit (Eq. 5) */
+  int pad_;
 } orc_config;
 
 /* Eq. (1) integrated from xi_min to 1, times alpha a_S / gamma. */
@@ -336,7 +347,7 @@ double orc_rate_photon(const orc_config *cfg, double chi, double gamma) {
   if (!(chi > 0.0) || !(gamma > 1.0)) return 0.0;
   double xi_min = cfg->xi_min_energy / gamma;
   if (xi_min >= 1.0) return 0.0;
-  return cfg->alpha * cfg->a_S / gamma * orc_cum_photon(xi_min, 1.0, chi);
+  return cfg->alpha * cfg->a_S / gamma * orc_cum_photon_m(xi_min, 1.0, chi, cfg->model);
 }
 
 /* Eq. (6) integrated over 0 < xi < 1, times alpha a_S / gamma_ph.  A photon
@@ -357,17 +368,18 @@ double orc_sample_photon(const orc_config *cfg, double chi, double gamma, double
   double xi_min = cfg->xi_min_energy / gamma;
   if (xi_min < 0.0) xi_min = 0.0;
   if (xi_min >= 1.0 || !(chi > 0.0)) return 0.0;
-  double total = orc_cum_photon(xi_min, 1.0, chi);
+  const int m = cfg->model;
+  double total = orc_cum_photon_m(xi_min, 1.0, chi, m);
   int upper = r2 > 0.5;
   double target = upper ? c2 * total : r2 * total;
   double lo = cbrt(xi_min), hi = 1.0, tau = 0.5 * (lo + hi);
   for (int it = 0; it < 200; ++it) {
     double xi = tau * tau * tau;
     /* F(tau) is increasing in tau in both forms after the sign flip. */
-    double F = upper ? (target - orc_cum_photon(xi, 1.0, chi))
-                     : (orc_cum_photon(xi_min, xi, chi) - target);
+    double F = upper ? (target - orc_cum_photon_m(xi, 1.0, chi, m))
+                     : (orc_cum_photon_m(xi_min, xi, chi, m) - target);
     if (F > 0.0) hi = tau; else lo = tau;
-    double dF = 3.0 * tau * tau * orc_spec_I(xi, chi);
+    double dF = 3.0 * tau * tau * spec_photon(xi, chi, m);
     double next = (dF > 0.0) ? tau - F / dF : 0.5 * (lo + hi);
     if (!(next > lo && next < hi)) next = 0.5 * (lo + hi);
     if (fabs(next - tau) <= 1e-15 * (tau > 1e-300 ? tau : 1.0) || hi - lo <= 1e-16 * hi) {
