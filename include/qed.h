@@ -76,6 +76,11 @@ enum { QED_SAMPLER_TABLE = 0, QED_SAMPLER_MLP = 1 };
  * with sub-steps), Method II (cumulative probability P_cum += W Dt, emit when
  * 1 - exp(-P_cum) > r3), Method III (emit when P_cum > r3, as printed). */
 enum { QED_GEN_METHOD_I = 0, QED_GEN_METHOD_II = 1, QED_GEN_METHOD_III = 2 };
+/* photon spectrum the tables are built from: formula I (Eq. 1; formula II,
+ * Eq. 4, is the same function) or the classic limit (Eq. 5) restricted to
+ * photons below the lepton's energy (the tables end at delta = 200, i.e.
+ * 1 - xi > 1/(1 + 300 chi); the classic tail beyond is dropped). */
+enum { QED_MODEL_FORMULA_I = 0, QED_MODEL_CLASSIC = 1 };
 enum { QED_FIELDS_UNIFORM = 0, QED_FIELDS_PER_PARTICLE = 1, QED_FIELDS_GRID = 2 };
 
 /* ---- configuration ---------------------------------------------------- */
@@ -101,6 +106,8 @@ typedef struct {
   int sampler;             /* QED_SAMPLER_TABLE (default) or QED_SAMPLER_MLP (FP32 contexts) */
   int generator;           /* QED_GEN_METHOD_I (default), _II or _III: photon event generator;
                               II and III need od_p, od_r on every lepton species */
+  int model;               /* QED_MODEL_FORMULA_I (default) or QED_MODEL_CLASSIC */
+  int pad3_;
 } qed_config;
 
 /* Fill *cfg with the paper-derived defaults (FP32, dt = 0.01, seed 0). */

@@ -163,7 +163,8 @@ static bool cfg_valid(const qed_config *c) {
          (c->sampler == QED_SAMPLER_TABLE ||
           (c->sampler == QED_SAMPLER_MLP && c->precision == QED_FP32)) &&
          (c->generator == QED_GEN_METHOD_I || c->generator == QED_GEN_METHOD_II ||
-          c->generator == QED_GEN_METHOD_III);
+          c->generator == QED_GEN_METHOD_III) &&
+         (c->model == QED_MODEL_FORMULA_I || c->model == QED_MODEL_CLASSIC);
 }
 
 extern "C" int qed_init_tables(const qed_config *cfg, qed_ctx **out, qed_stream_t stream) {

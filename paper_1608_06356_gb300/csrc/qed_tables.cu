@@ -53,14 +53,24 @@ __device__ void bessel_k23_ik13(double x, double &k23, double &ik13) {
 
 constexpr double INV_SQRT3_PI = 0.18377629847393068;  // 1/(sqrt(3) pi)
 
-// Density of Eq. (1) (reduced by alpha a_S / gamma) in y = ln delta.
-__device__ double photon_density(double y, double chi) {
+// Density in y = ln delta (reduced by alpha a_S / gamma) of the photon
+// spectrum: model 0, formula I (Eq. 1); model 1, the classic limit (Eq. 5),
+// (sqrt(3) chi / (2 pi xi)) zeta int_zeta^inf K_{5/3}, zeta = 2 xi / (3 chi),
+// which is int_zeta^inf K_{5/3} / (sqrt(3) pi) = (2 K_{2/3} - int K_{1/3}) /
+// (sqrt(3) pi) at zeta.  dxi/dy = xi (1 - xi) = a (1 - xi)^2, a = 1.5 chi delta.
+__device__ double photon_density(double y, double chi, int model) {
   double d = exp(y);
-  if (d > 700.0) return 0.0;
   double a = 1.5 * chi * d;
-  double k23, ik13;
-  bessel_k23_ik13(d, k23, ik13);
   double omx = 1.0 / (1.0 + a);  // 1 - xi
+  double k23, ik13;
+  if (model == 1) {
+    double zeta = d * omx;  // = 2 xi / (3 chi)
+    if (zeta > 700.0) return 0.0;
+    bessel_k23_ik13(zeta, k23, ik13);
+    return (2.0 * k23 - ik13) * INV_SQRT3_PI * a * omx * omx;
+  }
+  if (d > 700.0) return 0.0;
+  bessel_k23_ik13(d, k23, ik13);
   double br = (omx + (1.0 + a)) * k23 - ik13;
   return br * INV_SQRT3_PI * a * omx * omx;
 }
@@ -78,6 +88,7 @@ __device__ double pair_density(double eta, double chi, double sign) {
 
 struct RowJob {
   int kind;            // 0 photon, 1 pair
+  int model;           // photon spectrum: 0 formula I, 1 classic limit
   double pair_sign;
   Grid gl;             // rows: l = ln chi
   double z0, hz;       // integration nodes z_j = z0 + j hz, j = 0..nz
@@ -94,7 +105,7 @@ struct RowJob {
 };
 
 __device__ __forceinline__ double density(const RowJob &J, double z, double chi) {
-  return J.kind == 0 ? photon_density(z, chi) : pair_density(z, chi, J.pair_sign);
+  return J.kind == 0 ? photon_density(z, chi, J.model) : pair_density(z, chi, J.pair_sign);
 }
 
 // Rate of change of delta per unit z at z (sets the sub-panel count).
@@ -106,8 +117,10 @@ __device__ __forceinline__ double ddelta_dz(const RowJob &J, double z, double ch
 // exp(-delta) cut-off (delta changes by <= 2 per sub-panel).
 __device__ double integrate(const RowJob &J, double a, double b, double chi) {
   if (!(b > a)) return 0.0;
-  // beyond delta = 700 the density underflows (it decreases with z there)
+  // beyond delta = 700 the density underflows (it decreases with z there);
+  // the classic spectrum's argument is zeta = delta (1 - xi) instead
   double delta_a = J.kind == 0 ? exp(a) : (8.0 / (3.0 * chi)) * (1.0 + exp(a));
+  if (J.kind == 0 && J.model == 1) delta_a /= 1.0 + 1.5 * chi * exp(a);
   if (delta_a > 700.0) return 0.0;
   double rate = ddelta_dz(J, b, chi);
   int m = (int)ceil((b - a) * rate / 2.0);
@@ -270,6 +283,7 @@ int build_tables(qed_ctx *c, cudaStream_t st) {
   // ---- photon rows: integration nodes on the forward y grid, extended
   RowJob J{};
   J.kind = 0;
+  J.model = cfg.model;
   J.pair_sign = cfg.pair_sign;
   J.gl = c->gl;
   J.hz = c->gy.h;
