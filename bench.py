@@ -302,6 +302,32 @@ def generator_rates(api, torch, steps=480, dt=0.01):
     return out
 
 
+def spectra_fig1(api, torch, nu=1 << 20, gamma=1000.0):
+    """Fig. 1's comparison: photon-energy spectra (dW/dxi, 16 log bins of xi
+    over [2/gamma, 1]) sampled with the formula-I and the classic-limit
+    tables at chi = 0.1, 1 and 10, and their ratio per bin."""
+    edges = np.exp(np.linspace(np.log(2.0 / gamma), 0.0, 17))
+    out = {"gamma": gamma, "samples": nu, "xi_edges": edges.tolist()}
+    hist = {}
+    for model, name in ((0, "formula_I"), (1, "classic")):
+        ctx = api.qed_init_tables(api.config(model=model))
+        for chi in (0.1, 1.0, 10.0):
+            c = torch.full((nu,), chi, device="cuda")
+            g = torch.full((nu,), gamma, device="cuda")
+            xi = torch.empty(nu, device="cuda")
+            api.qed_sample_xi(ctx, c, g, xi, 3)
+            # rate-weighted: the classic and formula-I totals differ
+            W = float(api.qed_rates(ctx, 0, torch.tensor([chi], device="cuda"),
+                                    torch.tensor([gamma], device="cuda"))[0])
+            h = np.histogram(xi.cpu().numpy(), edges)[0] / nu * W / np.diff(edges)
+            hist[(name, chi)] = h
+    for chi in (0.1, 1.0, 10.0):
+        out[f"chi_{chi:g}"] = {"dW_dxi_formula_I": hist[("formula_I", chi)].tolist(),
+                               "classic_over_formula_I": (hist[("classic", chi)] /
+                                                          np.maximum(hist[("formula_I", chi)], 1e-300)).tolist()}
+    return out
+
+
 def cascade_fig5(api, torch, runs=4000, t_end_trad=3.0, steps_per_trad=60):
     """The paper's cascade benchmark setting (Fig. 5): one electron per run,
     gamma = 2e5, in a static B = 0.2 E_S perpendicular to its motion
@@ -429,6 +455,7 @@ def main():
     ap.add_argument("--mlp-train-samples", type=float, default=4e9)
     ap.add_argument("--generator-bench", type=int, default=1)
     ap.add_argument("--cascade-bench", type=int, default=1)
+    ap.add_argument("--spectra-bench", type=int, default=1)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -611,6 +638,7 @@ def main():
             "batched_runs": batched,
             "event_generators_fig2": generator_rates(api, torch) if args.generator_bench else None,
             "cascade_fig5": cascade_fig5(api, torch) if args.cascade_bench else None,
+            "spectra_fig1": spectra_fig1(api, torch) if args.spectra_bench else None,
             "counters": {"emit_events": emitted,
                          "pair_events": c_after["pair_events"] - c_before["pair_events"],
                          "substeps": c_after["substeps"] - c_before["substeps"],

@@ -78,8 +78,7 @@ enum { QED_SAMPLER_TABLE = 0, QED_SAMPLER_MLP = 1 };
 enum { QED_GEN_METHOD_I = 0, QED_GEN_METHOD_II = 1, QED_GEN_METHOD_III = 2 };
 /* photon spectrum the tables are built from: formula I (Eq. 1; formula II,
  * Eq. 4, is the same function) or the classic limit (Eq. 5) restricted to
- * photons below the lepton's energy (the tables end at delta = 200, i.e.
- * 1 - xi > 1/(1 + 300 chi); the classic tail beyond is dropped). */
+ * photons below the lepton's energy (0 < xi < 1). */
 enum { QED_MODEL_FORMULA_I = 0, QED_MODEL_CLASSIC = 1 };
 enum { QED_FIELDS_UNIFORM = 0, QED_FIELDS_PER_PARTICLE = 1, QED_FIELDS_GRID = 2 };
 

@@ -108,8 +108,14 @@ __device__ __forceinline__ double density(const RowJob &J, double z, double chi)
   return J.kind == 0 ? photon_density(z, chi, J.model) : pair_density(z, chi, J.pair_sign);
 }
 
-// Rate of change of delta per unit z at z (sets the sub-panel count).
+// Rate of change of the Bessel argument per unit z at z (sets the sub-panel
+// count): delta for formula I and pairs; zeta = delta / (1 + a) for the
+// classic spectrum, whose d zeta / dz = zeta / (1 + a) vanishes as xi -> 1.
 __device__ __forceinline__ double ddelta_dz(const RowJob &J, double z, double chi) {
+  if (J.kind == 0 && J.model == 1) {
+    const double d = exp(z), opa = 1.0 + 1.5 * chi * d;
+    return d / (opa * opa);
+  }
   return J.kind == 0 ? exp(z) : (8.0 / (3.0 * chi)) * exp(z);
 }
 
@@ -289,7 +295,9 @@ int build_tables(qed_ctx *c, cudaStream_t st) {
   J.hz = c->gy.h;
   int below = (int)ceil((c->gy.x0 - (-60.0)) / J.hz);
   J.z0 = c->gy.x0 - below * J.hz;
-  J.nz = (int)ceil((5.3 - J.z0) / J.hz);
+  // top of the integration: formula I is below e^-200 beyond delta = e^5.3;
+  // the classic spectrum falls only like 1 - xi ~ e^-y, so it runs to e^16
+  J.nz = (int)ceil(((cfg.model == 1 ? 16.0 : 5.3) - J.z0) / J.hz);
   J.fwd_offset = below;
   J.fwd_n = c->gy.n;
   J.gk = c->gk;
