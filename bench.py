@@ -41,7 +41,7 @@ LEPTON_BYTES = 84       # R x,y,z,px,py,pz,w (28) + id (8) + E,B (24); W x,y,z,p
 LEPTON_STREAM_BYTES = 81  # streaming pass alone: R x..pz, id, E,B (56); W x..pz (24) + class flag (1)
 # DRAM bytes (read + write) per lepton of one lepton step, from an ncu capture of
 # the lepton-step kernels (None when the kernels changed since it was taken)
-LEPTON_TRAFFIC_PER_LEPTON = 183.0
+LEPTON_TRAFFIC_PER_LEPTON = 185.0
 PHOTON_APPEND_BYTES = 61  # x,y,z,px,py,pz,w (28) + id (8) + alive (1) + inherited E,B (24)
 PHOTON_BYTES = 85       # photon step: R 28+8+1+24, W x,y,z (12) [+ alive on pair]
 
@@ -328,7 +328,7 @@ def spectra_fig1(api, torch, nu=1 << 20, gamma=1000.0):
     return out
 
 
-def cascade_fig5(api, torch, runs=4000, t_end_trad=3.0, steps_per_trad=60):
+def cascade_fig5(api, torch, runs=4000, t_end_trad=2.5, steps_per_trad=60):
     """The paper's cascade benchmark setting (Fig. 5): one electron per run,
     gamma = 2e5, in a static B = 0.2 E_S perpendicular to its motion
     (chi_e = 4e4; tables extended to chi = 1e5); pairs with energy above
@@ -345,7 +345,7 @@ def cascade_fig5(api, torch, runs=4000, t_end_trad=3.0, steps_per_trad=60):
     phi = np.random.default_rng(0).uniform(0, 2 * np.pi, n)
     p0 = np.sqrt(2e5 ** 2 - 1.0)
     z = np.zeros(n, np.float32)
-    cap = 1 << 26  # the cascade reaches ~4e3 pairs per run by 3 t_rad
+    cap = 1 << 27  # ~1.4e4 leptons and ~1.7e4 photons per run by 2.5 t_rad
     ctx = api.qed_init_tables(api.config(dt=dt, seed=23, chi_max=1e5, chi_pair_max=1e5,
                                          max_particles=cap))
     e = api.Species.empty(cap, -1).load(x=z, y=z, z=z, px=(p0 * np.cos(phi)).astype(np.float32),
