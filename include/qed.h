@@ -259,7 +259,8 @@ int qed_reset_counters(qed_ctx *ctx, qed_stream_t stream);
  * runs in BF16 on the tensor cores with FP32 accumulation; training in FP32.
  * Parameters: 8577 floats, W1[2][64], b1[64], W2[64][64], b2[64], W3[64][64],
  * b3[64], W4[64], b4 (row index = input unit).  With sampler = QED_SAMPLER_MLP
- * the single-event emission pass and qed_sample_xi draw xi with the network.
+ * emissions of particles with one sub-step (N = 1) and qed_sample_xi draw xi
+ * with the network.
  *
  * qed_mlp_load: copy host weights in (resets the optimiser state).
  * qed_mlp_get:  copy the FP32 weights out.

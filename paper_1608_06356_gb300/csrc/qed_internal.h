@@ -23,7 +23,7 @@ struct qed_ctx {
   int64_t max_tiles;
   int64_t *snap;       // [4] counts snapshotted at the start of a fused step
   int64_t heavy_slots;   // block-tile slots of both lepton species
-  uint8_t *heavy_flags;  // [heavy_slots] main-pass deferral flags
+  uint8_t *heavy_flags;  // [heavy_slots] streaming-pass class flags
   int *heavy_list;       // [heavy_slots] ordered deferred slots
   int64_t *heavy_n;      // length of heavy_list (photon pass)
   // class list of the streaming lepton pass: per-chunk packed counts and

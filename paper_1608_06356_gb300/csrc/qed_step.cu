@@ -222,8 +222,8 @@ template <class Real> struct LeptonArgs {
   Tables<Real> T;  // R, F staged to shared memory; Y read through L1/L2
   Out o;
   int64_t step;
-  uint8_t *heavy_flags;     // [main-pass slots] 1 = deferred to the heavy pass
-  const int *heavy_list;    // ordered main-pass slots of the deferred particles
+  uint8_t *heavy_flags;     // [streaming-pass slot] class flag (0 = finished)
+  const int *heavy_list;    // class list: staging record or -(slot + 1), class-major
   const int64_t *heavy_n;   // length of heavy_list
   const int64_t *d_step;    // if set, the step index is read here (graph replay)
   const int64_t *cls_off;   // class list: class c occupies [cls_off[c-1], cls_off[c])
@@ -1019,7 +1019,7 @@ __global__ void __launch_bounds__(TILE, REPLAY || sizeof(Real) == 8 ? 2 : 4) k_s
 
 // ---------------------------------------------------------------------------
 // Ordered list of the deferred (heavy) particles: stable compaction of the
-// main pass's flags, one flag per main-pass slot (tile * TILE + lane).
+// streaming pass's flags, one flag per slot (tile * TILE + lane).
 // ---------------------------------------------------------------------------
 struct HeavyListArgs {
   const uint8_t *flags;
@@ -1027,7 +1027,7 @@ struct HeavyListArgs {
   const int32_t *stage_idx;  // if set: list the staging record (or -(slot + 1))
   int *list;
   int64_t *count;
-  const int64_t *n0, *n1;  // species counts (sizes the main pass's slot range)
+  const int64_t *n0, *n1;  // species counts (size the streaming pass's slot range)
   Out o;
 };
 
@@ -1317,7 +1317,7 @@ template <class Real> struct PhotonArgs {
 // Streaming photon pass: ballistic push, chi_ph, pair rate and the first
 // Method I draw, with no block-wide synchronisation.  Photons with one
 // sub-step and no event are finished here; the rest are flagged and redone
-// from their stored state by the ordered pass (k_photon over the list).
+// by the pair passes over the list (k_pair_count, k_pair_write).
 // ---------------------------------------------------------------------------
 template <class Real, int FM>
 __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 4 : 2) k_photon_stream(PhotonArgs<Real> A) {

@@ -130,10 +130,10 @@ def test_training_reduces_loss_and_spectral_error(api):
 
 
 def test_fused_step_with_learned_sampler(api, W=None):
-    """With sampler = MLP the single-event pass draws xi from the network: the
-    same particles emit as with the table (events do not depend on the
-    sampler), every emission conserves energy, and photon energies agree with
-    the table path within the network's accuracy."""
+    """With sampler = MLP the emissions of one-sub-step particles draw xi from
+    the network: the same particles emit as with the table (events do not
+    depend on the sampler), every emission conserves energy, and photon
+    energies agree with the table path within the network's accuracy."""
     from paper_1608_06356_gb300 import workloads
     mlp = _mlp()
     n = 200_000

@@ -368,7 +368,7 @@ def test_spectrum_histogram_matches_photons(api, W):
 
 def test_heavy_particles_match_oracle(api, orc, W):
     """Particles needing many sub-steps (W Dt up to ~50) are deferred to the
-    heavy pass; their states and photons still match the oracle."""
+    counting and writing passes; their states and photons still match the oracle."""
     n, step, dt, seed = 1200, 3, 0.05, 4242
     st, chi, gam = W.chi_target(n, seed=61, chi_lo=1.0, chi_hi=100.0, g_lo=100.0, g_hi=1000.0)
     st = to32(st)
