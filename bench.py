@@ -41,7 +41,7 @@ LEPTON_BYTES = 84       # R x,y,z,px,py,pz,w (28) + id (8) + E,B (24); W x,y,z,p
 LEPTON_STREAM_BYTES = 81  # streaming pass alone: R x..pz, id, E,B (56); W x..pz (24) + class flag (1)
 # DRAM bytes (read + write) per lepton of one lepton step, from an ncu capture of
 # the lepton-step kernels (None when the kernels changed since it was taken)
-LEPTON_TRAFFIC_PER_LEPTON = 185.0
+LEPTON_TRAFFIC_PER_LEPTON = 178.0
 PHOTON_APPEND_BYTES = 61  # x,y,z,px,py,pz,w (28) + id (8) + alive (1) + inherited E,B (24)
 PHOTON_BYTES = 85       # photon step: R 28+8+1+24, W x,y,z (12) [+ alive on pair]
 
@@ -556,7 +556,7 @@ def main():
         traffic = LEPTON_TRAFFIC_PER_LEPTON * leptons / max(nprof, 1)
     roofline = {"bound": "hbm",
                 "kernel": "lepton step: k_lepton_stream + k_cls_count/scan/scatter + "
-                          "k_substep_count + k_sub_scan + k_substep_write",
+                          "k_substep_count + k_sub_scan + k_substep_write_coop + k_substep_replay",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": f"{peak_kind} HBM copy (MEASURED_PEAKS.json hbm_gbs)",
                 "traffic": traffic, "bytes_per_launch": lep_bytes, "ms_per_launch": lep_t * 1e3,

@@ -816,6 +816,121 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 && !MLP ? 3 : 2) k_sub
   block_tally_commit(&bt, A.o.cnt, 0);
 }
 
+// Writing pass, warp-cooperative: a warp takes 32 consecutive entries; each
+// lane stores its own particle's final state, and then the warp's photons are
+// written by consecutive lanes -- one photon per lane, its parent's data
+// fetched by shuffles -- so the 14 per-photon stores are coalesced and every
+// lane has a photon to write.  Particles whose photons are not all recorded
+// are listed for the replay launch (k_substep_replay).
+template <class Real, int FM, int MODE>
+__global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 4 : 2) k_substep_write_coop(LeptonArgs<Real> A) {
+  const int64_t step_ = A.d_step ? *A.d_step : A.step;
+  __shared__ uint8_t s_parent[TILE / 32][32 * REC];  // warp photon -> parent lane
+  __shared__ long long s_meta[4];
+  __shared__ BlockTally bt;
+  block_tally_init(&bt);
+  if (threadIdx.x == 0) {
+    s_meta[0] = *(volatile int64_t *)A.sp[0].d_n;
+    s_meta[1] = A.cls_off[NCLS];
+    s_meta[2] = A.sub_meta[0];  // photons of all entries
+    s_meta[3] = A.sub_meta[1];  // photon count before them
+  }
+  __syncthreads();
+  const int64_t T0 = (s_meta[0] + TILE - 1) / TILE;
+  const int64_t nh = s_meta[1];
+  const uint32_t total = (uint32_t)s_meta[2];
+  const int64_t nph = s_meta[3];
+  const Real dt = sel<Real>(A.C.dt, A.C.f_dt);
+  const int64_t rc = A.rec_cap;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint8_t *par = s_parent[wid];
+  Tally tl;
+  tl.clear();
+  const int64_t nwarps = (int64_t)gridDim.x * (TILE / 32);
+  for (int64_t wb = (blockIdx.x * (int64_t)(TILE / 32) + wid) * 32; wb < nh; wb += nwarps * 32) {
+    const int64_t h = wb + lane;
+    const bool act = h < nh;
+    uint32_t off = 0, cnt = 0;
+    int32_t e = 0;
+    if (act) {
+      off = A.sub_cnt[h];  // exclusive prefix of the counts now
+      cnt = (h + 1 < nh ? A.sub_cnt[h + 1] : total) - off;
+      e = A.heavy_list[h];
+    }
+    const bool rep = act && cnt > 0 && (cnt > REC || h >= rc);
+    if (rep) A.replay_list[atomicAdd(A.replay_n, 1u)] = (int32_t)h;
+    const uint32_t mine = (act && !rep) ? cnt : 0u;  // photons this lane's entry gives the warp
+    // the particle: staged with no photon needs nothing (the streaming pass
+    // stored it); otherwise its final state is stored here
+    Entry<Real> P;
+    P.x = P.y = P.z = P.px = P.py = P.w = (Real)0;
+    P.pz = P.g = (Real)1;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) { P.E[c] = (Real)0; P.B[c] = (Real)0; }
+    P.id = 0;
+    P.tag = 0;
+    Real nx = 0, ny = 0, nz = 0;
+    const bool need = act && !rep && (cnt > 0 || e < 0);
+    if (need) {
+      Real gfin = (Real)0;
+      if (cnt > 0) gfin = A.sub_gf[h];
+      load_entry<Real, FM, MODE>(A, e, T0, dt, P);
+      unit_dir(P, nx, ny, nz);
+      store_entry<Real, MODE>(A, P, cnt > 0 ? gfin : P.g, nx, ny, nz);
+    }
+    // the warp's photons, in entry order
+    uint32_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const uint32_t excl = incl - mine;
+    const uint32_t T = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    for (uint32_t j = 0; j < mine; ++j) par[excl + j] = (uint8_t)lane;
+    __syncwarp();
+    for (uint32_t q0 = 0; q0 < T; q0 += 32) {
+      const uint32_t q = q0 + lane;
+      const bool valid = q < T;
+      const int L = valid ? par[q] : 0;
+      // the parent's data, by shuffles (every lane takes part)
+      const Real x = __shfl_sync(0xFFFFFFFFu, P.x, L), y = __shfl_sync(0xFFFFFFFFu, P.y, L),
+                 z = __shfl_sync(0xFFFFFFFFu, P.z, L);
+      const Real ux = __shfl_sync(0xFFFFFFFFu, nx, L), uy = __shfl_sync(0xFFFFFFFFu, ny, L),
+                 uz = __shfl_sync(0xFFFFFFFFu, nz, L);
+      const Real w = __shfl_sync(0xFFFFFFFFu, P.w, L);
+      Real E[3], B[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        E[c] = __shfl_sync(0xFFFFFFFFu, P.E[c], L);
+        B[c] = __shfl_sync(0xFFFFFFFFu, P.B[c], L);
+      }
+      const uint64_t pid = (uint64_t)__shfl_sync(0xFFFFFFFFu, (unsigned long long)P.id, L);
+      const uint32_t ptag = __shfl_sync(0xFFFFFFFFu, P.tag, L);
+      const uint32_t poff = __shfl_sync(0xFFFFFFFFu, off, L);
+      const uint32_t pex = __shfl_sync(0xFFFFFFFFu, excl, L);
+      const int64_t ph = wb + L;
+      if (!valid) continue;
+      const uint32_t j = q - pex;  // the parent's j-th photon
+      const Real eph = A.rec_e[j * rc + ph];
+      const int64_t kk = A.rec_k[j * rc + ph];
+      const int64_t out = nph + (int64_t)poff + j;
+      if (out >= A.ph.cap) {
+        tl.dropped += 1;
+        tl.status |= QED_STATUS_CAPACITY;
+        continue;
+      }
+      const U4 cid = draw(A.C.seed, pid, step_, kk, STREAM_PHOTON_ID);
+      write_child(A.ph, out, x, y, z, eph * ux, eph * uy, eph * uz, w,
+                  (uint64_t)cid.x | ((uint64_t)cid.y << 32), E, B, ptag);
+    }
+    __syncwarp();  // par is rewritten by the next window
+  }
+  tally_flush(&bt, tl);
+  __syncthreads();
+  block_tally_commit(&bt, A.o.cnt, 0);
+}
+
 // Exclusive scan, in place, of the sub-step entries' photon counts (single
 // pass, decoupled look-back over 4096-entry tiles).  The total and the photon
 // count at launch go to sub_meta[0] and sub_meta[1]; the last tile publishes
@@ -896,22 +1011,24 @@ __global__ void __launch_bounds__(TILE) k_sub_scan(SubScanArgs A) {
   launch_epilogue(A.o.scan, epoch);
 }
 
-// REPLAY = false: every particle whose photons are all in its records; it
-// lists the others (more than REC photons, or past the record capacity, both
-// rare), whose chains the REPLAY = true launch redoes -- separately, so that
-// the common case carries neither the tables nor the chain's registers, and
-// densely, so that the rare long replays share warps.
-template <class Real, int FM, int MODE, bool REPLAY>
-__global__ void __launch_bounds__(TILE, REPLAY || sizeof(Real) == 8 ? 2 : 4) k_substep_write(LeptonArgs<Real> A) {
+// Replay launch of the writing pass: the particles k_substep_write_coop listed
+// (more than REC photons, or past the record capacity, both rare) redo their
+// emission chains -- same draws, same tables -- and write their photons and
+// final momenta.  It is separate so that the common case carries neither the
+// tables nor the chain's registers, and dense, so that the rare long replays
+// share warps.
+template <class Real, int FM, int MODE>
+__global__ void __launch_bounds__(TILE, 2) k_substep_replay(LeptonArgs<Real> A) {
   const int64_t step_ = A.d_step ? *A.d_step : A.step;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  constexpr bool kSmem = sizeof(Real) == 4 && REPLAY;
+  constexpr bool kSmem = sizeof(Real) == 4;
   Real *sR = kSmem ? reinterpret_cast<Real *>(smem_raw) : const_cast<Real *>(A.T.R);
   Real *sF = kSmem ? sR + A.T.gl.n : const_cast<Real *>(A.T.F);
-  __shared__ long long s_meta[5];
+  __shared__ long long s_meta[4];
   __shared__ BlockTally bt;
-  // a replay block with nothing to replay leaves before staging the tables
-  if (REPLAY && (int64_t)blockIdx.x * TILE >= (int64_t)*(volatile unsigned int *)A.replay_n) return;
+  // a block with nothing to replay leaves before staging the tables
+  const int64_t n_iter = (int64_t)*(volatile unsigned int *)A.replay_n;
+  if ((int64_t)blockIdx.x * TILE >= n_iter) return;
   if (kSmem) {
     load_tables_smem(sR, A.T.R, A.T.gl.n);
     load_tables_smem(sF, A.T.F, A.T.gl.n * A.T.gy.n);
@@ -919,54 +1036,32 @@ __global__ void __launch_bounds__(TILE, REPLAY || sizeof(Real) == 8 ? 2 : 4) k_s
   block_tally_init(&bt);
   if (threadIdx.x == 0) {
     s_meta[0] = *(volatile int64_t *)A.sp[0].d_n;
-    s_meta[1] = 0;  // the whole class list
-    s_meta[2] = A.cls_off[NCLS];
-    s_meta[3] = A.sub_meta[0];  // photons of all entries
-    s_meta[4] = A.sub_meta[1];  // photon count before them
+    s_meta[1] = A.cls_off[NCLS];
+    s_meta[2] = A.sub_meta[0];  // photons of all entries
+    s_meta[3] = A.sub_meta[1];  // photon count before them
   }
   __syncthreads();
   const int64_t T0 = (s_meta[0] + TILE - 1) / TILE;
-  const int64_t begin = s_meta[1], nh = s_meta[2] - s_meta[1];
-  const uint32_t total = (uint32_t)s_meta[3];
-  const int64_t nph = s_meta[4];
+  const int64_t nh = s_meta[1];
+  const uint32_t total = (uint32_t)s_meta[2];
+  const int64_t nph = s_meta[3];
   const Real inv_aS = sel<Real>(A.C.inv_aS, A.C.f_inv_aS);
   const Real dt = sel<Real>(A.C.dt, A.C.f_dt);
   const Real wdt_max = sel<Real>(A.C.wdt_max, A.C.f_wdt_max);
-  const int64_t rc = A.rec_cap;
-  // the replay launch runs over the entries the first launch listed
-  const int64_t n_iter = REPLAY ? (int64_t)*(volatile unsigned int *)A.replay_n : nh;
   Tally tl;
   tl.clear();
   for (int64_t q = blockIdx.x * (int64_t)TILE + threadIdx.x; q < n_iter; q += (int64_t)gridDim.x * TILE) {
-    const int64_t h = REPLAY ? (int64_t)A.replay_list[q] : q;
+    const int64_t h = (int64_t)A.replay_list[q];
     // sub_cnt holds the exclusive prefix of the counts now
     const uint32_t off = A.sub_cnt[h];
     const uint32_t cnt = (h + 1 < nh ? A.sub_cnt[h + 1] : total) - off;
-    const int32_t e = A.heavy_list[begin + h];
-    if (!REPLAY && cnt > 0 && (cnt > REC || h >= rc)) {  // its photons are not all recorded
-      A.replay_list[atomicAdd(A.replay_n, 1u)] = (int32_t)h;
-      continue;
-    }
-    if (cnt == 0 && e >= 0) continue;  // staged, no photon: the streaming pass stored it
+    const int32_t e = A.heavy_list[h];
     const int64_t out0 = nph + (int64_t)off;
-    // the first record and the final gamma are loaded with the entry itself
-    // (one round trip to memory instead of three in a row)
-    Real rec0 = 0, gfin = 0;
-    uint32_t krec0 = 0;
-    if (!REPLAY && cnt > 0) {
-      rec0 = A.rec_e[h];
-      krec0 = A.rec_k[h];
-      gfin = A.sub_gf[h];
-    }
     Entry<Real> P;
     load_entry<Real, FM, MODE>(A, e, T0, dt, P);
     Real nx, ny, nz;
     unit_dir(P, nx, ny, nz);
     Real g = P.g;
-    if (cnt == 0) {
-      store_entry<Real, MODE>(A, P, g, nx, ny, nz);
-      continue;
-    }
     auto put = [&](uint32_t j, Real eph, int64_t kk) {
       const int64_t out = out0 + j;
       if (out >= A.ph.cap) {
@@ -978,37 +1073,31 @@ __global__ void __launch_bounds__(TILE, REPLAY || sizeof(Real) == 8 ? 2 : 4) k_s
       write_child(A.ph, out, P.x, P.y, P.z, eph * nx, eph * ny, eph * nz, P.w,
                   (uint64_t)cid.x | ((uint64_t)cid.y << 32), P.E, P.B, P.tag);
     };
-    if (!REPLAY) {
-      put(0, rec0, (int64_t)krec0);
-      for (uint32_t j = 1; j < cnt; ++j) put(j, A.rec_e[j * rc + h], (int64_t)A.rec_k[j * rc + h]);
-      g = gfin;
-    } else {
-      // more photons than records: replay the chain (same draws, same tables)
-      Tally dummy;
-      dummy.clear();
-      const Real *E = P.E, *B = P.B;
-      Real chi = chi_lepton(P.px, P.py, P.pz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
-      RateOut<Real> ro = photon_rate(sR, sF, A.T, A.C, chi, g, dummy);
-      const bool forced = A.C.generator != GEN_METHOD_I;  // Methods II/III: one photon at k = 0
-      const int64_t N = forced ? 1 : substep_count(A.C, ro.W, dt, wdt_max, dummy.status);
-      const Real dts = dt / (Real)N;
-      uint32_t j = 0;
-      for (int64_t kk = 0; kk < N && j < cnt; ++kk) {
-        U4 r = draw(A.C.seed, P.id, step_, kk, STREAM_EMIT);
-        if (!forced && !(ro.W * dts > unif<Real>(r.x))) continue;
-        XiOut<Real> xo = photon_xi(A.T.Y, A.T, ro.l, chi, ro.kmin, unif<Real>(r.y), unif<Real>(~r.y), dummy);
-        Real g2 = g * xo.omxi, eph = g * xo.xi;
-        if (g2 < (Real)1) { g2 = (Real)1; eph = g - (Real)1; }
-        put(j++, eph, kk);
-        Real pm2 = m_sqrt((g2 - (Real)1) * (g2 + (Real)1));
-        g = g2;
-        chi = chi_lepton(pm2 * nx, pm2 * ny, pm2 * nz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
-        ro = photon_rate(sR, sF, A.T, A.C, chi, g, dummy);
-      }
-      if (j != cnt) {  // the replay disagreed with the count: zero-energy photons fill the slots
-        tl.status |= QED_STATUS_REPLAY;
-        for (; j < cnt; ++j) put(j, (Real)0, 0);
-      }
+    // the chain again (its counters went to the counting pass's tally)
+    Tally dummy;
+    dummy.clear();
+    const Real *E = P.E, *B = P.B;
+    Real chi = chi_lepton(P.px, P.py, P.pz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
+    RateOut<Real> ro = photon_rate(sR, sF, A.T, A.C, chi, g, dummy);
+    const bool forced = A.C.generator != GEN_METHOD_I;  // Methods II/III: one photon at k = 0
+    const int64_t N = forced ? 1 : substep_count(A.C, ro.W, dt, wdt_max, dummy.status);
+    const Real dts = dt / (Real)N;
+    uint32_t j = 0;
+    for (int64_t kk = 0; kk < N && j < cnt; ++kk) {
+      U4 r = draw(A.C.seed, P.id, step_, kk, STREAM_EMIT);
+      if (!forced && !(ro.W * dts > unif<Real>(r.x))) continue;
+      XiOut<Real> xo = photon_xi(A.T.Y, A.T, ro.l, chi, ro.kmin, unif<Real>(r.y), unif<Real>(~r.y), dummy);
+      Real g2 = g * xo.omxi, eph = g * xo.xi;
+      if (g2 < (Real)1) { g2 = (Real)1; eph = g - (Real)1; }
+      put(j++, eph, kk);
+      Real pm2 = m_sqrt((g2 - (Real)1) * (g2 + (Real)1));
+      g = g2;
+      chi = chi_lepton(pm2 * nx, pm2 * ny, pm2 * nz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
+      ro = photon_rate(sR, sF, A.T, A.C, chi, g, dummy);
+    }
+    if (j != cnt) {  // the replay disagreed with the count: zero-energy photons fill the slots
+      tl.status |= QED_STATUS_REPLAY;
+      for (; j < cnt; ++j) put(j, (Real)0, 0);
     }
     store_entry<Real, MODE>(A, P, g, nx, ny, nz);
   }
@@ -2212,8 +2301,8 @@ static cudaError_t launch_lepton_t(qed_ctx *c, const LeptonArgs<Real> &a, cudaSt
   if (e == cudaSuccess) e = prof_mark(c, 3, st);
   if (e == cudaSuccess) e = launch_sub_scan(c, c->cls_off + NCLS, a.ph.d_n, a.ph.cap, nullptr, 0, st);
   if (e == cudaSuccess) e = prof_mark(c, 4, st);
-  if (e == cudaSuccess) e = launch_plain_kernel<Real>(c, k_substep_write<Real, FM, MODE, false>, a, st);
-  if (e == cudaSuccess) e = launch_tables_kernel<Real>(c, k_substep_write<Real, FM, MODE, true>, a, false, st);
+  if (e == cudaSuccess) e = launch_plain_kernel<Real>(c, k_substep_write_coop<Real, FM, MODE>, a, st);
+  if (e == cudaSuccess) e = launch_tables_kernel<Real>(c, k_substep_replay<Real, FM, MODE>, a, false, st);
   if (e == cudaSuccess) e = prof_mark(c, 5, st);
   return e;
 }
