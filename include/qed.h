@@ -251,6 +251,14 @@ int qed_table_get(qed_ctx *ctx, int which, double *host_out, size_t n, double *d
 int qed_read_counters(qed_ctx *ctx, qed_counters *out, qed_stream_t stream);
 int qed_reset_counters(qed_ctx *ctx, qed_stream_t stream);
 
+/* Device status since the last qed_reset_counters: `bits` gets the OR of the
+ * QED_STATUS_* bits the kernels set, `dropped` the appends not written because
+ * a species was full (either pointer may be NULL).  Waits for all work on the
+ * context's device (cudaDeviceSynchronize), so it needs no stream.  Returns
+ * QED_ERR_TIMEOUT when QED_STATUS_TIMEOUT is set (the outputs are still
+ * written), QED_ERR_CUDA on a CUDA error. */
+int qed_last_device_status(qed_ctx *ctx, uint32_t *bits, int64_t *dropped);
+
 /* ---- learned inverse CDF (surrogate for the tabulated inverse of Eq. 7) --
  * A 2 -> 64 -> 64 -> 64 -> 1 SiLU network maps x0 = (ln chi + 1.1512925)/5.7564627,
  * x1 = (kappa + 3.25)/6.75 to z; ln delta = z + 3 kappa - 2 ln(1 + e^kappa), where

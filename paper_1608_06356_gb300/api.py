@@ -307,6 +307,16 @@ def qed_reset_counters(ctx: Context, stream=None) -> None:
     B.check(B.lib().qed_reset_counters(ctx.handle, _stream(stream)), "qed_reset_counters")
 
 
+def qed_last_device_status(ctx: Context) -> tuple[int, int]:
+    """(status bits, dropped appends) since the last reset; waits for the device.
+    A set QED_STATUS_TIMEOUT bit is returned, not raised."""
+    bits, dropped = C.c_uint32(0), C.c_int64(0)
+    code = B.lib().qed_last_device_status(ctx.handle, C.byref(bits), C.byref(dropped))
+    if code not in (B.QED_OK, -5):
+        B.check(code, "qed_last_device_status")
+    return int(bits.value), int(dropped.value)
+
+
 def qed_profile_begin(ctx: Context, max_steps: int) -> None:
     B.check(B.lib().qed_profile_begin(ctx.handle, int(max_steps)), "qed_profile_begin")
 

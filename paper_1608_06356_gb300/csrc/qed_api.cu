@@ -478,4 +478,17 @@ extern "C" int qed_reset_counters(qed_ctx *c, qed_stream_t stream) {
                    "qed_reset_counters");
 }
 
+extern "C" int qed_last_device_status(qed_ctx *c, uint32_t *bits, int64_t *dropped) {
+  if (!c) return QED_ERR_ARG;
+  qed_counters h;
+  cudaError_t e = cudaSetDevice(c->device);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(&h, c->d_counters, sizeof(qed_counters), cudaMemcpyDeviceToHost);
+  int rc = cuda_fail(e, "qed_last_device_status");
+  if (rc != QED_OK) return rc;
+  if (bits) *bits = h.status;
+  if (dropped) *dropped = h.dropped;
+  return (h.status & QED_STATUS_TIMEOUT) ? QED_ERR_TIMEOUT : QED_OK;
+}
+
 extern "C" int64_t qed_launch_count(const qed_ctx *c) { return c ? c->launches : 0; }

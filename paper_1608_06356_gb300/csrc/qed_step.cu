@@ -1700,10 +1700,13 @@ __global__ void __launch_bounds__(TILE) k_pair_write(PhotonArgs<Real> A) {
 // writes only below the end of its own range, after every earlier tile has
 // published -- so no data is overwritten before it has been read.
 // ---------------------------------------------------------------------------
-// Compaction tiles are 1024 particles (one per thread of a 1024-thread CTA),
-// so a call takes a quarter of the tile-counter atomics and look-backs that
-// 256-particle tiles would.
+// Compaction tiles are COMPACT_ITEMS x 1024 particles (1024-thread CTAs, item k
+// of thread i is particle k * 1024 + i of the tile, so every load and store is
+// coalesced).  Tiles this large matter: a tile learns its prefix from the tile
+// states of its predecessors, a warp-wide window of 32 per round trip, so the
+// pass advances about 32 tiles per L2 round trip whatever the bandwidth.
 constexpr int COMPACT_TILE = 1024;
+template <class Real> __host__ __device__ constexpr int compact_items() { return sizeof(Real) == 4 ? 2 : 1; }
 
 template <class Real> struct CompactArgs {
   Sp<Real> s;
@@ -1712,6 +1715,8 @@ template <class Real> struct CompactArgs {
 
 template <class Real>
 __global__ void __launch_bounds__(COMPACT_TILE) k_compact(CompactArgs<Real> A) {
+  constexpr int CI = compact_items<Real>();
+  constexpr int64_t TP = (int64_t)CI * COMPACT_TILE;  // particles per tile
   __shared__ uint32_t scan_sm[33];
   __shared__ long long s_meta[8];
   if (threadIdx.x == 0) {
@@ -1721,7 +1726,7 @@ __global__ void __launch_bounds__(COMPACT_TILE) k_compact(CompactArgs<Real> A) {
   __syncthreads();
   const int64_t n = s_meta[2];
   const uint32_t epoch = (uint32_t)s_meta[5];
-  const int64_t ntiles = (n + COMPACT_TILE - 1) / COMPACT_TILE;
+  const int64_t ntiles = (n + TP - 1) / TP;
   const bool fields = A.s.ex != nullptr;
   uint32_t status = 0;
   for (;;) {
@@ -1730,24 +1735,38 @@ __global__ void __launch_bounds__(COMPACT_TILE) k_compact(CompactArgs<Real> A) {
     const int64_t t = s_meta[0];
     __syncthreads();
     if (t >= ntiles) break;
-    const int64_t i = t * COMPACT_TILE + threadIdx.x;
-    uint32_t keep = 0;
-    Real v[13];
-    uint64_t id = 0;
-    uint32_t tg = 0;
-    if (i < n && A.s.alive[i]) {
-      keep = 1;
-      if (A.s.tag) tg = A.s.tag[i];
-      v[0] = A.s.x[i]; v[1] = A.s.y[i]; v[2] = A.s.z[i];
-      v[3] = A.s.px[i]; v[4] = A.s.py[i]; v[5] = A.s.pz[i]; v[6] = A.s.w[i];
-      id = A.s.id[i];
-      if (fields) {
-        v[7] = A.s.ex[i]; v[8] = A.s.ey[i]; v[9] = A.s.ez[i];
-        v[10] = A.s.bx[i]; v[11] = A.s.by[i]; v[12] = A.s.bz[i];
+    uint32_t keep[CI];
+    Real v[CI][13];
+    uint64_t id[CI];
+    uint32_t tg[CI];
+#pragma unroll
+    for (int k = 0; k < CI; ++k) {
+      const int64_t i = t * TP + k * COMPACT_TILE + threadIdx.x;
+      keep[k] = 0;
+      id[k] = 0;
+      tg[k] = 0;
+      if (i < n && A.s.alive[i]) {
+        keep[k] = 1;
+        if (A.s.tag) tg[k] = A.s.tag[i];
+        v[k][0] = A.s.x[i]; v[k][1] = A.s.y[i]; v[k][2] = A.s.z[i];
+        v[k][3] = A.s.px[i]; v[k][4] = A.s.py[i]; v[k][5] = A.s.pz[i]; v[k][6] = A.s.w[i];
+        id[k] = A.s.id[i];
+        if (fields) {
+          v[k][7] = A.s.ex[i]; v[k][8] = A.s.ey[i]; v[k][9] = A.s.ez[i];
+          v[k][10] = A.s.bx[i]; v[k][11] = A.s.by[i]; v[k][12] = A.s.bz[i];
+        }
       }
     }
-    uint32_t excl = block_excl_scan(keep, scan_sm);
-    uint32_t agg = scan_sm[32];
+    // destination of item k within the tile: the items of the earlier stripes,
+    // then this stripe's prefix
+    uint32_t excl[CI];
+    uint32_t agg = 0;
+#pragma unroll
+    for (int k = 0; k < CI; ++k) {
+      if (k > 0) __syncthreads();  // scan_sm is reused
+      excl[k] = agg + block_excl_scan(keep[k], scan_sm);
+      agg += scan_sm[32];
+    }
     if (threadIdx.x < 32) {
       uint32_t pre = lookback_warp(A.o.scan, t, epoch, agg, status);
       if (threadIdx.x == 0) {
@@ -1756,16 +1775,18 @@ __global__ void __launch_bounds__(COMPACT_TILE) k_compact(CompactArgs<Real> A) {
       }
     }
     __syncthreads();
-    if (keep) {
-      int64_t d = s_meta[1] + excl;
-      A.s.x[d] = v[0]; A.s.y[d] = v[1]; A.s.z[d] = v[2];
-      A.s.px[d] = v[3]; A.s.py[d] = v[4]; A.s.pz[d] = v[5]; A.s.w[d] = v[6];
-      A.s.id[d] = id;
+#pragma unroll
+    for (int k = 0; k < CI; ++k) {
+      if (!keep[k]) continue;
+      const int64_t d = s_meta[1] + excl[k];
+      A.s.x[d] = v[k][0]; A.s.y[d] = v[k][1]; A.s.z[d] = v[k][2];
+      A.s.px[d] = v[k][3]; A.s.py[d] = v[k][4]; A.s.pz[d] = v[k][5]; A.s.w[d] = v[k][6];
+      A.s.id[d] = id[k];
       A.s.alive[d] = 1;
-      if (A.s.tag) A.s.tag[d] = tg;
+      if (A.s.tag) A.s.tag[d] = tg[k];
       if (fields) {
-        A.s.ex[d] = v[7]; A.s.ey[d] = v[8]; A.s.ez[d] = v[9];
-        A.s.bx[d] = v[10]; A.s.by[d] = v[11]; A.s.bz[d] = v[12];
+        A.s.ex[d] = v[k][7]; A.s.ey[d] = v[k][8]; A.s.ez[d] = v[k][9];
+        A.s.bx[d] = v[k][10]; A.s.by[d] = v[k][11]; A.s.bz[d] = v[k][12];
       }
     }
   }

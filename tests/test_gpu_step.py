@@ -304,6 +304,9 @@ def test_capacity_overflow_drops_in_order(api, orc, W):
     assert len(h["id"]) == cap
     np.testing.assert_array_equal(h["id"], full["id"][:cap])
     assert c["dropped"] == len(full["id"]) - cap and c["status"] & 1
+    assert api.qed_last_device_status(ctx2) == (c["status"], c["dropped"])
+    bits, dropped = api.qed_last_device_status(ctx)  # the run with room for every photon
+    assert dropped == 0 and not bits & 1
     # recoil happened regardless of storage
     np.testing.assert_array_equal(e2.host()["px"], e.host()["px"])
 
