@@ -36,6 +36,7 @@ METRIC = "QED particle-steps/s at 64M particles (table vs MLP) and % HBM rooflin
 UNIT = "particle-steps/s"
 N_PART = 1 << 26
 DT = 0.01
+DEFAULT_STEPS, DEFAULT_WARMUP, DEFAULT_E2E_STEPS = 10, 3, 2
 COMPACT_EVERY = 4  # dead photons (pair conversions) are removed every this many steps
 LEPTON_BYTES = 84       # R x,y,z,px,py,pz,w (28) + id (8) + E,B (24); W x,y,z,px,py,pz (24)
 LEPTON_STREAM_BYTES = 81  # streaming pass alone: R x..pz, id, E,B (56); W x..pz (24) + class flag (1)
@@ -55,6 +56,17 @@ def workload_desc(n):
                         "counted on the device each step (qed_count_alive)",
             "particles": n, "dt": DT, "precision": "fp32 state, fp64 chi where it cancels",
             "sampler": "table", "l2": "inputs larger than L2 (>= 5.4 GB read per step)"}
+
+
+def capacities(n, total_steps):
+    """Species capacities and the context's max_particles for n electrons run
+    for total_steps steps: photons at ~0.25 emissions per electron per step at
+    Dt = 0.01 at the start (falling as the ensemble cools), leptons for the
+    pairs the photons of the hottest electrons create (a cascade)."""
+    cap_g = int(n * 0.3 * (total_steps + 1)) + 4096
+    cap_e = 3 * n
+    cap_p = 2 * n
+    return cap_e, cap_p, cap_g, max(cap_g, cap_e)
 
 
 def rank_id_offset(rank: int) -> int:
@@ -443,11 +455,11 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=DEFAULT_STEPS)
+    ap.add_argument("--warmup", type=int, default=DEFAULT_WARMUP)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--particles", type=int, default=N_PART)
-    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=DEFAULT_E2E_STEPS)
     ap.add_argument("--ref-particles", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--sampler-bench", type=int, default=1)
@@ -479,14 +491,8 @@ def main():
     from paper_1608_06356_gb300 import api
 
     n = args.particles
-    total_steps = args.warmup + args.steps + args.e2e_steps
-    # photon/pair capacity: ~0.25 emissions per electron per step at Dt = 0.01 at the start,
-    # falling as the ensemble cools; dead photons are removed every step
-    cap_g = int(n * 0.3 * (total_steps + 1)) + 4096
-    # the photons of the hottest electrons create pairs (a cascade): room for the leptons it adds
-    cap_e = 3 * n
-    cap_p = 2 * n
-    ctx = api.qed_init_tables(api.config(dt=DT, seed=1 + rank, max_particles=max(cap_g, cap_e)))
+    cap_e, cap_p, cap_g, max_particles = capacities(n, args.warmup + args.steps + args.e2e_steps)
+    ctx = api.qed_init_tables(api.config(dt=DT, seed=1 + rank, max_particles=max_particles))
     host = host_workload(n, seed=rank)
     host["id"] += np.uint64(rank_id_offset(rank))
     e = api.Species.empty(cap_e, -1, fields=True).load(**host)
