@@ -1,10 +1,15 @@
 """Host-side checks of the C-ABI boundary (no GPU needed): the shared library
 loads, it exports every function include/qed.h declares, the Python binding
-covers each of them, and the ctypes struct layouts match the C compiler's."""
+covers each of them, the ctypes struct layouts match the C compiler's, bad
+arguments and null contexts are rejected before any CUDA call, and a missing
+library raises.  Also the benchmark's host-only parts: the reference arm's
+JSON line and the capacities of the default run."""
 import ctypes as C
+import json
 import os
 import re
 import subprocess
+import sys
 import textwrap
 
 import numpy as np
@@ -97,3 +102,46 @@ def test_workload_generators_are_seeded():
     e = W.ensemble(500, seed=1)
     gam = np.sqrt(1 + e["px"] ** 2 + e["py"] ** 2 + e["pz"] ** 2)
     assert gam.min() >= 100 * (1 - 1e-12) and gam.max() <= 1e4 * (1 + 1e-12)
+
+
+def test_entry_points_reject_a_null_context(qlib):
+    lib = qlib.lib()
+    bits, dropped = C.c_uint32(7), C.c_int64(7)
+    assert lib.qed_last_device_status(None, C.byref(bits), C.byref(dropped)) == -1
+    assert bits.value == 7 and dropped.value == 7  # untouched on error
+    assert lib.qed_count_alive(None, None, None, None) == -1
+    assert lib.qed_compact_fill(None, None, None) == -1
+    assert lib.qed_compact(None, None, None) == -1
+    assert lib.qed_profile_end_phases(None, None, None) == -1
+
+
+def test_missing_library_fails_loudly(qlib, monkeypatch, tmp_path):
+    # no fallback: without the built library every call path raises
+    monkeypatch.setattr(qlib, "LIB_PATH", str(tmp_path / "absent.so"))
+    monkeypatch.setattr(qlib, "_lib", None)
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        qlib.lib()
+
+
+def test_reference_arm_prints_one_line():
+    # the reference arm is the oracle on the host cores; a tiny sample here
+    out = subprocess.check_output([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                                   "--steps", "1", "--warmup", "3", "--ref-particles", "64"], text=True,
+                                  cwd=ROOT)
+    lines = [l for l in out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "particle-steps/s"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+
+
+def test_bench_capacities_hold_the_default_run():
+    sys.path.insert(0, ROOT)
+    import bench
+    n = bench.N_PART
+    steps = bench.DEFAULT_WARMUP + bench.DEFAULT_STEPS + bench.DEFAULT_E2E_STEPS
+    cap_e, cap_p, cap_g, maxp = bench.capacities(n, steps)
+    assert cap_e >= 3 * n and cap_p >= 2 * n and cap_g > 0.3 * n * steps
+    assert maxp == max(cap_e, cap_g)
