@@ -819,9 +819,10 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 && !MLP ? 3 : 2) k_sub
 // Writing pass, warp-cooperative: a warp takes 32 consecutive entries; each
 // lane stores its own particle's final state, and then the warp's photons are
 // written by consecutive lanes -- one photon per lane, its parent's data
-// fetched by shuffles -- so the 15 per-photon stores (state, id, alive flag, fields) are coalesced and every
-// lane has a photon to write.  Particles whose photons are not all recorded
-// are listed for the replay launch (k_substep_replay).
+// fetched by shuffles -- so the 15 per-photon stores (state, id, alive flag,
+// fields) are coalesced and every lane has a photon to write.  Particles whose
+// photons are not all recorded are listed for the replay launch
+// (k_substep_replay).
 template <class Real, int FM, int MODE>
 __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 4 : 2) k_substep_write_coop(LeptonArgs<Real> A) {
   const int64_t step_ = A.d_step ? *A.d_step : A.step;
