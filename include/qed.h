@@ -259,6 +259,15 @@ int qed_reset_counters(qed_ctx *ctx, qed_stream_t stream);
  * written), QED_ERR_CUDA on a CUDA error. */
 int qed_last_device_status(qed_ctx *ctx, uint32_t *bits, int64_t *dropped);
 
+/* Failure-detection check of the bounded waits: launches one decoupled
+ * look-back (one warp) behind a tile that never publishes, on two scratch
+ * words of the context -- no particle data is touched.  The wait gives up at
+ * its iteration limit (about a second), sets QED_STATUS_TIMEOUT and the kernel
+ * returns, leaving the context usable.  Asynchronous on `stream`; read the
+ * result with qed_last_device_status or qed_read_counters (both then return
+ * QED_ERR_TIMEOUT) and clear it with qed_reset_counters. */
+int qed_test_wait_expiry(qed_ctx *ctx, qed_stream_t stream);
+
 /* ---- learned inverse CDF (surrogate for the tabulated inverse of Eq. 7) --
  * A 2 -> 64 -> 64 -> 64 -> 1 SiLU network maps x0 = (ln chi + 1.1512925)/5.7564627,
  * x1 = (kappa + 3.25)/6.75 to z; ln delta = z + 3 kappa - 2 ln(1 + e^kappa), where

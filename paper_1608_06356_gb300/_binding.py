@@ -98,6 +98,7 @@ SIGNATURES = {
     "qed_read_counters": (C.c_int, [_P, C.POINTER(qed_counters), _P]),
     "qed_reset_counters": (C.c_int, [_P, _P]),
     "qed_last_device_status": (C.c_int, [_P, C.POINTER(C.c_uint32), C.POINTER(C.c_int64)]),
+    "qed_test_wait_expiry": (C.c_int, [_P, _P]),
     "qed_launch_count": (C.c_int64, [_P]),
     "qed_profile_begin": (C.c_int, [_P, C.c_int]),
     "qed_compact_noalloc": (C.c_int, [C.POINTER(qed_species), C.c_int, _P, _P]),

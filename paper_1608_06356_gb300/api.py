@@ -317,6 +317,11 @@ def qed_last_device_status(ctx: Context) -> tuple[int, int]:
     return int(bits.value), int(dropped.value)
 
 
+def qed_test_wait_expiry(ctx: Context, stream=None) -> None:
+    """Launch the bounded-wait expiry check (sets QED_STATUS_TIMEOUT on the device)."""
+    B.check(B.lib().qed_test_wait_expiry(ctx.handle, _stream(stream)), "qed_test_wait_expiry")
+
+
 def qed_profile_begin(ctx: Context, max_steps: int) -> None:
     B.check(B.lib().qed_profile_begin(ctx.handle, int(max_steps)), "qed_profile_begin")
 

@@ -81,7 +81,7 @@ static void free_ctx(qed_ctx *c) {
                   c->heavy_flags, c->heavy_list, c->heavy_n, c->cls_chunk_cnt,
                   c->cls_chunk_off, c->cls_off, c->sub_cnt, c->sub_gf, c->rec_e,
                   c->rec_k, c->sub_meta, c->fill_meta, c->replay_n, c->stage, c->stage_tag,
-                  c->stage_idx, c->stage_n,
+                  c->stage_idx, c->stage_n, c->probe_state,
                   c->mlp_mem};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -247,7 +247,8 @@ extern "C" int qed_init_tables(const qed_config *cfg, qed_ctx **out, qed_stream_
       cudaMalloc(&c->stage_n, sizeof(unsigned int)) != cudaSuccess ||
       cudaMalloc(&c->sub_meta, 4 * sizeof(int64_t)) != cudaSuccess ||
       cudaMalloc(&c->fill_meta, 2 * sizeof(int64_t)) != cudaSuccess ||
-      cudaMalloc(&c->replay_n, sizeof(unsigned int)) != cudaSuccess) {
+      cudaMalloc(&c->replay_n, sizeof(unsigned int)) != cudaSuccess ||
+      cudaMalloc(&c->probe_state, 2 * sizeof(unsigned long long)) != cudaSuccess) {
     free_ctx(c);
     return QED_ERR_NOMEM;
   }
@@ -256,6 +257,7 @@ extern "C" int qed_init_tables(const qed_config *cfg, qed_ctx **out, qed_stream_
   if (e == cudaSuccess) e = cudaMemsetAsync(c->snap, 0, sizeof(int64_t) * 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->d_counters, 0, sizeof(qed_counters), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->stage_n, 0, sizeof(unsigned int), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->probe_state, 0, 2 * sizeof(unsigned long long), st);
   if (e != cudaSuccess) { free_ctx(c); return cuda_fail(e, "memset"); }
   // epoch starts at 1 so that zeroed state words never look valid
   unsigned int init_sync[4] = {0u, 0u, 1u, 0u};
@@ -476,6 +478,23 @@ extern "C" int qed_reset_counters(qed_ctx *c, qed_stream_t stream) {
   if (!c) return QED_ERR_ARG;
   return cuda_fail(cudaMemsetAsync(c->d_counters, 0, sizeof(qed_counters), (cudaStream_t)stream),
                    "qed_reset_counters");
+}
+
+// One decoupled look-back (one warp) for tile 1 behind a tile 0 whose state
+// word stays zero -- never published, so never valid for epoch 1: lane 0 polls
+// it until the spin limit, records QED_STATUS_TIMEOUT and the walk ends.
+__global__ void k_wait_expiry(unsigned long long *words, qed_counters *cnt) {
+  const ScanState S{words, nullptr, 2};
+  uint32_t status = 0;
+  lookback_warp(S, 1, 1u, 0u, status);
+  if (threadIdx.x == 0 && status) atomicOr(&cnt->status, status);
+}
+
+extern "C" int qed_test_wait_expiry(qed_ctx *c, qed_stream_t stream) {
+  if (!c) return QED_ERR_ARG;
+  k_wait_expiry<<<1, 32, 0, (cudaStream_t)stream>>>(c->probe_state, c->d_counters);
+  c->launches += 1;
+  return cuda_fail(cudaGetLastError(), "qed_test_wait_expiry");
 }
 
 extern "C" int qed_last_device_status(qed_ctx *c, uint32_t *bits, int64_t *dropped) {

@@ -41,6 +41,7 @@ struct qed_ctx {
   int64_t *sub_meta;  // [4] appends of the emission (or pair) entries, counts before them
   int64_t *fill_meta; // [2] count before and after a hole-filling compaction
   unsigned int *replay_n;  // entries the writing pass leaves to its replay launch
+  unsigned long long *probe_state;  // [2] look-back words of qed_test_wait_expiry (tile 0 never published)
   // staging records of the flagged leptons (streaming pass -> later passes)
   void *stage;          // Stage<Real> [stage_cap] (64 B FP32, 128 B FP64)
   uint32_t *stage_tag;  // [stage_cap]

@@ -113,6 +113,7 @@ def test_entry_points_reject_a_null_context(qlib):
     assert lib.qed_compact_fill(None, None, None) == -1
     assert lib.qed_compact(None, None, None) == -1
     assert lib.qed_profile_end_phases(None, None, None) == -1
+    assert lib.qed_test_wait_expiry(None, None) == -1
 
 
 def test_missing_library_fails_loudly(qlib, monkeypatch, tmp_path):

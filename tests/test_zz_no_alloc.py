@@ -8,8 +8,8 @@ that of qed_compact, the context-based entry point, element by element (the
 compaction moves values, so the comparison is exact), on two calls in a row --
 the second call reuses the array the first one left behind.
 
-This file is collected last, so a run that stops at the first failure has run
-every other test before it."""
+This file is collected after the parity tests, so a run that stops at the
+first failure has run them before it."""
 import ctypes as C
 
 import numpy as np
