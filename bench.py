@@ -1,20 +1,27 @@
 """Benchmark of the per-macroparticle QED Monte Carlo step on GB300.
 
-Workload (one step = one qed_step_fused pass over all species): 2^26 = 64M
-electrons with chi log-uniform in [1e-3, 1e2] and gamma log-uniform in
-[1e2, 1e4], per-particle fields (B perpendicular to p, |B| = chi a_S/|p|,
-E = 0), Dt = 0.01 / omega0, table sampler, FP32 state.  Photons (and the
-pairs they create) accumulate across steps and are advanced in the steps
-after their birth.
+Headline workload (one step = one qed_step_fused pass): 2^26 = 64M electrons
+with chi log-uniform in [1e-3, 1e2] and gamma log-uniform in [1e2, 1e4],
+per-particle fields (B perpendicular to p, |B| = chi a_S/|p|, E = 0),
+Dt = 0.01 / omega0, FP32 state.  Every step starts from the same ensemble:
+the electrons' positions and momenta are restored from a device copy and the
+photon buffer is emptied before the step (both inside the timed region), so
+each step advances exactly 64M electrons and the work per step does not
+drift with the step count.  Two arms on identical inputs: the table sampler
+and the learned sampler (network trained here on the device).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Prints one JSON line.  `value` = particle-steps per second over all ranks
-(device-resident inputs); `e2e` = the same metric with the state on the host,
-copied in and out around every step; `roofline` = the lepton kernel's
-algorithmic bytes per launch over its CUDA-event time against the measured
-HBM copy bandwidth; `cpu_baseline` = the FP64 oracle on the host's cores on
-a bounded sample.  `--impl reference` times that oracle alone.
+Prints one JSON line.  `value` = particle-steps per second of the table arm
+over all ranks (device-resident inputs); `arms` holds both samplers;
+`e2e` = the same metric with the ensemble on pinned host memory, copied in
+and the results copied out around every step; `roofline` = the lepton step's
+algorithmic bytes over its CUDA-event time against the measured HBM copy
+bandwidth; `cpu_baseline` = the FP64 oracle on the host's cores on a bounded
+sample.  No value is printed for a run that dropped appends (capacity
+overflow).  Secondary blocks: the isolated sampler, batched runs, the paper's
+single-particle, uniform-field and 3D cascade configurations, and the
+settings of Figs. 1, 2 and 5.  `--impl reference` times the oracle alone.
 """
 from __future__ import annotations
 
@@ -37,36 +44,48 @@ UNIT = "particle-steps/s"
 N_PART = 1 << 26
 DT = 0.01
 DEFAULT_STEPS, DEFAULT_WARMUP, DEFAULT_E2E_STEPS = 10, 3, 2
-COMPACT_EVERY = 4  # dead photons (pair conversions) are removed every this many steps
 LEPTON_BYTES = 84       # R x,y,z,px,py,pz,w (28) + id (8) + E,B (24); W x,y,z,px,py,pz (24)
-LEPTON_STREAM_BYTES = 81  # streaming pass alone: R x..pz, id, E,B (56); W x..pz (24) + class flag (1)
-# DRAM bytes (read + write) per lepton of one lepton step, from an ncu capture of
-# the lepton-step kernels (None when the kernels changed since it was taken)
-LEPTON_TRAFFIC_PER_LEPTON = 178.0
+LEPTON_STREAM_BYTES = 80  # streaming pass alone: R x..pz, id, E,B (56); W x..pz (24)
 PHOTON_APPEND_BYTES = 61  # x,y,z,px,py,pz,w (28) + id (8) + alive (1) + inherited E,B (24)
-PHOTON_BYTES = 85       # photon step: R 28+8+1+24, W x,y,z (12) [+ alive on pair]
+# photons a fresh electron of the headline ensemble emits per step: the mean of
+# W_rad Dt over the ensemble is 0.184 (an upper bound of the mean event count);
+# the photon buffer holds 1.6x that
+PHOTONS_PER_ELECTRON_CAP = 0.3
+QED_STATUS_CAPACITY = 1
+QED_STATUS_ERRORS = 1 | 4 | 8 | 32  # capacity, non-finite, timeout, replay
 
 
 def workload_desc(n):
-    return {"workload": f"chi-target ensemble: {n} electrons (chi log-uniform [1e-3,1e2], gamma "
-                        "log-uniform [1e2,1e4], per-particle B perp p, E=0), fused step "
-                        "(gather+Boris+chi+rate+Method I+xi+recoil+append; photon push+pairs), "
-                        "table sampler, photons/pairs accumulate; dead photons removed every "
-                        f"{COMPACT_EVERY} steps by stable compaction (qed_compact), live photons "
-                        "counted on the device each step (qed_count_alive)",
-            "particles": n, "dt": DT, "precision": "fp32 state, fp64 chi where it cancels",
-            "sampler": "table", "l2": "inputs larger than L2 (>= 5.4 GB read per step)"}
+    return {"workload": f"chi-target ensemble of {n} electrons (chi log-uniform [1e-3,1e2], gamma "
+                        "log-uniform [1e2,1e4], per-particle B perp p, E=0, Dt=0.01), one fused step "
+                        "(gather+Boris+chi+rate+Method I sub-steps+xi+recoil+photon append; photon "
+                        "stage empty) per step; every step starts from the same ensemble (positions "
+                        "and momenta restored from a device copy, photon buffer emptied, both timed)",
+            "particles_per_step": n, "dt": DT, "precision": "fp32 state, fp64 chi where it cancels",
+            "samplers": ["table", "mlp"], "value_arm": "table",
+            "l2": "inputs larger than L2 (>= 5.6 GB read and written per step)"}
 
 
-def capacities(n, total_steps):
-    """Species capacities and the context's max_particles for n electrons run
-    for total_steps steps: photons at ~0.25 emissions per electron per step at
-    Dt = 0.01 at the start (falling as the ensemble cools), leptons for the
-    pairs the photons of the hottest electrons create (a cascade)."""
-    cap_g = int(n * 0.3 * (total_steps + 1)) + 4096
-    cap_e = 3 * n
-    cap_p = 2 * n
-    return cap_e, cap_p, cap_g, max(cap_g, cap_e)
+def capacities(n):
+    """Buffers of the headline run: the electrons (room for pair electrons,
+    which only a run with photons at the start of a step creates), positrons,
+    and photons for one step's emissions.  Every step starts from the same
+    ensemble, so nothing accumulates and the sizes do not depend on the
+    number of steps.  Returns (cap_e, cap_p, cap_g, max_particles)."""
+    cap_e = n + n // 2
+    cap_p = n // 2
+    cap_g = int(PHOTONS_PER_ELECTRON_CAP * n) + 4096
+    return cap_e, cap_p, cap_g, max(cap_e, cap_g)
+
+
+def run_status(counters: dict) -> str:
+    """'ok', or why the run's throughput is not a measurement: appends were
+    dropped (capacity overflow) or a device error bit was set."""
+    if counters["dropped"] > 0 or counters["status"] & QED_STATUS_CAPACITY:
+        return "overflow"
+    if counters["status"] & QED_STATUS_ERRORS:
+        return f"device-status-{counters['status']}"
+    return "ok"
 
 
 def rank_id_offset(rank: int) -> int:
@@ -82,6 +101,25 @@ def reduce_over_ranks(dist, ms: float, particle_steps: float, device):
     dist.all_reduce(mx, op=dist.ReduceOp.MAX)
     dist.all_reduce(tt, op=dist.ReduceOp.SUM)
     return float(mx[0]), float(tt[1])
+
+
+COUNTER_KEYS = ("emit_events", "pair_events", "substeps", "dropped", "domain", "deferred")
+
+
+def reduce_counters(dist, c: dict, device) -> dict:
+    """End-of-run reduction of the event counters and the 64-bin photon
+    spectrum over ranks (sums; status bits OR-ed): the only collective of the
+    multi-GPU path, about 1 KB."""
+    import torch
+    v = torch.tensor([c[k] for k in COUNTER_KEYS] + list(c["hist"]), dtype=torch.int64, device=device)
+    dist.all_reduce(v, op=dist.ReduceOp.SUM)
+    bits = torch.tensor([(c["status"] >> b) & 1 for b in range(32)], dtype=torch.int64, device=device)
+    dist.all_reduce(bits, op=dist.ReduceOp.MAX)
+    vl = [int(x) for x in v.cpu().tolist()]
+    out = dict(zip(COUNTER_KEYS, vl[:len(COUNTER_KEYS)]))
+    out["hist"] = vl[len(COUNTER_KEYS):]
+    out["status"] = sum(int(b) << i for i, b in enumerate(bits.cpu().tolist()))
+    return out
 
 
 def peaks():
@@ -158,21 +196,191 @@ def host_workload(n, seed, chunk=1 << 22):
     return out
 
 
-def sampler_comparison(api, torch, n, args, reps=5):
+MUTABLE = ("x", "y", "z", "px", "py", "pz")
+LEPTON_ARRAYS = ("x", "y", "z", "px", "py", "pz", "w", "id", "ex", "ey", "ez", "bx", "by", "bz")
+
+
+class Headline:
+    """The headline ensemble on the device: electrons whose positions and
+    momenta live in one [6, capacity] block, a pristine copy of them, and the
+    positron and photon buffers.  `restore()` puts the ensemble back into its
+    initial state (one device copy and two count writes)."""
+
+    def __init__(self, api, torch, n, host):
+        cap_e, cap_p, cap_g, self.max_particles = capacities(n)
+        self.n = n
+        self.torch = torch
+        e = api.Species.empty(cap_e, -1, fields=True)
+        self.blk = torch.empty((6, cap_e), dtype=torch.float32, device="cuda")
+        for r, k in enumerate(MUTABLE):
+            setattr(e, k, self.blk[r])
+        e.load(**host)
+        self.pristine = self.blk[:, :n].clone()
+        self.e = e
+        self.p = api.Species.empty(cap_p, +1, fields=True)
+        self.g = api.Species.empty(cap_g, 0, fields=True)
+
+    def restore(self):
+        self.blk[:, :self.n].copy_(self.pristine)
+        self.e.n.fill_(self.n)
+        self.p.n.zero_()
+        self.g.n.zero_()
+
+
+def time_arm(api, torch, ctx, H, F, steps, warmup, step0, dist=None, profile=True):
+    """W untimed and K timed headline steps on one context; returns times,
+    counters and the library's per-phase event times."""
+    stream = torch.cuda.current_stream()
+    for s in range(warmup):
+        H.restore()
+        api.qed_step_fused(ctx, H.e, H.p, H.g, F, step0 + s)
+    torch.cuda.synchronize()
+    api.qed_reset_counters(ctx)
+    if profile:
+        api.qed_profile_begin(ctx, steps)
+    l0 = ctx.launches
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for k in range(steps):
+        H.restore()
+        api.qed_step_fused(ctx, H.e, H.p, H.g, F, step0 + warmup + k)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms = t0.elapsed_time(t1)
+    out = {"ms": ms, "launches": ctx.launches - l0 + 0, "counters": api.qed_read_counters(ctx),
+           "photons_last_step": H.g.count()}
+    if profile:
+        out["phases"], out["nprof"] = api.qed_profile_end_phases(ctx)
+    return out
+
+
+def lepton_roofline(r, n, steps, peak, peak_kind):
+    """Roofline of the lepton step (the per-lepton unit whose algorithmic
+    bytes are 84 B + 61 B per emitted photon): its five phases (streaming
+    pass, class list, counting pass, scan, writing pass) are timed by CUDA
+    events recorded on the launching stream between them."""
+    import paper_1608_06356_gb300.api as A
+    phases, nprof = r["phases"], max(r["nprof"], 1)
+    lep_ms = sum(phases[k] for k in A.PROF_PHASES[:5]) / nprof
+    emitted = r["counters"]["emit_events"] / steps
+    lep_bytes = LEPTON_BYTES * n + PHOTON_APPEND_BYTES * emitted
+    achieved = lep_bytes / (lep_ms * 1e-3) / 1e9
+    stream_ms = phases["lepton_stream"] / nprof
+    return {"bound": "hbm",
+            "kernel": "lepton step: k_lepton_stream + k_cls_count/scan/scatter + k_substep_count + "
+                      "k_sub_scan + k_substep_write_coop + k_substep_replay",
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": f"{peak_kind} HBM copy (MEASURED_PEAKS.json hbm_gbs)",
+            "traffic": None,
+            "traffic_note": "per-launch DRAM bytes of the lepton kernels are in profiles/ "
+                            "(ncu capture of the same kernels at 4M electrons, scaled by units)",
+            "bytes_per_launch": lep_bytes, "ms_per_launch": lep_ms,
+            "algorithmic_bytes": "84 B per lepton + 61 B per emitted photon",
+            "emitted_per_step": emitted,
+            "phases_ms_per_step": {k: v / nprof for k, v in phases.items()},
+            "deferred_fraction": r["counters"]["deferred"] / max(n * steps, 1),
+            "streaming_pass": {"bytes_per_launch": LEPTON_STREAM_BYTES * n,
+                               "ms_per_launch": stream_ms,
+                               "achieved_gbs": LEPTON_STREAM_BYTES * n / (stream_ms * 1e-3) / 1e9}}
+
+
+def e2e_arm(api, torch, ctx, H, F, host, steps, step0):
+    """The headline step through the public API with the ensemble on pinned
+    host memory: every step copies the electrons in, runs qed_step_fused,
+    reads the photon count and copies the electrons' new state and the new
+    photons back."""
+    n = H.n
+    stream = torch.cuda.current_stream()
+    pin_in = {k: torch.from_numpy(host[k].view(np.int64) if k == "id" else host[k]).pin_memory()
+              for k in LEPTON_ARRAYS}
+    cap_g = H.g.capacity
+    pin_out = {k: torch.empty(n, dtype=torch.float32, pin_memory=True) for k in MUTABLE}
+    pin_g = {k: torch.empty(cap_g, dtype=getattr(H.g, k).dtype, pin_memory=True)
+             for k in LEPTON_ARRAYS + ("alive",)}
+    n_host = torch.zeros(1, dtype=torch.int64, pin_memory=True)
+    h2d = d2h = 0
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for k in range(steps):
+        for nm in LEPTON_ARRAYS:
+            getattr(H.e, nm)[:n].copy_(pin_in[nm], non_blocking=True)
+            h2d += n * pin_in[nm].element_size()
+        H.e.n.fill_(n)
+        H.g.n.zero_()
+        api.qed_step_fused(ctx, H.e, H.p, H.g, F, step0 + k)
+        n_host.copy_(H.g.n, non_blocking=True)
+        stream.synchronize()
+        m = int(n_host[0])
+        d2h += 8
+        for nm in MUTABLE:
+            pin_out[nm].copy_(getattr(H.e, nm)[:n], non_blocking=True)
+            d2h += 4 * n
+        for nm, t in pin_g.items():
+            t[:m].copy_(getattr(H.g, nm)[:m], non_blocking=True)
+            d2h += m * t.element_size()
+        stream.synchronize()
+    wall = time.perf_counter() - w0
+    return {"value": n * steps / wall, "unit": UNIT,
+            "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps, "steps": steps,
+            "note": "ensemble on pinned host memory; every step copies the 64M electrons in "
+                    "(60 B each), runs qed_step_fused, reads the photon count and copies the "
+                    "electrons' positions and momenta and the new photons back"}
+
+
+def spectral_error(api, torch, ctx_m, ctx_judge, n_chi=64, gamma=1e4, iters=34):
+    """Deterministic spectral error of the learned sampler: at n_chi values of
+    chi log-spaced over its domain [1e-3, 1e2], the uniform u at each of the 65
+    edges of 64 log bins of xi over [2/gamma, 1] is found by bisection in u
+    (the sampler is monotone in u), giving the sampler's bin probabilities;
+    `ctx_judge`'s inverse table gives the reference ones the same way.  Returns
+    the largest relative error over bins with probability >= 1e-3, and the
+    largest total-variation distance, over all chi."""
+    chis = np.exp(np.linspace(np.log(1e-3), np.log(1e2), n_chi))
+    edges = np.exp(np.linspace(np.log(2.0 / gamma), 0.0, 65))
+    C_ = np.repeat(chis, 65)
+    X = np.tile(edges, n_chi)
+    chi_d = torch.tensor(C_, device="cuda")
+    g_d = torch.full_like(chi_d, gamma)
+
+    def u_at_edges(ctx, which):
+        lo = np.zeros(len(C_), dtype=np.int64)
+        hi = np.full(len(C_), 2 ** 32, dtype=np.int64)  # xi(word) >= edge for word >= hi
+        for _ in range(iters):
+            mid = (lo + hi) // 2
+            w = torch.tensor((np.minimum(mid, 2 ** 32 - 1)).astype(np.uint32).view(np.int32),
+                             device="cuda")
+            xi = api.qed_sample_table(ctx, which, chi_d, g_d, w).cpu().numpy()
+            below = xi < X
+            lo = np.where(below, mid, lo)
+            hi = np.where(below, hi, mid)
+        return hi.astype(np.float64) * 2.0 ** -32  # u of the first word at or above the edge
+
+    um = u_at_edges(ctx_m, 2).reshape(n_chi, 65)
+    ut = u_at_edges(ctx_judge, 0).reshape(n_chi, 65)
+    pm, pt = np.diff(um, axis=1), np.diff(ut, axis=1)
+    big = pt >= 1e-3
+    rel = np.where(big, np.abs(pm - pt) / np.maximum(pt, 1e-300), 0.0)
+    tv = 0.5 * np.abs(pm - pt).sum(axis=1)
+    return {"max_rel_error_bins_p_ge_1e-3": float(rel.max()),
+            "median_rel_error_bins_p_ge_1e-3": float(np.median(rel[big])),
+            "max_total_variation": float(tv.max()), "chi_nodes": n_chi, "bins": 64,
+            "gamma": gamma, "judge": "FP64 inverse table of the same library (bisection in u)"}
+
+
+def sampler_comparison(api, torch, n, ctx_t, ctx_m, reps=5):
     """Isolated inverse-CDF sampler (qed_sample_xi) at n samples, table vs the
-    learned network (trained here on the device), with the spectral error."""
+    learned network: 12 B per sample (chi, gamma read, xi written)."""
     rng = np.random.default_rng(123)
     chi = torch.tensor(np.exp(rng.uniform(np.log(1e-3), np.log(1e2), n)).astype(np.float32), device="cuda")
     gam = torch.tensor(np.exp(rng.uniform(np.log(1e2), np.log(1e4), n)).astype(np.float32), device="cuda")
     out = torch.empty(n, device="cuda")
     res = {}
-    ctx_t = api.qed_init_tables(api.config(dt=DT, seed=5))
-    ctx_m = api.qed_init_tables(api.config(dt=DT, seed=5, sampler=1))
-    api.qed_mlp_load(ctx_m, api.mlp_init_params(0))
-    t0 = time.perf_counter()
-    loss = api.qed_mlp_train(ctx_m, int(args.mlp_train_samples), lr=6e-3, seed=7)
-    train_s = time.perf_counter() - t0
-    peak, kind = peaks()
+    peak, _ = peaks()
     for name, ctx in (("table", ctx_t), ("mlp", ctx_m)):
         for s in range(3):
             api.qed_sample_xi(ctx, chi, gam, out, s)
@@ -189,25 +397,8 @@ def sampler_comparison(api, torch, n, args, reps=5):
                      "frac_hbm": 12 * n / (ms * 1e-3) / 1e9 / peak}
     # tensor work of the network: layers 2 and 3, 64x64 MACs, three split-BF16 products each
     res["mlp"]["tensor_tflops"] = 2 * 3 * 2 * 64 * 64 * res["mlp"]["samples_per_s"] / 1e12
-    # spectral error: 64 log bins of xi at five chi values, 2^16 paired draws each
-    errs = []
-    nu = 1 << 16
-    for c in (3e-3, 0.03, 0.3, 3.0, 30.0):
-        cc = torch.full((nu,), c, device="cuda")
-        gg = torch.full((nu,), 1000.0, device="cuda")
-        xm, xt = torch.empty(nu, device="cuda"), torch.empty(nu, device="cuda")
-        api.qed_sample_xi(ctx_m, cc, gg, xm, 5)
-        api.qed_sample_xi(ctx_t, cc, gg, xt, 5)
-        edges = np.exp(np.linspace(np.log(2e-3), 0.0, 65))
-        pm = np.histogram(xm.cpu().numpy(), edges)[0] / nu
-        pt = np.histogram(xt.cpu().numpy(), edges)[0] / nu
-        big = pt >= 1e-3
-        errs.append(float(np.max(np.abs(pm[big] - pt[big]) / pt[big])))
-    res["mlp"].update({"train_samples": int(args.mlp_train_samples), "train_s": train_s,
-                       "train_loss_mse_lndelta": loss, "spectral_error_max_rel": max(errs)})
     res["mlp_over_table_speed"] = res["mlp"]["samples_per_s"] / res["table"]["samples_per_s"]
     res["n"] = n
-    res["_weights"] = api.qed_mlp_get(ctx_m)
     return res
 
 
@@ -242,17 +433,14 @@ def batched_runs_bench(api, torch, mlp_weights, steps=4):
             cnt = torch.zeros((steps, 3), dtype=torch.int64, device="cuda")
             if mode == "graph":  # capture (first call), then time a replay from the same state
                 api.qed_run_batched(ctx, e, p, g, F, 0, steps)
-                torch.cuda.synchronize()
-                e.load(**host)
-                p.n.zero_()
-                g.n.zero_()
             else:  # load kernels once, then restore the state
                 api.qed_step_fused(ctx, e, p, g, F, 0)
                 api.qed_compact_fill(ctx, g)
-                torch.cuda.synchronize()
-                e.load(**host)
-                p.n.zero_()
-                g.n.zero_()
+            torch.cuda.synchronize()
+            e.load(**host)
+            p.n.zero_()
+            g.n.zero_()
+            api.qed_reset_counters(ctx)
             torch.cuda.synchronize()
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             l0 = ctx.launches
@@ -268,9 +456,10 @@ def batched_runs_bench(api, torch, mlp_weights, steps=4):
             b.record()
             torch.cuda.synchronize()
             ms = a.elapsed_time(b)
+            c = api.qed_read_counters(ctx)
+            res[mode + "_status"] = run_status(c)
             if mode == "eager":
-                ps = float(cnt.sum().item())
-                res["particle_steps"] = ps
+                res["particle_steps"] = float(cnt.sum().item())
                 res["eager_launches"] = ctx.launches - l0
             res[mode + "_ms_per_step"] = ms / steps
             if mode == "graph":
@@ -310,14 +499,16 @@ def generator_rates(api, torch, steps=480, dt=0.01):
                                  torch.tensor([float(np.sqrt(1 + float(p0) ** 2))], device="cuda"))[0])
         out["W_rad_initial"] = W0
         out[name] = {"rate_first_48_steps": float(cum[47]) / (n * 48 * dt),
-                     "rate_all_steps": float(cum[-1]) / (n * steps * dt)}
+                     "rate_all_steps": float(cum[-1]) / (n * steps * dt),
+                     "status": run_status(api.qed_read_counters(ctx))}
     return out
 
 
 def spectra_fig1(api, torch, nu=1 << 20, gamma=1000.0):
     """Fig. 1's comparison: photon-energy spectra (dW/dxi, 16 log bins of xi
     over [2/gamma, 1]) sampled with the formula-I and the classic-limit
-    tables at chi = 0.1, 1 and 10, and their ratio per bin."""
+    tables at chi = 0.1, 1 and 10, and their ratio per bin (null where the
+    formula-I bin is empty)."""
     edges = np.exp(np.linspace(np.log(2.0 / gamma), 0.0, 17))
     out = {"gamma": gamma, "samples": nu, "xi_edges": edges.tolist()}
     hist = {}
@@ -331,12 +522,13 @@ def spectra_fig1(api, torch, nu=1 << 20, gamma=1000.0):
             # rate-weighted: the classic and formula-I totals differ
             W = float(api.qed_rates(ctx, 0, torch.tensor([chi], device="cuda"),
                                     torch.tensor([gamma], device="cuda"))[0])
-            h = np.histogram(xi.cpu().numpy(), edges)[0] / nu * W / np.diff(edges)
-            hist[(name, chi)] = h
+            cnt = np.histogram(xi.cpu().numpy(), edges)[0]
+            hist[(name, chi)] = (cnt, cnt / nu * W / np.diff(edges))
     for chi in (0.1, 1.0, 10.0):
-        out[f"chi_{chi:g}"] = {"dW_dxi_formula_I": hist[("formula_I", chi)].tolist(),
-                               "classic_over_formula_I": (hist[("classic", chi)] /
-                                                          np.maximum(hist[("formula_I", chi)], 1e-300)).tolist()}
+        cI, dI = hist[("formula_I", chi)]
+        cC, dC = hist[("classic", chi)]
+        ratio = [float(a / b) if n > 0 else None for a, b, n in zip(dC, dI, cI)]
+        out[f"chi_{chi:g}"] = {"dW_dxi_formula_I": dI.tolist(), "classic_over_formula_I": ratio}
     return out
 
 
@@ -387,67 +579,243 @@ def cascade_fig5(api, torch, runs=4000, t_end_trad=2.5, steps_per_trad=60):
             "t_rad_in_inverse_omega0": t_rad, "steps": steps,
             "t_over_t_rad": times, "pairs_above_100MeV_per_run": pairs,
             "pairs_per_run_total": c["pair_events"] / n, "photons_emitted_per_run": c["emit_events"] / n,
-            "status": c["status"], "dropped": c["dropped"],
+            "status": run_status(c), "dropped": c["dropped"],
             "particles_at_end": {"electrons": e.count(), "positrons": p.count(), "photons": g.count()},
             "particle_steps_per_s": ps / (t0.elapsed_time(t1) * 1e-3),
             "note": "wall time includes a host read of the counts every step"}
 
 
-def cpu_baseline(sample_n=12288, steps=2, seed=0):
-    """The FP64 oracle as it stands on a bounded sample of the same workload."""
+def _block_roofline(bytes_per_step, ms_per_step, peak, peak_kind, bound="hbm"):
+    a = bytes_per_step / (ms_per_step * 1e-3) / 1e9
+    return {"bound": bound, "achieved": a, "peak": peak, "unit": "GB/s", "frac": a / peak,
+            "peak_source": f"{peak_kind} HBM copy"}
+
+
+def _oracle_block_baseline(make_species, cfg_kw, fields, steps):
+    """The oracle on a bounded sample of a configuration: particle-steps/s."""
+    import oracle as O
+    O.build()
+    cfg = O.make_config(**cfg_kw)
+    e, p, g = make_species(O)
+    ps, t0 = 0, time.perf_counter()
+    for s in range(steps):
+        ps += e.n + p.n + g.n
+        O.step(cfg, fields(O), e, p, g, s)
+    dt = time.perf_counter() - t0
+    return {"value": ps / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "seconds": dt, "particle_steps": ps}
+
+
+def config_single_particle(api, torch, n=10_000, steps=1000, cpu_n=2000, cpu_steps=2):
+    """The paper's single-particle-type test: 10^4 electrons, gamma0 = 1000 along
+    x, uniform B = 410 along z (chi_e ~ 1), E = 0, Dt = 0.01, 1000 steps, photon
+    emission only (formula I), FP64, Philox seed 0; output: the photon
+    spectrum in 64 log bins of energy over [2, 1000] m c^2.  Launch-bound
+    (10^4 particles per launch), so its roofline is reported for context."""
+    from paper_1608_06356_gb300 import workloads as W
+    st, fld = W.single(n)
+    ctx = api.qed_init_tables(api.config(dt=0.01, seed=0, precision=1, max_particles=1 << 22))
+    e = api.Species.empty(n, -1, dtype=torch.float64).load(**st)
+    g = api.Species.empty(1 << 22, 0, dtype=torch.float64)
+    F = api.Fields.uniform(fld["E"], fld["B"])
+    for s in range(3):  # load the kernels
+        api.qed_gather_push(ctx, e, F, s)
+        api.qed_emit(ctx, e, g, F, s)
+    e.load(**st)
+    g.n.zero_()
+    api.qed_reset_counters(ctx)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for s in range(steps):
+        api.qed_gather_push(ctx, e, F, s)
+        api.qed_emit(ctx, e, g, F, s)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    c = api.qed_read_counters(ctx)
+    peak, kind = peaks()
+    # FP64: lepton 64 B read + 48 B written (push + emission read it again: 2x), photon append 64 B
+    bytes_step = 2 * (64 + 48) * n + 64 * c["emit_events"] / steps
+    base = _oracle_block_baseline(
+        lambda O: (O.Species(cpu_n, -1.0).load(**{k: v[:cpu_n] for k, v in st.items()}),
+                   O.Species(1, 1.0), O.Species(cpu_n * 4, 0.0, with_alive=True)),
+        {"dt": 0.01, "seed": 0}, lambda O: O.uniform_fields(fld["E"], fld["B"]), cpu_steps)
+    base["sample"] = f"{cpu_n} electrons x {cpu_steps} steps (fused oracle step; no photons present)"
+    return {"electrons": n, "steps": steps, "precision": "fp64", "status": run_status(c),
+            "particle_steps_per_s": n * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+            "photons": g.count(), "emit_events": c["emit_events"],
+            "photon_spectrum_64_log_bins_2_to_1000": c["hist"],
+            "roofline": _block_roofline(bytes_step, ms / steps, peak, kind, bound="launch"),
+            "cpu_baseline": base}
+
+
+def config_uniform_ensemble(api, torch, n=1 << 20, steps=200, compact_every=4, cpu_n=1024):
+    """The uniform-field ensemble: 2^20 electrons + 2^20 photons, gamma (and
+    photon |p|) log-uniform in [1e2, 1e4], isotropic directions, per-particle E,
+    B with isotropic directions and magnitudes log-uniform in [10, 2000];
+    emission and Breit-Wheeler pairs, FP32 state (FP32 table look-ups, FP64
+    chi where it cancels), Dt = 0.01, 200 steps; children inherit their
+    parent's fields.  Dead photons are removed every 4 steps (qed_compact_fill)."""
+    from paper_1608_06356_gb300 import workloads as W
+    se = W.ensemble(n, seed=0)
+    sg = W.ensemble(n, seed=1, photons=True, id0=1 << 32)
+    f32 = lambda d: {k: (v.astype(np.float32) if v.dtype.kind == "f" else v) for k, v in d.items()}
+    se, sg = f32(se), f32(sg)
+    cap = 1 << 25
+    ctx = api.qed_init_tables(api.config(dt=DT, seed=3, max_particles=cap))
+    e = api.Species.empty(cap, -1, fields=True).load(**se)
+    p = api.Species.empty(cap, 1, fields=True)
+    g = api.Species.empty(cap, 0, fields=True).load(**sg)
+    F = api.Fields.per_particle()
+    cnt = torch.zeros((steps, 2), dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for s in range(steps):
+        cnt[s, 0].copy_(e.n[0] + p.n[0])
+        api.qed_count_alive(ctx, g, cnt[s, 1:2])
+        api.qed_step_fused(ctx, e, p, g, F, s)
+        if (s + 1) % compact_every == 0:
+            api.qed_compact_fill(ctx, g)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    c = api.qed_read_counters(ctx)
+    cn = cnt.cpu().numpy()
+    ps = float(cn.sum())
+    peak, kind = peaks()
+    # lepton 84 B, photon 68 B per particle-step; appends 61 B per photon, 2 x 61 + 1 B per pair
+    bytes_total = 84 * cn[:, 0].sum() + 68 * cn[:, 1].sum() + 61 * c["emit_events"] + 123 * c["pair_events"]
+    base = _oracle_block_baseline(
+        lambda O: (O.Species(cpu_n * 4, -1.0, per_particle_fields=True).load(
+                       **{k: v[:cpu_n].astype(np.float64) if v.dtype.kind == "f" else v[:cpu_n]
+                          for k, v in se.items()}),
+                   O.Species(cpu_n * 2, 1.0, per_particle_fields=True),
+                   O.Species(cpu_n * 8, 0.0, per_particle_fields=True, with_alive=True).load(
+                       **{k: v[:cpu_n].astype(np.float64) if v.dtype.kind == "f" else v[:cpu_n]
+                          for k, v in sg.items()})),
+        {"dt": DT, "seed": 3}, lambda O: O.per_particle_fields(), 2)
+    base["sample"] = f"{cpu_n} electrons + {cpu_n} photons of the same ensemble x 2 steps"
+    return {"electrons": n, "photons": n, "steps": steps, "status": run_status(c),
+            "particle_steps_per_s": ps / (ms * 1e-3), "ms_per_step": ms / steps,
+            "particles_at_end": {"leptons": e.count() + p.count(), "photons_alive": int(cn[-1, 1])},
+            "emit_events": c["emit_events"], "pair_events": c["pair_events"],
+            "roofline": _block_roofline(bytes_total / steps, ms / steps, peak, kind),
+            "cpu_baseline": base}
+
+
+def config_3d_cascade(api, torch, steps=40, seed_n=1 << 24, cap=1 << 28, nx=256, a0=800.0,
+                      dt=0.1, compact_every=4, cpu_n=4096):
+    """The 3D PIC-like cascade: a 256^3 periodic grid (dx = 2 pi / 32) of two
+    counter-propagating circularly polarised standing waves of amplitude
+    a0 = 800 each, filled on the device at every step's time; 16M electrons at
+    rest, uniform in the central 64^3 cells; CIC gather + Boris + emission and
+    pairs with in-place appends into preallocated 256M-slot buffers per species,
+    FP32, Dt = 0.1.  The first `steps` of the 500-step run are timed (a slice):
+    the particle count grows and the step cost with it.  Grid bytes: the field
+    fill (32 B per node written) plus one read of the touched nodes' 32 B."""
+    from paper_1608_06356_gb300 import workloads as W
+    dx = 2 * np.pi / 32
+    st = W.cascade_seed(seed_n, seed=0, nx=nx, dx=dx)
+    st = {k: (v.astype(np.float32) if v.dtype.kind == "f" else v) for k, v in st.items()}
+    ctx = api.qed_init_tables(api.config(dt=dt, seed=9, max_particles=cap))
+    e = api.Species.empty(cap, -1).load(**st)
+    p = api.Species.empty(cap, 1)
+    g = api.Species.empty(cap, 0)
+    grid = torch.zeros((nx, nx, nx, 8), dtype=torch.float32, device="cuda")
+    F = api.Fields.grid(grid, dx, dx, dx)
+    cnt = torch.zeros((steps, 2), dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for s in range(steps):
+        cnt[s, 0].copy_(e.n[0] + p.n[0])
+        api.qed_count_alive(ctx, g, cnt[s, 1:2])
+        api.qed_fill_standing_wave(ctx, grid, 0.0, dx, a0, s * dt)
+        api.qed_step_fused(ctx, e, p, g, F, s)
+        if (s + 1) % compact_every == 0:
+            api.qed_compact_fill(ctx, g)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    c = api.qed_read_counters(ctx)
+    cn = cnt.cpu().numpy()
+    ps = float(cn.sum())
+    peak, kind = peaks()
+    nodes = nx ** 3
+    bytes_total = (60 * cn[:, 0].sum() + 44 * cn[:, 1].sum() + 37 * c["emit_events"]
+                   + 73 * c["pair_events"] + 2 * 32 * nodes * steps)
+    del e, p, g, grid
+    torch.cuda.empty_cache()
+
+    def mk(O):
+        sub = {k: (v[:cpu_n].astype(np.float64) if v.dtype.kind == "f" else v[:cpu_n]) for k, v in st.items()}
+        return (O.Species(cpu_n * 4, -1.0).load(**sub), O.Species(cpu_n * 2, 1.0),
+                O.Species(cpu_n * 8, 0.0, with_alive=True))
+
+    def fields(O):
+        return O.grid_fields(O.fill_standing_wave(nx, nx, nx, 0.0, dx, a0, 0.0), dx, dx, dx)
+
+    try:
+        base = _oracle_block_baseline(mk, {"dt": dt, "seed": 9}, fields, 2)
+        base["sample"] = f"{cpu_n} seed electrons x 2 steps (grid fields at t = 0)"
+    except Exception as ex:
+        base = {"error": repr(ex)}
+    return {"grid": [nx, nx, nx], "a0": a0, "seed_electrons": seed_n, "capacity_per_species": cap,
+            "steps_timed": steps, "steps_of_run": 500, "dt": dt, "status": run_status(c),
+            "particle_steps_per_s": ps / (ms * 1e-3), "ms_per_step": ms / steps,
+            "particles_per_step_first_last": [int(cn[0].sum()), int(cn[-1].sum())],
+            "emit_events": c["emit_events"], "pair_events": c["pair_events"],
+            "roofline": _block_roofline(bytes_total / steps, ms / steps, peak, kind),
+            "field_fill_bytes_per_step": 32 * nodes, "cpu_baseline": base}
+
+
+def oracle_sample_rate(sample_n, steps, seed=0):
+    """The FP64 oracle as it stands on `sample_n` electrons of the headline
+    ensemble, `steps` steps, each from the same initial state (as the
+    headline's steps are); returns (particle-steps/s, cores, seconds)."""
     import oracle as O
     from paper_1608_06356_gb300 import workloads as W
+    O.build()
     st, _, _ = W.chi_target(sample_n, seed=seed)
     st = {k: (v.astype(np.float32).astype(np.float64) if v.dtype.kind == "f" else v)
           for k, v in st.items()}
     cfg = O.make_config(dt=DT, seed=1)
-    e = O.Species(sample_n * 2, -1.0, per_particle_fields=True).load(**st)
-    p = O.Species(sample_n, 1.0, per_particle_fields=True)
-    g = O.Species(sample_n * 4 * (steps + 1), 0.0, per_particle_fields=True, with_alive=True)
     f = O.per_particle_fields()
-    t0 = time.perf_counter()
-    ps = 0
+    total = 0.0
     for s in range(steps):
-        ps += e.n + p.n + g.n
+        e = O.Species(sample_n * 2, -1.0, per_particle_fields=True).load(**st)
+        p = O.Species(sample_n, 1.0, per_particle_fields=True)
+        g = O.Species(sample_n * 2, 0.0, per_particle_fields=True, with_alive=True)
+        t0 = time.perf_counter()
         O.step(cfg, f, e, p, g, s)
-    dt = time.perf_counter() - t0
-    return {"value": ps / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"{sample_n} electrons of the same ensemble x {steps} step(s) "
-                      f"({ps} particle-steps in {dt:.1f} s), FP64 quadrature rates"}
+        total += time.perf_counter() - t0
+    return sample_n * steps / total, O.num_threads(), total
+
+
+def cpu_baseline(sample_n=12288, steps=2):
+    v, cores, secs = oracle_sample_rate(sample_n, steps)
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{sample_n} electrons of the headline ensemble x {steps} step(s), each from "
+                      f"the initial state ({sample_n * steps} particle-steps in {secs:.1f} s), "
+                      "FP64 quadrature rates"}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import oracle as O
-    O.build()
-    from paper_1608_06356_gb300 import workloads as W
     n = args.ref_particles
-    st, _, _ = W.chi_target(n, seed=0)
-    st = {k: (v.astype(np.float32).astype(np.float64) if v.dtype.kind == "f" else v)
-          for k, v in st.items()}
-    cfg = O.make_config(dt=DT, seed=1)
-    total = args.warmup + args.steps
-    e = O.Species(n * 2, -1.0, per_particle_fields=True).load(**st)
-    p = O.Species(n, 1.0, per_particle_fields=True)
-    g = O.Species(n * 2 * (total + 1), 0.0, per_particle_fields=True, with_alive=True)
-    f = O.per_particle_fields()
-    for s in range(args.warmup):
-        O.step(cfg, f, e, p, g, s)
-    ps = 0
-    t0 = time.perf_counter()
-    for s in range(args.warmup, total):
-        ps += e.n + p.n + g.n
-        O.step(cfg, f, e, p, g, s)
-    dt = time.perf_counter() - t0
-    v = ps / dt
+    oracle_sample_rate(n, args.warmup)  # warm-up steps (untimed)
+    v, cores, secs = oracle_sample_rate(n, args.steps)
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference", "config": workload_desc(N_PART),
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-                             "sample": f"{n} electrons of the same ensemble per step"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n} electrons of the headline ensemble per step, each step "
+                                       "from the initial state"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -462,9 +830,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=DEFAULT_E2E_STEPS)
     ap.add_argument("--ref-particles", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mlp-train-samples", type=float, default=4e9)
     ap.add_argument("--sampler-bench", type=int, default=1)
     ap.add_argument("--batched-bench", type=int, default=1)
-    ap.add_argument("--mlp-train-samples", type=float, default=4e9)
+    ap.add_argument("--configs-bench", type=int, default=1)
     ap.add_argument("--generator-bench", type=int, default=1)
     ap.add_argument("--cascade-bench", type=int, default=1)
     ap.add_argument("--spectra-bench", type=int, default=1)
@@ -491,167 +860,86 @@ def main():
     from paper_1608_06356_gb300 import api
 
     n = args.particles
-    cap_e, cap_p, cap_g, max_particles = capacities(n, args.warmup + args.steps + args.e2e_steps)
-    ctx = api.qed_init_tables(api.config(dt=DT, seed=1 + rank, max_particles=max_particles))
     host = host_workload(n, seed=rank)
     host["id"] += np.uint64(rank_id_offset(rank))
-    e = api.Species.empty(cap_e, -1, fields=True).load(**host)
-    p = api.Species.empty(cap_p, +1, fields=True)
-    g = api.Species.empty(cap_g, 0, fields=True)
+    H = Headline(api, torch, n, host)
     F = api.Fields.per_particle()
-    counts = torch.zeros((args.steps, 3), dtype=torch.int64, device="cuda")
-    stream = torch.cuda.current_stream()
+    ctx_t = api.qed_init_tables(api.config(dt=DT, seed=1 + rank, max_particles=H.max_particles))
+    ctx_m = api.qed_init_tables(api.config(dt=DT, seed=1 + rank, max_particles=H.max_particles,
+                                           sampler=1))
+    api.qed_mlp_load(ctx_m, api.mlp_init_params(0))
+    t_train = time.perf_counter()
+    train_loss = api.qed_mlp_train(ctx_m, int(args.mlp_train_samples), lr=6e-3, seed=7)
+    train_s = time.perf_counter() - t_train
+    wts = api.qed_mlp_get(ctx_m)
+    dd = dist if world > 1 else None
 
-    def one_step(k, s):
-        counts[k, 0].copy_(e.n[0] + p.n[0])
-        api.qed_count_alive(ctx, g, counts[k, 1:2])  # photons the step advances
-        api.qed_step_fused(ctx, e, p, g, F, s)
-        if (s + 1) % COMPACT_EVERY == 0:
-            api.qed_compact(ctx, g)
-
-    # warm-up runs the exact loop body, so every kernel (ours and torch's) is loaded
-    for s in range(args.warmup):
-        one_step(0, s)
-    torch.cuda.synchronize()
-    api.qed_reset_counters(ctx)
-    c_before = api.qed_read_counters(ctx)
-    api.qed_profile_begin(ctx, args.steps)
-    launches0 = ctx.launches
     clk = ClockSampler(local)
     clk.start()
     time.sleep(0.3)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0.record(stream)
-    for k in range(args.steps):
-        one_step(k, args.warmup + k)
-    t1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    arms = {}
+    for name, ctx in (("table", ctx_t), ("mlp", ctx_m)):
+        arms[name] = time_arm(api, torch, ctx, H, F, args.steps, args.warmup, 0, dd)
     clocks = clk.stop()
-    launches = ctx.launches - launches0
-    ms = t0.elapsed_time(t1)
-    phases, nprof = api.qed_profile_end_phases(ctx)
-    lep_ms = sum(phases[k] for k in api.PROF_PHASES[:5])
-    pho_ms = phases["photon_stream"] + phases["photon_ordered"]
-    c_after = api.qed_read_counters(ctx)
-    cnt = counts.cpu().numpy()
-    ps_local = float(cnt[:, 0].sum() + cnt[:, 1].sum())
-    t_max = ms
-    ps_total = ps_local
-    if world > 1:
-        t_max, ps_total = reduce_over_ranks(dist, ms, ps_local, "cuda")
-    value = ps_total / (t_max * 1e-3)
 
-    # roofline of the lepton step (the per-lepton unit whose algorithmic bytes
-    # are 84 B + 61 B per emitted photon): its five phases (streaming pass,
-    # class list, counting pass, scan, writing pass) are timed by CUDA events
-    # recorded on the launching stream between them
-    emitted = c_after["emit_events"] - c_before["emit_events"]
-    deferred = c_after["deferred"] - c_before["deferred"]
-    leptons = float(cnt[:, 0].sum())
-    lep_bytes = (LEPTON_BYTES * leptons + PHOTON_APPEND_BYTES * emitted) / max(nprof, 1)
-    lep_t = lep_ms / max(nprof, 1) * 1e-3
     peak, peak_kind = peaks()
-    achieved = lep_bytes / lep_t / 1e9
-    traffic = None
-    if LEPTON_TRAFFIC_PER_LEPTON is not None:
-        traffic = LEPTON_TRAFFIC_PER_LEPTON * leptons / max(nprof, 1)
-    roofline = {"bound": "hbm",
-                "kernel": "lepton step: k_lepton_stream + k_cls_count/scan/scatter + "
-                          "k_substep_count + k_sub_scan + k_substep_write_coop + k_substep_replay",
-                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": f"{peak_kind} HBM copy (MEASURED_PEAKS.json hbm_gbs)",
-                "traffic": traffic, "bytes_per_launch": lep_bytes, "ms_per_launch": lep_t * 1e3,
-                "lepton_share_of_step": lep_ms / max(ms, 1e-9),
-                "phases_ms_per_step": {k: v / max(nprof, 1) for k, v in phases.items()},
-                "deferred_fraction": deferred / max(leptons, 1.0),
-                "streaming_pass": {
-                    "bytes_per_launch": LEPTON_STREAM_BYTES * leptons / max(nprof, 1),
-                    "achieved_gbs": LEPTON_STREAM_BYTES * leptons / max(nprof, 1)
-                                    / (phases["lepton_stream"] / max(nprof, 1) * 1e-3) / 1e9},
-                "photon_kernel_ms_per_launch": pho_ms / max(nprof, 1)}
+    arm_out = {}
+    for name, r in arms.items():
+        c = r["counters"]
+        t_max, ps_total = r["ms"], float(n * args.steps)
+        if world > 1:
+            t_max, ps_total = reduce_over_ranks(dist, r["ms"], ps_total, "cuda")
+            c = reduce_counters(dist, c, "cuda")
+        status = run_status(c)
+        arm_out[name] = {"value": ps_total / (t_max * 1e-3) if status == "ok" else None,
+                         "status": status, "ms_per_step": t_max / args.steps,
+                         "gpu_launches": r["launches"],
+                         "roofline": lepton_roofline(r, n, args.steps, peak, peak_kind),
+                         "counters": {k: c[k] for k in COUNTER_KEYS + ("status",)},
+                         "photons_per_step": r["photons_last_step"],
+                         "hist_64_log_bins_2_to_1000": c["hist"]}
+    arm_out["mlp"]["train"] = {"samples": int(args.mlp_train_samples), "seconds": train_s,
+                               "final_mse_lndelta": train_loss}
+    arm_out["mlp_over_table_speed"] = arm_out["table"]["ms_per_step"] / arm_out["mlp"]["ms_per_step"]
+    T = arm_out["table"]
+    status = T["status"]
 
-    # e2e: the same steps with the state on the host (pinned), copied in and out
     e2e = None
-    if args.e2e_steps > 0:
-        names_l = ("x", "y", "z", "px", "py", "pz", "w", "id", "ex", "ey", "ez", "bx", "by", "bz")
-        names_g = names_l + ("alive",)
-        api.qed_compact(ctx, g)  # start from live photons only (each e2e step compacts)
-        torch.cuda.synchronize()
-        sizes = {"e": e.count(), "p": p.count(), "g": g.count()}
-        pin = {}
-        grow = int(0.25 * n * args.e2e_steps) + 4096  # appends these steps may add
-        for sp_name, sp, names in (("e", e, names_l), ("p", p, names_l), ("g", g, names_g)):
-            room = min(sp.capacity, sizes[sp_name] + grow)
-            for k in names:
-                t = getattr(sp, k)
-                pin[(sp_name, k)] = torch.empty(room, dtype=t.dtype, pin_memory=True)
-                m = sizes[sp_name]
-                pin[(sp_name, k)][:m].copy_(t[:m])
-        n_host = torch.zeros(3, dtype=torch.int64, pin_memory=True)
-        torch.cuda.synchronize()
-        h2d = d2h = 0
-        ps_e2e = 0
-        w0 = time.perf_counter()
-        for k in range(args.e2e_steps):
-            for sp_name, sp, names in (("e", e, names_l), ("p", p, names_l), ("g", g, names_g)):
-                m = sizes[sp_name]
-                for nm in names:
-                    t = getattr(sp, nm)
-                    t[:m].copy_(pin[(sp_name, nm)][:m], non_blocking=True)
-                    h2d += m * t.element_size()
-                sp.n.fill_(m)
-            ps_e2e += sizes["e"] + sizes["p"] + sizes["g"]
-            api.qed_step_fused(ctx, e, p, g, F, args.warmup + args.steps + k)
-            api.qed_compact(ctx, g)
-            n_host[0].copy_(e.n[0], non_blocking=True)
-            n_host[1].copy_(p.n[0], non_blocking=True)
-            n_host[2].copy_(g.n[0], non_blocking=True)
-            stream.synchronize()
-            d2h += 24
-            sizes = {"e": int(n_host[0]), "p": int(n_host[1]), "g": int(n_host[2])}
-            for nm_, sp_ in (("e", e), ("p", p), ("g", g)):
-                sizes[nm_] = min(sizes[nm_], pin[(nm_, "x")].numel())
-            for sp_name, sp, names in (("e", e, names_l), ("p", p, names_l), ("g", g, names_g)):
-                m = sizes[sp_name]
-                for nm in names:
-                    t = getattr(sp, nm)
-                    pin[(sp_name, nm)][:m].copy_(t[:m], non_blocking=True)
-                    d2h += m * t.element_size()
-            stream.synchronize()
-        wall = time.perf_counter() - w0
-        e2e = {"value": ps_e2e / wall, "unit": UNIT,
-               "h2d_bytes_per_step": h2d // args.e2e_steps, "d2h_bytes_per_step": d2h // args.e2e_steps,
-               "steps": args.e2e_steps,
-               "note": "state on pinned host memory; every step copies all species in, runs "
-                       "qed_step_fused, reads the counts and copies all species back"}
+    if args.e2e_steps > 0 and status == "ok":
+        e2e = e2e_arm(api, torch, ctx_t, H, F, host, args.e2e_steps, 10_000)
+    del host
 
-    sampler = sampler_comparison(api, torch, n, args) if args.sampler_bench else None
-    wts = sampler.pop("_weights", None) if sampler else None
-    batched = None
-    if args.batched_bench:
-        batched = batched_runs_bench(api, torch, wts if wts is not None else api.mlp_init_params(0))
-    status = c_after["status"]
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_desc(n), "roofline": roofline, "e2e": e2e,
-            "gpu_launches": launches, "clocks": clocks, "sampler_table_vs_mlp": sampler,
-            "batched_runs": batched,
-            "event_generators_fig2": generator_rates(api, torch) if args.generator_bench else None,
-            "cascade_fig5": cascade_fig5(api, torch) if args.cascade_bench else None,
-            "spectra_fig1": spectra_fig1(api, torch) if args.spectra_bench else None,
-            "counters": {"emit_events": emitted,
-                         "pair_events": c_after["pair_events"] - c_before["pair_events"],
-                         "substeps": c_after["substeps"] - c_before["substeps"],
-                         "dropped": c_after["dropped"], "domain": c_after["domain"],
-                         "deferred": deferred,
-                         "status": status,
-                         "particles_at_end": {"leptons": int(cnt[-1, 0]), "photons": int(cnt[-1, 1])}}}
+    extra = {}
+    if rank == 0:
+        try:
+            extra["spectral_error_mlp"] = spectral_error(api, torch, ctx_m, ctx_t)
+        except Exception as ex:  # report, do not hide the headline
+            extra["spectral_error_mlp"] = {"error": repr(ex)}
+        if args.sampler_bench:
+            extra["sampler_table_vs_mlp"] = sampler_comparison(api, torch, n, ctx_t, ctx_m)
+    del H
+    torch.cuda.empty_cache()
+    if rank == 0:
+        if args.batched_bench:
+            extra["batched_runs"] = batched_runs_bench(api, torch, wts)
+        if args.configs_bench:
+            extra["config_single_particle_fp64"] = config_single_particle(api, torch)
+            extra["config_uniform_field_ensemble"] = config_uniform_ensemble(api, torch)
+            extra["config_3d_cascade"] = config_3d_cascade(api, torch)
+        if args.generator_bench:
+            extra["event_generators_fig2"] = generator_rates(api, torch)
+        if args.cascade_bench:
+            extra["cascade_fig5"] = cascade_fig5(api, torch)
+        if args.spectra_bench:
+            extra["spectra_fig1"] = spectra_fig1(api, torch)
+
+    line = {"metric": METRIC, "value": T["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": T["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "status": status, "config": workload_desc(n),
+            "roofline": T["roofline"], "e2e": e2e, "gpu_launches": T["gpu_launches"],
+            "clocks": clocks, "arms": arm_out}
+    line.update(extra)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

@@ -192,7 +192,11 @@ int qed_pair(qed_ctx *ctx, const qed_species *photons, const qed_species *electr
              const qed_species *positrons, const qed_fields *f, int64_t step,
              qed_stream_t stream);
 
-/* Stable in-place removal of dead particles (alive == 0). */
+/* Stable in-place removal of dead particles (alive == 0).  If a look-back
+ * wait runs out (QED_STATUS_TIMEOUT), the tile that gave up writes nothing
+ * and the count is left unchanged when it is the last tile: the species is
+ * then not compacted (particles may be duplicated or stale) and must not be
+ * used as the result. */
 int qed_compact(qed_ctx *ctx, const qed_species *s, qed_stream_t stream);
 
 /* Removal of dead particles that moves only as many particles as died.  With
@@ -229,11 +233,25 @@ int qed_sample_xi(qed_ctx *ctx, const float *chi, const float *gamma, float *xi,
 int qed_rates(qed_ctx *ctx, int which, const double *chi, const double *gamma, double *W,
               int64_t n, qed_stream_t stream);
 
-/* Inverse CDF from the tables, for parity checks.  which = 0: photon xi at
- * (chi, gamma) for the uniform word w (u = (w + 1/2) 2^-32); which = 1: pair
- * xi at chi.  Device arrays; evaluated in the context's precision. */
+/* Inverse CDF at given inputs, for parity checks and the spectral error of
+ * the learned sampler (Eq. 7).  which = 0: photon xi at (chi, gamma) for the
+ * uniform word w (u = (w + 1/2) 2^-32) from the inverse table; which = 1: pair
+ * xi at chi (Eq. 6; gamma unused, may be NULL); which = 2: photon xi as the
+ * learned sampler gives it -- the network where (ln chi, kappa) is in its
+ * domain, else the table -- in a QED_FP32 context whose weights are loaded
+ * (QED_ERR_ARG before qed_mlp_load, QED_ERR_UNSUPPORTED in QED_FP64).  Device
+ * arrays (double chi, gamma, xi; uint32 words); evaluated in the context's
+ * precision. */
 int qed_sample_table(qed_ctx *ctx, int which, const double *chi, const double *gamma,
                      const uint32_t *word, double *xi, int64_t n, qed_stream_t stream);
+
+/* chi of every particle of s from its momentum and per-particle fields, for
+ * parity checks: Eq. (2) (chi_e) when s->q != 0, Eq. (3) (chi_ph) when
+ * s->q == 0, by the functions the step kernels use, in the context's precision
+ * (QED_FP32: FP32, with the vector sum redone in FP64 where it cancels by more
+ * than 2^7).  Needs px, py, pz and ex..bz; the count is read from s->d_n on the
+ * device.  chi: device double[count]. */
+int qed_chi(qed_ctx *ctx, const qed_species *s, double *chi, qed_stream_t stream);
 
 /* Analytic standing wave (two counter-propagating circularly polarised waves
  * of amplitude a0 each) sampled at the nodes of a grid as qed_fields.GRID. */
@@ -346,8 +364,10 @@ int qed_profile_end_phases(qed_ctx *ctx, double *ms, int64_t *steps);
  *             by precision, QED_FP32 -> float, QED_FP64 -> double; the six
  *             field arrays are moved when all six are non-NULL)
  *   d_status  optional caller-owned device uint32 OR-ed with QED_STATUS_* bits
- * Returns QED_ERR_CAPACITY if s->capacity exceeds 16,777,216 particles.  Calls
- * no allocating routine.  Every call shares the static array: calls that
+ * Returns QED_ERR_CAPACITY if s->capacity exceeds 16,777,216 particles; a count
+ * *s->d_n above s->capacity is clamped to the capacity on the device and
+ * reported as QED_STATUS_CAPACITY in *d_status.  After QED_STATUS_TIMEOUT the
+ * species is not compacted (as for qed_compact).  Calls no allocating routine.  Every call shares the static array: calls that
  * overlap on the GPU race, so issue them to one stream or order them.  The
  * first call on a device performs a one-time set-up (cudaGetSymbolAddress of
  * the array with that device current); make it before any stream capture. */

@@ -126,6 +126,8 @@ def lib():
             "orc_philox_v": (None, [P(C.c_uint32), P(C.c_uint32), P(C.c_uint32), i64]),
             "orc_step": (None, [P(Config), P(Fields), P(_Species), P(_Species), P(_Species), i64,
                                 P(Counters), P(Counters)]),
+            "orc_emit_pass": (None, [P(Config), P(Fields), P(_Species), P(_Species), i64,
+                                     P(Counters)]),
             "orc_compact": (i64, [P(_Species)]),
             "orc_num_threads": (C.c_int, []),
             "orc_set_num_threads": (None, [C.c_int]),
@@ -392,6 +394,17 @@ def step(cfg: Config, fields: Fields, electrons: Species | None, positrons: Spec
         if sp is not None:
             sp.n = s.n
     return lc, pc
+
+
+def emit(cfg: Config, fields: Fields, leptons: Species, photons: Species, step_index: int):
+    """Photon emission of every lepton at its current momentum and fields, no
+    push (the counterpart of the library's qed_emit).  Returns the counters."""
+    sl, sg = leptons._struct(), photons._struct()
+    c = Counters()
+    lib().orc_emit_pass(C.byref(cfg), C.byref(fields), C.byref(sl), C.byref(sg), int(step_index),
+                        C.byref(c))
+    leptons.n, photons.n = sl.n, sg.n
+    return c
 
 
 def compact(sp: Species) -> int:

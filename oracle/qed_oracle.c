@@ -643,14 +643,19 @@ static void emit_photon(const orc_config *cfg, const orc_species *s, int64_t i, 
  *   with a fresh r3 (word 2 of the same draw).  No sub-steps: at most one
  *   photon per step.  1 - exp(-P) is evaluated as -expm1(-P). */
 static void lepton_one(const orc_config *cfg, const orc_fields *f, orc_species *s, int64_t i,
-                       int64_t step, orc_childlist *out, int64_t *substeps) {
+                       int64_t step, orc_childlist *out, int64_t *substeps, int push) {
   double E[3], B[3];
   get_fields(f, s, i, E, B);
   double p[3] = {s->px[i], s->py[i], s->pz[i]};
-  double g = orc_boris(p, E, B, s->q, cfg->dt);
-  s->x[i] += p[0] / g * cfg->dt;
-  s->y[i] += p[1] / g * cfg->dt;
-  s->z[i] += p[2] / g * cfg->dt;
+  double g;
+  if (push) {
+    g = orc_boris(p, E, B, s->q, cfg->dt);
+    s->x[i] += p[0] / g * cfg->dt;
+    s->y[i] += p[1] / g * cfg->dt;
+    s->z[i] += p[2] / g * cfg->dt;
+  } else { /* emission only, at the current momentum (the library's qed_emit) */
+    g = sqrt(1.0 + p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+  }
 
   double chi = orc_chi_lepton(p, E, B, cfg->a_S);
   double W = orc_rate_photon(cfg, chi, g);
@@ -766,12 +771,12 @@ static void append_children(orc_species *s, const orc_childlist *l, int64_t *dro
  * (in parallel when OpenMP is on -- each particle depends only on its own
  * state); photons are then appended sequentially in particle order, and in
  * sub-step order within a particle. */
-void orc_lepton_pass(const orc_config *cfg, const orc_fields *f, orc_species *s, int64_t n0,
-                     orc_species *photons, int64_t step, orc_counters *cnt) {
+static void lepton_pass(const orc_config *cfg, const orc_fields *f, orc_species *s, int64_t n0,
+                        orc_species *photons, int64_t step, orc_counters *cnt, int push) {
   orc_childlist *lists = (orc_childlist *)calloc((size_t)(n0 > 0 ? n0 : 1), sizeof(orc_childlist));
   int64_t subs = 0;
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : subs)
-  for (int64_t i = 0; i < n0; ++i) lepton_one(cfg, f, s, i, step, &lists[i], &subs);
+  for (int64_t i = 0; i < n0; ++i) lepton_one(cfg, f, s, i, step, &lists[i], &subs, push);
   cnt->substeps += subs;
   for (int64_t i = 0; i < n0; ++i) {
     for (int j = 0; j < lists[i].n; ++j) {
@@ -785,6 +790,18 @@ void orc_lepton_pass(const orc_config *cfg, const orc_fields *f, orc_species *s,
     free(lists[i].c);
   }
   free(lists);
+}
+
+void orc_lepton_pass(const orc_config *cfg, const orc_fields *f, orc_species *s, int64_t n0,
+                     orc_species *photons, int64_t step, orc_counters *cnt) {
+  lepton_pass(cfg, f, s, n0, photons, step, cnt, 1);
+}
+
+/* Photon emission of every lepton of s at its current momentum and fields,
+ * with no push (the same generator, order and appends as the lepton pass). */
+void orc_emit_pass(const orc_config *cfg, const orc_fields *f, orc_species *s,
+                   orc_species *photons, int64_t step, orc_counters *cnt) {
+  lepton_pass(cfg, f, s, s->n, photons, step, cnt, 0);
 }
 
 /* Photon pass over the first n0 photons; pairs appended in photon order. */

@@ -92,6 +92,7 @@ SIGNATURES = {
     "qed_sample_xi": (C.c_int, [_P, _P, _P, _P, C.c_int64, C.c_int64, _P]),
     "qed_rates": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_int64, _P]),
     "qed_sample_table": (C.c_int, [_P, C.c_int, _P, _P, _P, _P, C.c_int64, _P]),
+    "qed_chi": (C.c_int, [_P, C.POINTER(qed_species), _P, _P]),
     "qed_fill_standing_wave": (C.c_int, [_P, _P, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                          C.c_double, C.c_double, _P]),
     "qed_table_get": (C.c_int, [_P, C.c_int, _P, C.c_size_t, C.POINTER(C.c_double)]),

@@ -275,6 +275,15 @@ def qed_sample_table(ctx: Context, which: int, chi: torch.Tensor, gamma: torch.T
     return out
 
 
+def qed_chi(ctx: Context, s: Species, stream=None) -> torch.Tensor:
+    """chi_e (leptons) or chi_ph (photons, q = 0) of every particle of s, from
+    its momentum and per-particle fields (device float64 tensor)."""
+    out = torch.zeros(max(s.capacity, 1), dtype=torch.float64, device=s.x.device)
+    B.check(B.lib().qed_chi(ctx.handle, C.byref(s.struct()), out.data_ptr(), _stream(stream)),
+            "qed_chi")
+    return out[:s.count()]
+
+
 def qed_fill_standing_wave(ctx: Context, grid: torch.Tensor, x0: float, dx: float, a0: float,
                            t: float, stream=None) -> None:
     nz, ny, nx = grid.shape[:3]

@@ -23,6 +23,10 @@ cudaError_t launch_eval(qed_ctx *, int, int, const double *, const double *, con
 cudaError_t launch_snapshot(qed_ctx *, const int64_t *, int64_t *, cudaStream_t);
 cudaError_t launch_sample_xi(qed_ctx *, const float *, const float *, float *, int64_t, int64_t,
                              cudaStream_t);
+cudaError_t launch_eval_xi_mlp(qed_ctx *, const double *, const double *, const uint32_t *, double *,
+                               int64_t, cudaStream_t);
+template <class Real>
+cudaError_t launch_eval_chi(qed_ctx *, const qed_species *, double *, cudaStream_t);
 cudaError_t launch_fill(qed_ctx *, float *, int, int, int, double, double, double, double,
                         cudaStream_t);
 enum { MODE_PUSH_ = 0, MODE_EMIT_ = 1, MODE_FUSED_ = 2 };
@@ -421,14 +425,29 @@ extern "C" int qed_rates(qed_ctx *c, int which, const double *chi, const double 
 
 extern "C" int qed_sample_table(qed_ctx *c, int which, const double *chi, const double *gamma,
                                 const uint32_t *word, double *xi, int64_t n, qed_stream_t stream) {
-  if (!c || (which != 0 && which != 1) || n < 0 ||
-      (n > 0 && (!chi || !word || !xi || (which == 0 && !gamma))))
+  if (!c || which < 0 || which > 2 || n < 0 ||
+      (n > 0 && (!chi || !word || !xi || (which != 1 && !gamma))))
     return QED_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
+  if (which == 2) {  // the learned sampler (FP32 contexts with loaded weights)
+    if (c->cfg.precision != QED_FP32) return QED_ERR_UNSUPPORTED;
+    if (!c->mlp_ready) return QED_ERR_ARG;
+    return cuda_fail(launch_eval_xi_mlp(c, chi, gamma, word, xi, n, st), "qed_sample_table");
+  }
   cudaError_t e = c->cfg.precision == QED_FP64
                       ? launch_eval<double>(c, 1, which, chi, gamma, word, xi, n, st)
                       : launch_eval<float>(c, 1, which, chi, gamma, word, xi, n, st);
   return cuda_fail(e, "qed_sample_table");
+}
+
+extern "C" int qed_chi(qed_ctx *c, const qed_species *s, double *chi, qed_stream_t stream) {
+  if (!c || !s || !chi || !s->d_n || !s->px || !s->py || !s->pz || !s->ex || !s->ey || !s->ez ||
+      !s->bx || !s->by || !s->bz)
+    return QED_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = c->cfg.precision == QED_FP64 ? launch_eval_chi<double>(c, s, chi, st)
+                                               : launch_eval_chi<float>(c, s, chi, st);
+  return cuda_fail(e, "qed_chi");
 }
 
 extern "C" int qed_fill_standing_wave(qed_ctx *c, float *grid, int nx, int ny, int nz, double x0,

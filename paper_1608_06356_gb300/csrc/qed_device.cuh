@@ -206,16 +206,27 @@ struct Tally {
 // ---------------------------------------------------------------------------
 template <class Real> struct V3 { Real x, y, z; };
 
+// FP64 chi_e a_S = sqrt(E_par^2 + |gamma E_perp + p x B|^2) with the vector sum
+// written as E_perp / (gamma + |p|) + |p| (E_perp + n x B), using
+// gamma - |p| = 1 / (gamma + |p|): for a lepton co-moving with a plane wave
+// the two large terms gamma E_perp and p x B cancel to O(1/gamma), and this
+// form keeps that difference to full relative precision instead of losing
+// ~2 gamma^2 units of rounding.  What remains, E_perp + n x B, cancels only
+// where the field itself is a plane wave along n.
 __device__ __forceinline__ double chi_lepton_d(double px, double py, double pz, double ex,
                                                double ey, double ez, double bx, double by,
                                                double bz, double inv_aS) {
-  double g = sqrt(1.0 + px * px + py * py + pz * pz);
-  double fx = g * ex + (py * bz - pz * by);
-  double fy = g * ey + (pz * bx - px * bz);
-  double fz = g * ez + (px * by - py * bx);
-  double pe = px * ex + py * ey + pz * ez;
-  double s = fx * fx + fy * fy + fz * fz - pe * pe;
-  return s > 0.0 ? sqrt(s) * inv_aS : 0.0;
+  const double p2 = px * px + py * py + pz * pz;
+  if (!(p2 > 0.0)) return sqrt(ex * ex + ey * ey + ez * ez) * inv_aS;
+  const double pm = sqrt(p2), g = sqrt(1.0 + p2), ip = 1.0 / pm;
+  const double nx = px * ip, ny = py * ip, nz = pz * ip;
+  const double epar = nx * ex + ny * ey + nz * ez;
+  const double ax = ex - epar * nx, ay = ey - epar * ny, az = ez - epar * nz;
+  const double fx = ax + (ny * bz - nz * by), fy = ay + (nz * bx - nx * bz),
+               fz = az + (nx * by - ny * bx);
+  const double ig = 1.0 / (g + pm);
+  const double dx = ax * ig + pm * fx, dy = ay * ig + pm * fy, dz = az * ig + pm * fz;
+  return sqrt(epar * epar + dx * dx + dy * dy + dz * dz) * inv_aS;
 }
 
 template <class Real>
@@ -236,15 +247,7 @@ __device__ __forceinline__ Real chi_lepton(Real px, Real py, Real pz, Real g, Re
   Real scale = g * (fabsf(eqx) + fabsf(eqy) + fabsf(eqz)) + fabsf(cx) + fabsf(cy) + fabsf(cz);
   if (d2 * (Real)16384 < scale * scale) {
     // cancellation: |d| < scale/128; redo the vector sum in FP64
-    double g64 = sqrt(1.0 + (double)px * px + (double)py * py + (double)pz * pz);
-    double p64 = sqrt((double)px * px + (double)py * py + (double)pz * pz);
-    double nx6 = px / p64, ny6 = py / p64, nz6 = pz / p64;
-    double ep = nx6 * ex + ny6 * ey + nz6 * ez;
-    double ax = (double)ex - ep * nx6, ay = (double)ey - ep * ny6, az = (double)ez - ep * nz6;
-    double qx = g64 * ax + ((double)py * bz - (double)pz * by);
-    double qy = g64 * ay + ((double)pz * bx - (double)px * bz);
-    double qz = g64 * az + ((double)px * by - (double)py * bx);
-    return (Real)(sqrt(ep * ep + qx * qx + qy * qy + qz * qz) * (double)inv_aS);
+    return (Real)chi_lepton_d(px, py, pz, ex, ey, ez, bx, by, bz, (double)inv_aS);
   }
   return m_sqrt(epar * epar + d2) * inv_aS;
 }

@@ -21,7 +21,9 @@
 //     cleared (cudaMemsetAsync on the stream) before every launch;
 //   * calls that overlap on the GPU (on different streams without ordering,
 //     or from different threads at once) race on the array: issue them to one
-//     stream or order them.
+//     stream or order them;
+//   * a count *d_n above the capacity is clamped to the capacity (and
+//     QED_STATUS_CAPACITY is reported), so no tile reaches past the array.
 // The first call on a device looks up the array's device address with
 // cudaGetSymbolAddress (once per device, with that device current); make that
 // first call before any stream capture.
@@ -84,6 +86,7 @@ template <class Real> struct NoallocCompactArgs {
   uint8_t *alive;
   uint32_t *tag;       // optional
   int64_t *d_n;
+  int64_t capacity;    // the species' capacity (<= NOALLOC_MAX_PARTICLES)
   uint32_t *d_status;  // caller-owned, may be null
   ScanState scan;
 };
@@ -95,23 +98,26 @@ template <class Real> struct NoallocCompactArgs {
 template <class Real>
 __global__ void __launch_bounds__(TILE) k_compact_noalloc(NoallocCompactArgs<Real> A) {
   __shared__ uint32_t scan_sm[33];
-  __shared__ long long s_meta[4];
+  __shared__ long long s_meta[5];
   if (threadIdx.x == 0) {
     s_meta[2] = *(volatile int64_t *)A.d_n;
     s_meta[3] = (long long)A.scan.sync[2];
   }
   __syncthreads();
-  const int64_t n = s_meta[2];
+  // a count above the capacity (a caller's error) is clamped to it, so the
+  // tiles stay inside the static scan state and the caller's arrays
+  const int64_t n_in = s_meta[2];
+  const int64_t n = n_in < 0 ? 0 : (n_in > A.capacity ? A.capacity : n_in);
   const uint32_t epoch = (uint32_t)s_meta[3];
   const int64_t ntiles = (n + TILE - 1) / TILE;
   const bool fields = A.v[7] != nullptr;
-  uint32_t status = 0;
+  uint32_t status = n != n_in ? (uint32_t)QED_STATUS_CAPACITY : 0u;
   for (;;) {
     if (threadIdx.x == 0) s_meta[0] = (long long)atomicAdd(&A.scan.sync[0], 1u);
     __syncthreads();
     const int64_t t = s_meta[0];
     __syncthreads();
-    if (t >= ntiles) break;
+    if (t >= ntiles || t >= A.scan.max_tiles) break;
     const int64_t i = t * TILE + threadIdx.x;
     uint32_t keep = 0;
     Real r[13];
@@ -131,14 +137,21 @@ __global__ void __launch_bounds__(TILE) k_compact_noalloc(NoallocCompactArgs<Rea
     uint32_t excl = block_excl_scan(keep, scan_sm);
     uint32_t agg = scan_sm[32];
     if (threadIdx.x < 32) {
-      uint32_t pre = lookback_warp(A.scan, t, epoch, agg, status);
+      uint32_t st_tile = 0;
+      uint32_t pre = lookback_warp(A.scan, t, epoch, agg, st_tile);
+      // any lane of the walk may have given up (warp 0 runs converged here)
+      const bool gave_up = __any_sync(0xFFFFFFFFu, (st_tile & QED_STATUS_TIMEOUT) != 0);
+      status |= st_tile;
       if (threadIdx.x == 0) {
         s_meta[1] = pre;
-        if (t == ntiles - 1) *A.d_n = (int64_t)pre + agg;
+        // no valid prefix after a look-back that gave up: write nothing (see
+        // the context-based compaction); the status word reports it
+        s_meta[4] = gave_up ? 1 : 0;
+        if (t == ntiles - 1 && !s_meta[4]) *A.d_n = (int64_t)pre + agg;
       }
     }
     __syncthreads();
-    if (keep) {
+    if (keep && !s_meta[4]) {
       const int64_t d = s_meta[1] + excl;
 #pragma unroll
       for (int c = 0; c < 7; ++c) A.v[c][d] = r[c];
@@ -186,6 +199,7 @@ int launch_noalloc(const qed_species *s, uint32_t *d_status, cudaStream_t st) {
   a.alive = s->alive;
   a.tag = s->tag;
   a.d_n = s->d_n;
+  a.capacity = s->capacity;
   a.d_status = d_status;
   a.scan = ScanState{scratch, sync, NOALLOC_MAX_TILES};
   int per_sm = 0;

@@ -1769,16 +1769,25 @@ __global__ void __launch_bounds__(COMPACT_TILE) k_compact(CompactArgs<Real> A) {
       agg += scan_sm[32];
     }
     if (threadIdx.x < 32) {
-      uint32_t pre = lookback_warp(A.o.scan, t, epoch, agg, status);
+      uint32_t st_tile = 0;
+      uint32_t pre = lookback_warp(A.o.scan, t, epoch, agg, st_tile);
+      // any lane of the walk may have given up (warp 0 runs converged here)
+      const bool gave_up = __any_sync(0xFFFFFFFFu, (st_tile & QED_STATUS_TIMEOUT) != 0);
+      status |= st_tile;
       if (threadIdx.x == 0) {
         s_meta[1] = pre;
-        if (t == ntiles - 1) *A.s.d_n = (int64_t)pre + agg;
+        // a look-back that gave up has no valid prefix: this tile writes
+        // nothing (an in-place write could land on particles an earlier tile
+        // has not read yet); the result is flagged QED_STATUS_TIMEOUT
+        s_meta[3] = gave_up ? 1 : 0;
+        if (t == ntiles - 1 && !s_meta[3]) *A.s.d_n = (int64_t)pre + agg;
       }
     }
     __syncthreads();
+    const bool skip = s_meta[3] != 0;
 #pragma unroll
     for (int k = 0; k < CI; ++k) {
-      if (!keep[k]) continue;
+      if (!keep[k] || skip) continue;
       const int64_t d = s_meta[1] + excl[k];
       A.s.x[d] = v[k][0]; A.s.y[d] = v[k][1]; A.s.z[d] = v[k][2];
       A.s.px[d] = v[k][3]; A.s.py[d] = v[k][4]; A.s.pz[d] = v[k][5]; A.s.w[d] = v[k][6];
@@ -2088,6 +2097,61 @@ template <class Real> __global__ void k_eval_xi(EvalArgs<Real> A) {
     if (!(chi >= sel<Real>(A.C.chi_pair_min, A.C.f_chi_pair_min))) l = A.T.glp.lo;
     XiOut<Real> xo = pair_xi(A.T.Yp, A.T, l, unif<Real>(w), unif<Real>(~w));
     A.out[i] = (double)xo.xi;
+  }
+}
+
+// chi of every particle of a species from its momentum and per-particle
+// fields (Eq. 2 for leptons, Eq. 3 for photons), in the context's precision,
+// by the same functions the step kernels use (parity hook).
+template <class Real> __global__ void k_eval_chi(Sp<Real> S, Real inv_aS, double *out) {
+  const int64_t n = *(volatile const int64_t *)S.d_n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const Real px = S.px[i], py = S.py[i], pz = S.pz[i];
+    Real chi;
+    if (S.q == (Real)0) {
+      chi = chi_photon(px, py, pz, S.ex[i], S.ey[i], S.ez[i], S.bx[i], S.by[i], S.bz[i], inv_aS);
+    } else {
+      const Real g = m_sqrt((Real)1 + px * px + py * py + pz * pz);
+      chi = chi_lepton(px, py, pz, g, S.ex[i], S.ey[i], S.ez[i], S.bx[i], S.by[i], S.bz[i], inv_aS);
+    }
+    out[i] = (double)chi;
+  }
+}
+
+// Learned inverse CDF at given inputs (parity and spectral-error hook): xi
+// of the photon sampler at (chi, gamma) for the uniform word w, through the
+// network where (ln chi, kappa) lies in its domain, else through the inverse
+// table -- exactly the choice the step kernels make.  Warp-uniform loop (the
+// network is a warp-collective call); rates from the global-memory tables.
+__global__ void __launch_bounds__(TILE) k_eval_xi_mlp(EvalArgs<float> A, const uint32_t *frag,
+                                                      const float *w) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint32_t *s_frag = reinterpret_cast<uint32_t *>(smem_raw);
+  float *s_fw = reinterpret_cast<float *>(s_frag + MLP_FRAG_WORDS);
+  mlp_stage(s_frag, s_fw, frag, w);
+  __syncthreads();
+  Tally tl;
+  tl.clear();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t ib = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); ib < A.n; ib += stride) {
+    const int64_t i = ib + (threadIdx.x & 31);
+    const bool active = i < A.n;
+    const float chi = active ? (float)A.chi[i] : 1.f, g = active ? (float)A.gamma[i] : 1e3f;
+    const uint32_t wd = active ? A.word[i] : 0u;
+    RateOut<float> ro = photon_rate(A.T.R, A.T.F, A.T, A.C, chi, g, tl);
+    const float kap = photon_kappa(ro.kmin, unif<float>(wd), unif<float>(~wd));
+    const float lchi = logf(chi);
+    const bool in_mlp = lchi >= MLP_L_LO && lchi <= MLP_L_HI && kap >= MLP_K_LO && kap <= MLP_K_HI;
+    float Y = mlp_infer_warp(s_frag, s_fw, (lchi - MLP_LC) / MLP_LS, (kap - MLP_KC) / MLP_KS) +
+              mlp_baseline(kap);
+    if (!active) continue;
+    double xi = 0.0;
+    if (ro.W > 0.f) {
+      if (!in_mlp) Y = photon_lndelta_table(A.T.Y, A.T, ro.l, kap, tl);
+      xi = (double)xi_from_lndelta(chi, Y).xi;
+    }
+    A.out[i] = xi;
   }
 }
 
@@ -2531,6 +2595,34 @@ cudaError_t launch_eval(qed_ctx *c, int kind, int which, const double *chi, cons
   if (blocks == 0) return cudaSuccess;
   if (kind == 0) k_eval_rates<Real><<<blocks, 256, 0, st>>>(a);
   else k_eval_xi<Real><<<blocks, 256, 0, st>>>(a);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+template <class Real> cudaError_t launch_eval_chi(qed_ctx *c, const qed_species *s, double *out,
+                                                   cudaStream_t st) {
+  const Consts C = consts_of(c);
+  k_eval_chi<Real><<<c->num_sms * 4, 256, 0, st>>>(to_sp<Real>(s), sizeof(Real) == 8 ? (Real)C.inv_aS : (Real)C.f_inv_aS,
+                                                   out);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+template cudaError_t launch_eval_chi<float>(qed_ctx *, const qed_species *, double *, cudaStream_t);
+template cudaError_t launch_eval_chi<double>(qed_ctx *, const qed_species *, double *, cudaStream_t);
+
+cudaError_t launch_eval_xi_mlp(qed_ctx *c, const double *chi, const double *gamma,
+                               const uint32_t *word, double *out, int64_t n, cudaStream_t st) {
+  EvalArgs<float> a{};
+  a.which = 0; a.chi = chi; a.gamma = gamma; a.word = word; a.out = out; a.n = n;
+  a.C = consts_of(c);
+  a.T = tables_of<float>(c);
+  if (n == 0) return cudaSuccess;
+  const size_t sm = MLP_SMEM_BYTES;
+  cudaError_t e = cudaFuncSetAttribute(k_eval_xi_mlp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int64_t blocks = (n + TILE - 1) / TILE;
+  if (blocks > (int64_t)c->num_sms * 8) blocks = (int64_t)c->num_sms * 8;
+  k_eval_xi_mlp<<<(unsigned)blocks, TILE, sm, st>>>(a, c->mlp_frag, c->mlp_w);
   c->launches += 1;
   return cudaGetLastError();
 }

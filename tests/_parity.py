@@ -13,10 +13,10 @@ import math
 import numpy as np
 
 
-def first_substep_threshold(orc, cfg, states, fields_fn, q, photon=False, rtol=1e-4):
-    """Per particle: W*Dt_s of its first sub-step (after the oracle's push),
-    and whether the sub-step count N = ceil(W Dt / wdt_max) is within the rate
-    tolerance of changing."""
+def first_substep_threshold(orc, cfg, states, fields_fn, q, photon=False, rtol=1e-4, push=True):
+    """Per particle: W*Dt_s of its first sub-step (after the oracle's push,
+    unless push=False), and whether the sub-step count N = ceil(W Dt /
+    wdt_max) is within the rate tolerance of changing."""
     n = len(states["x"])
     chis, gammas = np.zeros(n), np.zeros(n)
     for i in range(n):
@@ -26,7 +26,10 @@ def first_substep_threshold(orc, cfg, states, fields_fn, q, photon=False, rtol=1
             g = float(np.linalg.norm(p))
             chi = orc.chi_photon(p, E, B, cfg.a_S)
         else:
-            p, g = orc.boris(p, E, B, q, cfg.dt)
+            if push:
+                p, g = orc.boris(p, E, B, q, cfg.dt)
+            else:
+                g = float(np.sqrt(1.0 + p @ p))
             chi = orc.chi_lepton(p, E, B, cfg.a_S)
         chis[i], gammas[i] = chi, g
     W = (orc.rate_pair if photon else orc.rate_photon)(cfg, chis, gammas)
@@ -42,9 +45,9 @@ def first_substep_threshold(orc, cfg, states, fields_fn, q, photon=False, rtol=1
     return amb, thr
 
 
-def ambiguous(orc, cfg, states, fields_fn, q, step, photon=False, rtol=1e-4, atol=1e-7):
+def ambiguous(orc, cfg, states, fields_fn, q, step, photon=False, rtol=1e-4, atol=1e-7, push=True):
     """Indices whose first-sub-step Method I decision is within tolerance."""
-    amb, thr = first_substep_threshold(orc, cfg, states, fields_fn, q, photon, rtol)
+    amb, thr = first_substep_threshold(orc, cfg, states, fields_fn, q, photon, rtol, push)
     n = len(states["x"])
     ids = np.asarray(states["id"], dtype=np.uint64)
     ctr = np.zeros((n, 4), dtype=np.uint32)

@@ -289,6 +289,29 @@ def test_step_energy_conservation_per_emission(orc):
     assert np.all(eph >= 2.0 - 1e-9)  # xi >= xi_min = 2/gamma
 
 
+def test_step_histogram_matches_numpy_binning(orc):
+    # The oracle's 64-bin photon spectrum (the single-particle-type test's
+    # output: photon energies in 64 log bins over [spec_lo, spec_hi)) against
+    # numpy's binning of the photons the same step appended.
+    cfg = orc.make_config(dt=0.2, seed=31, spec_lo=2.0, spec_hi=1000.0)
+    n = 1500
+    e = _electrons(orc, n, 1000.0)
+    g = orc.Species(8 * n, 0.0, with_alive=True)
+    lc, _ = orc.step(cfg, orc.uniform_fields([0, 0, 0], [410.0, 0, 0]), e, orc.Species(1, 1.0), g, 0)
+    eph = np.sqrt(g.view("px") ** 2 + g.view("py") ** 2 + g.view("pz") ** 2)
+    assert lc.events == g.n > 300
+    edges = 2.0 * (1000.0 / 2.0) ** (np.arange(65) / 64.0)
+    # numpy closes the last bin on the right; the oracle's range is half-open
+    inside = eph < 1000.0
+    ref = np.histogram(eph[inside], bins=edges)[0]
+    # an energy within rounding of an edge may fall on either side
+    near = np.abs(np.log(eph[:, None] / edges[None, :])).min(axis=1) < 1e-12
+    assert np.abs(np.asarray(lc.hist) - ref).sum() <= 2 * int(near.sum())
+    assert sum(lc.hist) == int((eph >= 2.0).sum() - (~inside).sum())
+    # and a planted mistake (bins shifted by one) is seen
+    assert np.abs(np.roll(np.asarray(lc.hist), 1) - ref).sum() > 10
+
+
 def test_pair_energy_conservation(orc):
     cfg = orc.make_config(dt=0.05, seed=9)
     n = 200
