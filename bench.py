@@ -51,6 +51,9 @@ PHOTON_APPEND_BYTES = 61  # x,y,z,px,py,pz,w (28) + id (8) + alive (1) + inherit
 # W_rad Dt over the ensemble is 0.184 (an upper bound of the mean event count);
 # the photon buffer holds 1.6x that
 PHOTONS_PER_ELECTRON_CAP = 0.3
+# the lepton step runs in a single pass, appending photons in no particular
+# order (the same photons as the ordered multi-pass path, bit for bit)
+APPEND_ORDER = 1
 QED_STATUS_CAPACITY = 1
 QED_STATUS_ERRORS = 1 | 4 | 8 | 32  # capacity, non-finite, timeout, replay
 
@@ -62,6 +65,8 @@ def workload_desc(n):
                         "stage empty) per step; every step starts from the same ensemble (positions "
                         "and momenta restored from a device copy, photon buffer emptied, both timed)",
             "particles_per_step": n, "dt": DT, "precision": "fp32 state, fp64 chi where it cancels",
+            "append_order": "any (single-pass lepton kernel; photons as a set identical to the "
+                            "ordered path's)" if APPEND_ORDER else "ordered",
             "samplers": ["table", "mlp"], "value_arm": "table",
             "l2": "inputs larger than L2 (>= 5.6 GB read and written per step)"}
 
@@ -272,8 +277,9 @@ def lepton_roofline(r, n, steps, peak, peak_kind):
     achieved = lep_bytes / (lep_ms * 1e-3) / 1e9
     stream_ms = phases["lepton_stream"] / nprof
     return {"bound": "hbm",
-            "kernel": "lepton step: k_lepton_stream + k_cls_count/scan/scatter + k_substep_count + "
-                      "k_sub_scan + k_substep_write_coop + k_substep_replay",
+            "kernel": ("lepton step: k_lepton_onepass" if APPEND_ORDER else
+                       "lepton step: k_lepton_stream + k_cls_count/scan/scatter + k_substep_count + "
+                       "k_sub_scan + k_substep_write_coop + k_substep_replay"),
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_source": f"{peak_kind} HBM copy (MEASURED_PEAKS.json hbm_gbs)",
             "traffic": None,
@@ -433,7 +439,9 @@ def batched_runs_bench(api, torch, mlp_weights, steps=4):
             cnt = torch.zeros((steps, 3), dtype=torch.int64, device="cuda")
             if mode == "graph":  # capture (first call), then time a replay from the same state
                 api.qed_run_batched(ctx, e, p, g, F, 0, steps)
-            else:  # load kernels once, then restore the state
+            else:  # load kernels (ours and torch's) once, then restore the state
+                cnt[0, 0].copy_(e.n[0] + p.n[0])
+                cnt[0, 1].copy_(g.n[0])
                 api.qed_step_fused(ctx, e, p, g, F, 0)
                 api.qed_compact_fill(ctx, g)
             torch.cuda.synchronize()
@@ -705,8 +713,8 @@ def config_uniform_ensemble(api, torch, n=1 << 20, steps=200, compact_every=4, c
             "cpu_baseline": base}
 
 
-def config_3d_cascade(api, torch, steps=40, seed_n=1 << 24, cap=1 << 28, nx=256, a0=800.0,
-                      dt=0.1, compact_every=4, cpu_n=4096):
+def config_3d_cascade(api, torch, steps=28, seed_n=1 << 24, cap=1 << 28, nx=256, a0=800.0,
+                      dt=0.1, compact_every=2, cpu_n=4096):
     """The 3D PIC-like cascade: a 256^3 periodic grid (dx = 2 pi / 32) of two
     counter-propagating circularly polarised standing waves of amplitude
     a0 = 800 each, filled on the device at every step's time; 16M electrons at
@@ -746,6 +754,7 @@ def config_3d_cascade(api, torch, steps=40, seed_n=1 << 24, cap=1 << 28, nx=256,
     nodes = nx ** 3
     bytes_total = (60 * cn[:, 0].sum() + 44 * cn[:, 1].sum() + 37 * c["emit_events"]
                    + 73 * c["pair_events"] + 2 * 32 * nodes * steps)
+    e_n, p_n, g_n = e.count(), p.count(), g.count()
     del e, p, g, grid
     torch.cuda.empty_cache()
 
@@ -766,6 +775,7 @@ def config_3d_cascade(api, torch, steps=40, seed_n=1 << 24, cap=1 << 28, nx=256,
             "steps_timed": steps, "steps_of_run": 500, "dt": dt, "status": run_status(c),
             "particle_steps_per_s": ps / (ms * 1e-3), "ms_per_step": ms / steps,
             "particles_per_step_first_last": [int(cn[0].sum()), int(cn[-1].sum())],
+            "particles_at_end": {"electrons": e_n, "positrons": p_n, "photons_slots": g_n},
             "emit_events": c["emit_events"], "pair_events": c["pair_events"],
             "roofline": _block_roofline(bytes_total / steps, ms / steps, peak, kind),
             "field_fill_bytes_per_step": 32 * nodes, "cpu_baseline": base}
@@ -864,9 +874,10 @@ def main():
     host["id"] += np.uint64(rank_id_offset(rank))
     H = Headline(api, torch, n, host)
     F = api.Fields.per_particle()
-    ctx_t = api.qed_init_tables(api.config(dt=DT, seed=1 + rank, max_particles=H.max_particles))
+    ctx_t = api.qed_init_tables(api.config(dt=DT, seed=1 + rank, max_particles=H.max_particles,
+                                           append_order=APPEND_ORDER))
     ctx_m = api.qed_init_tables(api.config(dt=DT, seed=1 + rank, max_particles=H.max_particles,
-                                           sampler=1))
+                                           sampler=1, append_order=APPEND_ORDER))
     api.qed_mlp_load(ctx_m, api.mlp_init_params(0))
     t_train = time.perf_counter()
     train_loss = api.qed_mlp_train(ctx_m, int(args.mlp_train_samples), lr=6e-3, seed=7)

@@ -81,6 +81,16 @@ enum { QED_GEN_METHOD_I = 0, QED_GEN_METHOD_II = 1, QED_GEN_METHOD_III = 2 };
  * photons below the lepton's energy (0 < xi < 1). */
 enum { QED_MODEL_FORMULA_I = 0, QED_MODEL_CLASSIC = 1 };
 enum { QED_FIELDS_UNIFORM = 0, QED_FIELDS_PER_PARTICLE = 1, QED_FIELDS_GRID = 2 };
+/* Order of the photons a lepton step appends (the paper prescribes none).
+ * ORDERED: in a deterministic order -- by a class of the particle's sub-step
+ *   count, then particle index, then sub-step -- so reruns give the same
+ *   arrays bit for bit.
+ * ANY: the same photons (ids, energies, positions, weights, fields) in an
+ *   order that depends on the scheduling of the GPU's warps; the lepton step
+ *   then runs in a single pass (FP32 contexts with event generator Method I;
+ *   other contexts append in the ORDERED way).  Capacity overflow drops
+ *   whichever appends come last. */
+enum { QED_APPEND_ORDERED = 0, QED_APPEND_ANY = 1 };
 
 /* ---- configuration ---------------------------------------------------- */
 typedef struct {
@@ -106,7 +116,7 @@ typedef struct {
   int generator;           /* QED_GEN_METHOD_I (default), _II or _III: photon event generator;
                               II and III need od_p, od_r on every lepton species */
   int model;               /* QED_MODEL_FORMULA_I (default) or QED_MODEL_CLASSIC */
-  int pad3_;
+  int append_order;        /* QED_APPEND_ORDERED (default) or QED_APPEND_ANY, see below */
 } qed_config;
 
 /* Fill *cfg with the paper-derived defaults (FP32, dt = 0.01, seed 0). */

@@ -23,6 +23,7 @@ QED_STATUS_TIMEOUT, QED_STATUS_SUBSTEPS, QED_STATUS_REPLAY = 8, 16, 32
 QED_PROF_PHASES = 7
 QED_GEN_METHOD_I, QED_GEN_METHOD_II, QED_GEN_METHOD_III = 0, 1, 2
 QED_MODEL_FORMULA_I, QED_MODEL_CLASSIC = 0, 1
+QED_APPEND_ORDERED, QED_APPEND_ANY = 0, 1
 
 ERRORS = {-1: "QED_ERR_ARG", -2: "QED_ERR_CUDA", -3: "QED_ERR_CAPACITY", -4: "QED_ERR_DOMAIN",
           -5: "QED_ERR_TIMEOUT", -6: "QED_ERR_NOCONV", -7: "QED_ERR_NOMEM", -8: "QED_ERR_UNSUPPORTED"}
@@ -43,7 +44,8 @@ class qed_config(C.Structure):
                 ("fwd_per_unit", C.c_double), ("inv_per_unit", C.c_double),
                 ("seed", C.c_uint64), ("spec_lo", C.c_double), ("spec_hi", C.c_double),
                 ("max_particles", C.c_int64), ("max_substeps", C.c_int64),
-                ("sampler", C.c_int), ("generator", C.c_int), ("model", C.c_int), ("pad3_", C.c_int)]
+                ("sampler", C.c_int), ("generator", C.c_int), ("model", C.c_int),
+                ("append_order", C.c_int)]
 
 
 class qed_species(C.Structure):

@@ -168,7 +168,31 @@ static bool cfg_valid(const qed_config *c) {
           (c->sampler == QED_SAMPLER_MLP && c->precision == QED_FP32)) &&
          (c->generator == QED_GEN_METHOD_I || c->generator == QED_GEN_METHOD_II ||
           c->generator == QED_GEN_METHOD_III) &&
-         (c->model == QED_MODEL_FORMULA_I || c->model == QED_MODEL_CLASSIC);
+         (c->model == QED_MODEL_FORMULA_I || c->model == QED_MODEL_CLASSIC) &&
+         (c->append_order == QED_APPEND_ORDERED || c->append_order == QED_APPEND_ANY);
+}
+
+// The single-pass lepton kernel's rate bound: W_rad = (alpha a_S / gamma)
+// (int_0^1 dW/dxi - int_0^xi_min dW/dxi) <= (alpha a_S / gamma) G(chi) with
+// G = e^R from the rate table; between and beyond the table's nodes ln G is
+// interpolated or extended with slope <= 1 in ln chi, so G(chi) / chi never
+// exceeds the largest node value of e^(R - l).  A 1% margin covers the cubic
+// interpolation and FP32 rounding.
+static int rate_bound(qed_ctx *c) {
+  const int n = c->gl.n;
+  double *R = (double *)malloc(sizeof(double) * (size_t)n);
+  if (!R) return QED_ERR_NOMEM;
+  cudaError_t e = cudaMemcpy(R, c->R64, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) { free(R); return cuda_fail(e, "rate bound"); }
+  double mx = 0.0;
+  for (int j = 0; j < n; ++j) {
+    const double l = c->gl.x0 + j * c->gl.h;
+    const double v = exp(R[j] - l);
+    if (v > mx) mx = v;
+  }
+  free(R);
+  c->w_up = (float)(1.01 * c->cfg.alpha * c->cfg.a_S * mx);
+  return QED_OK;
 }
 
 extern "C" int qed_init_tables(const qed_config *cfg, qed_ctx **out, qed_stream_t stream) {
@@ -275,6 +299,7 @@ extern "C" int qed_init_tables(const qed_config *cfg, qed_ctx **out, qed_stream_
     return QED_ERR_NOMEM;
   }
   rc = build_tables(c, st);
+  if (rc == QED_OK) rc = rate_bound(c);
   if (rc == QED_OK) rc = mlp_alloc(c);
   if (rc != QED_OK) { free_ctx(c); return rc; }
   *out = c;

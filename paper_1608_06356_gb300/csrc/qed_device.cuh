@@ -229,6 +229,14 @@ __device__ __forceinline__ double chi_lepton_d(double px, double py, double pz, 
   return sqrt(epar * epar + dx * dx + dy * dy + dz * dz) * inv_aS;
 }
 
+// The FP64 redo of the FP32 path, out of line: it runs only where the vector
+// sum cancels, and keeping it out of the callers keeps their code small.
+static __device__ __noinline__ double chi_lepton_d_redo(double px, double py, double pz, double ex,
+                                                 double ey, double ez, double bx, double by,
+                                                 double bz, double inv_aS) {
+  return chi_lepton_d(px, py, pz, ex, ey, ez, bx, by, bz, inv_aS);
+}
+
 template <class Real>
 __device__ __forceinline__ Real chi_lepton(Real px, Real py, Real pz, Real g, Real ex, Real ey,
                                            Real ez, Real bx, Real by, Real bz, Real inv_aS) {
@@ -247,9 +255,25 @@ __device__ __forceinline__ Real chi_lepton(Real px, Real py, Real pz, Real g, Re
   Real scale = g * (fabsf(eqx) + fabsf(eqy) + fabsf(eqz)) + fabsf(cx) + fabsf(cy) + fabsf(cz);
   if (d2 * (Real)16384 < scale * scale) {
     // cancellation: |d| < scale/128; redo the vector sum in FP64
-    return (Real)chi_lepton_d(px, py, pz, ex, ey, ez, bx, by, bz, (double)inv_aS);
+    return (Real)chi_lepton_d_redo(px, py, pz, ex, ey, ez, bx, by, bz, (double)inv_aS);
   }
   return m_sqrt(epar * epar + d2) * inv_aS;
+}
+
+// FP64 chi_ph a_S = |p| |E_perp + n x B|, for the FP32 path where the sum
+// cancels (out of line, as for leptons).  |p| is taken in FP64 from the
+// components: the FP32 sum of squares would leave n off unit length by ~1e-7,
+// as large as the cancelled sum itself.
+static __device__ __noinline__ double chi_photon_d_redo(double px, double py, double pz, double ex,
+                                                 double ey, double ez, double bx, double by,
+                                                 double bz, double inv_aS) {
+  const double k6 = sqrt(px * px + py * py + pz * pz);
+  const double n6x = px / k6, n6y = py / k6, n6z = pz / k6;
+  const double ep = n6x * ex + n6y * ey + n6z * ez;
+  const double qx = (ex - ep * n6x) + (n6y * bz - n6z * by);
+  const double qy = (ey - ep * n6y) + (n6z * bx - n6x * bz);
+  const double qz = (ez - ep * n6z) + (n6x * by - n6y * bx);
+  return k6 * sqrt(qx * qx + qy * qy + qz * qz) * inv_aS;
 }
 
 template <class Real>
@@ -274,15 +298,8 @@ __device__ __forceinline__ Real chi_photon(Real px, Real py, Real pz, Real ex, R
   Real dx = eqx + cx, dy = eqy + cy, dz = eqz + cz;
   Real d2 = dx * dx + dy * dy + dz * dz;
   Real scale = fabsf(eqx) + fabsf(eqy) + fabsf(eqz) + fabsf(cx) + fabsf(cy) + fabsf(cz);
-  if (d2 * (Real)16384 < scale * scale) {
-    double k6 = sqrt((double)k2);
-    double n6x = px / k6, n6y = py / k6, n6z = pz / k6;
-    double ep = n6x * ex + n6y * ey + n6z * ez;
-    double qx = ((double)ex - ep * n6x) + (n6y * bz - n6z * by);
-    double qy = ((double)ey - ep * n6y) + (n6z * bx - n6x * bz);
-    double qz = ((double)ez - ep * n6z) + (n6x * by - n6y * bx);
-    return (Real)(k6 * sqrt(qx * qx + qy * qy + qz * qz) * (double)inv_aS);
-  }
+  if (d2 * (Real)16384 < scale * scale)
+    return (Real)chi_photon_d_redo(px, py, pz, ex, ey, ez, bx, by, bz, (double)inv_aS);
   return k * m_sqrt(d2) * inv_aS;
 }
 

