@@ -86,7 +86,7 @@ static void free_ctx(qed_ctx *c) {
                   c->cls_chunk_off, c->cls_off, c->sub_cnt, c->sub_gf, c->rec_e,
                   c->rec_k, c->sub_meta, c->fill_meta, c->replay_n, c->stage, c->stage_tag,
                   c->stage_idx, c->stage_n, c->probe_state,
-                  c->mlp_mem};
+                  c->mlp_mem, c->w_up_row};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   free(c);
@@ -172,27 +172,33 @@ static bool cfg_valid(const qed_config *c) {
          (c->append_order == QED_APPEND_ORDERED || c->append_order == QED_APPEND_ANY);
 }
 
-// The single-pass lepton kernel's rate bound: W_rad = (alpha a_S / gamma)
+// The single-pass lepton kernel's rate bounds: W_rad = (alpha a_S / gamma)
 // (int_0^1 dW/dxi - int_0^xi_min dW/dxi) <= (alpha a_S / gamma) G(chi) with
-// G = e^R from the rate table; between and beyond the table's nodes ln G is
-// interpolated or extended with slope <= 1 in ln chi, so G(chi) / chi never
-// exceeds the largest node value of e^(R - l).  A 1% margin covers the cubic
-// interpolation and FP32 rounding.
+// G = e^R from the rate table.  Between and beyond the table's nodes ln G is
+// interpolated or extended with slope <= 1 in ln chi, so G(chi) / chi for
+// ln chi >= l_j never exceeds the largest node value of e^(R - l) at nodes
+// m >= j (w_up_row[j]; below the table G / chi is the first node's value).
+// A 1% margin covers the cubic interpolation between nodes and FP32 rounding.
 static int rate_bound(qed_ctx *c) {
   const int n = c->gl.n;
   double *R = (double *)malloc(sizeof(double) * (size_t)n);
-  if (!R) return QED_ERR_NOMEM;
+  float *row = (float *)malloc(sizeof(float) * (size_t)n);
+  if (!R || !row) { free(R); free(row); return QED_ERR_NOMEM; }
   cudaError_t e = cudaMemcpy(R, c->R64, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) { free(R); return cuda_fail(e, "rate bound"); }
+  if (e != cudaSuccess) { free(R); free(row); return cuda_fail(e, "rate bound"); }
+  const double k = 1.01 * c->cfg.alpha * c->cfg.a_S;
   double mx = 0.0;
-  for (int j = 0; j < n; ++j) {
+  for (int j = n - 1; j >= 0; --j) {
     const double l = c->gl.x0 + j * c->gl.h;
     const double v = exp(R[j] - l);
     if (v > mx) mx = v;
+    row[j] = (float)(k * mx);
   }
   free(R);
-  c->w_up = (float)(1.01 * c->cfg.alpha * c->cfg.a_S * mx);
-  return QED_OK;
+  if (cudaMalloc(&c->w_up_row, sizeof(float) * (size_t)n) != cudaSuccess) { free(row); return QED_ERR_NOMEM; }
+  e = cudaMemcpy(c->w_up_row, row, sizeof(float) * (size_t)n, cudaMemcpyHostToDevice);
+  free(row);
+  return cuda_fail(e, "rate bound");
 }
 
 extern "C" int qed_init_tables(const qed_config *cfg, qed_ctx **out, qed_stream_t stream) {
@@ -202,7 +208,10 @@ extern "C" int qed_init_tables(const qed_config *cfg, qed_ctx **out, qed_stream_
   if (!c) return QED_ERR_NOMEM;
   c->cfg = *cfg;
   const bool f64 = cfg->precision == QED_FP64;
-  if (!(c->cfg.fwd_per_unit > 0)) c->cfg.fwd_per_unit = f64 ? 16.0 : 4.0;
+  // the classic spectrum's tail near xi = 1 varies like exp(-2 / (3 chi)) with
+  // chi, so its FP32 rows need 2.5x the density for xi to 1e-5
+  if (!(c->cfg.fwd_per_unit > 0))
+    c->cfg.fwd_per_unit = f64 ? 16.0 : (cfg->model == QED_MODEL_CLASSIC ? 10.0 : 4.0);
   if (!(c->cfg.inv_per_unit > 0)) c->cfg.inv_per_unit = f64 ? 32.0 : 16.0;
   int rc = QED_OK;
   cudaError_t e = cudaGetDevice(&c->device);

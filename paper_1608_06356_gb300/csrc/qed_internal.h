@@ -69,8 +69,8 @@ struct qed_ctx {
   // persistent-grid occupancy factor (0 = as many CTAs per SM as fit)
   int grid_factor;
   // bound of the photon emission rate used by the single-pass lepton kernel:
-  // W_rad <= w_up chi / gamma for every chi and gamma (FP32 contexts)
-  float w_up;
+  // W_rad <= w_up_row[j] chi / gamma for ln chi >= row j of the rate table
+  float *w_up_row;  // [gl.n] (device)
   // measurement hooks (qed_profile_begin/end): 3 events per profiled step
   cudaEvent_t *prof_ev;   // QED_PROF_MARKS events per profiled step
   int prof_max, prof_n;

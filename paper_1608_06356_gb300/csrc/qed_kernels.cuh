@@ -197,7 +197,9 @@ template <class Real>
 __device__ __forceinline__ int spec_bin(const Consts &C, Real eps) {
   const Real lo = sel<Real>(C.spec_lo, C.f_spec_lo);
   if (!(eps >= lo)) return -1;
-  Real b = m_floor(sel<Real>(C.spec_scale, C.f_spec_scale) * m_log(eps / lo));
+  // (the FP32 path bins with the fast logarithm: a photon within ~1e-6 of a
+  // bin edge may fall on either side, as it may against FP64 binning anyway)
+  Real b = m_floor(sel<Real>(C.spec_scale, C.f_spec_scale) * r_log(r_div(eps, lo)));
   if (b < (Real)0 || b >= (Real)64) return -1;
   return (int)b;
 }

@@ -82,8 +82,10 @@ __global__ void __launch_bounds__(GRAD_THREADS) k_mlp_grad(GradArgs A) {
                                 (uint32_t)A.step, 0x4D4C5031u},
                              (uint32_t)A.seed, (uint32_t)(A.seed >> 32));
         const double ul = ((double)r.x + 0.5) * 0x1p-32, uk = ((double)r.y + 0.5) * 0x1p-32;
-        const double l = MLP_L_LO + (MLP_L_HI - MLP_L_LO) * ul;
-        const double k = MLP_K_LO + (MLP_K_HI - MLP_K_LO) * uk;
+        // the training domain extends past the one the network serves, so
+        // that its edges are not the edges of the fit
+        const double l = (MLP_L_LO - MLP_TRAIN_DL) + (MLP_L_HI - MLP_L_LO + 2 * MLP_TRAIN_DL) * ul;
+        const double k = (MLP_K_LO - MLP_TRAIN_DK) + (MLP_K_HI - MLP_K_LO + 2 * MLP_TRAIN_DK) * uk;
         const double Y = interp2(A.Y64, A.gl, l, A.gk, k);
         const double sp = k > 30.0 ? k : log1p(exp(k));
         x0 = (float)((l - MLP_LC) / MLP_LS);

@@ -32,6 +32,8 @@ constexpr float MLP_LS = 5.7564627325f;   // (ln 1e2 - ln 1e-3) / 2
 constexpr float MLP_KC = -3.25f, MLP_KS = 6.75f;
 constexpr float MLP_L_LO = -6.9077552790f, MLP_L_HI = 4.6051701860f;
 constexpr float MLP_K_LO = -10.0f, MLP_K_HI = 3.5f;
+// margins of the training domain beyond the served one, in ln chi and kappa
+constexpr double MLP_TRAIN_DL = 0.3, MLP_TRAIN_DK = 0.25;
 // BF16 fragments of W2 and W3: [layer 2][hi/lo 2][kt 4][nt 8][lane 32][2] uint32
 constexpr int MLP_FRAG_LAYER = 2 * 4 * 8 * 32 * 2;
 constexpr int MLP_FRAG_WORDS = 2 * MLP_FRAG_LAYER;

@@ -14,12 +14,13 @@
 // How the work is laid out, per warp of a persistent grid:
 //   streaming: each lane takes one particle of a 32-particle slice (the next
 //     slice's words are in flight into shared memory, cp.async), pushes it and
-//     computes chi.  The rate bound W <= w_up chi / gamma (w_up = alpha a_S
-//     times the largest value of int_0^1 dW/dxi / chi in the tables, so it
-//     holds with the xi_min cut and for every chi) settles most particles
-//     without the rate tables: if w_up chi Dt / gamma <= 0.2 the particle has
-//     one sub-step, and if its first draw r1 is not below that bound it has
-//     no event -- it is finished (its pushed state written).  The others go
+//     computes chi.  The rate bound W <= w_j chi / gamma (w_j = alpha a_S
+//     times the largest value of int_0^1 dW/dxi / chi in the rate table at
+//     and above the row j at or below ln chi, so it holds with the xi_min cut)
+//     settles most particles without the 2-D tables: if w_j chi Dt / gamma <=
+//     0.2 the particle has one sub-step, and if its first draw r1 is not
+//     below that bound it has no event -- it is finished (its pushed state
+//     written).  The others go
 //     to the warp's queue in shared memory (pushed momentum, fields, id,
 //     slot).
 //   heavy phase: when the queue holds 64 particles, the warp runs them with
@@ -47,9 +48,11 @@ namespace qed {
 
 namespace {
 
-constexpr int OP_WARPS = TILE / 32;
-constexpr int QCAP = 96;       // queue entries per warp
-constexpr int QTRIG = 64;      // a heavy phase starts when the queue holds this many
+// CTAs of 4 warps: with the per-warp shared memory below, 5 fit on an SM
+constexpr int OP_THREADS = 128;
+constexpr int OP_WARPS = OP_THREADS / 32;
+constexpr int QCAP = 64;       // queue entries per warp
+constexpr int QTRIG = 32;      // a heavy phase starts when the queue holds this many
 constexpr int QEXIT = QCAP - 32;  // ... and may end once it holds at most this many
 constexpr int MIN_LANES = 8;   // below this many lanes a round is deferred (lanes parked)
 constexpr int QF = 9;          // queue floats per entry: px py pz ex ey ez bx by bz
@@ -66,7 +69,7 @@ struct OnePassArgs {
   Out o;
   int64_t step;
   const int64_t *d_step;
-  float w_up;                  // W_rad <= w_up * chi / gamma
+  const float *w_up_row;       // W_rad <= w_up_row[j] chi / gamma for ln chi >= row j
   float chi_tab_lo, chi_tab_hi;  // chi range of the rate tables
   const uint32_t *mlp_frag;
   const float *mlp_w;
@@ -77,8 +80,8 @@ struct OnePassArgs {
 // only the queued particles evaluate the exact rate.
 template <int FM> __host__ __device__ size_t onepass_layout(const OnePassArgs &a, bool mlp, size_t off[5]) {
   size_t o = 0;
-  off[0] = o;  // prefetch
-  o += stream_prefetch_bytes<float, FM>();
+  off[0] = o;  // prefetch: two buffers of [NV][OP_THREADS] words and [OP_THREADS] ids
+  o += 2 * OP_THREADS * ((size_t)stream_words<FM>() * sizeof(float) + sizeof(uint64_t));
   off[1] = o;  // queues: slot [QCAP], floats [QF][QCAP], ids [QCAP] per warp
   o += (size_t)OP_WARPS * QCAP * (4 + 4 * QF + 8);
   off[2] = o;  // park: floats [PF][32], words [PU][32] per warp
@@ -95,7 +98,7 @@ enum { ST_IDLE = 0, ST_RATE = 1, ST_SCAN = 2, ST_PEND = 3, ST_DONE = 4 };
 // waits for this many pending lanes, a refill for this many idle ones; a
 // scanning round draws up to this many sub-steps per lane
 constexpr int CNT_MIN_EMIT_OP = 16;
-constexpr int CNT_SCAN_DRAWS_OP = 4;
+constexpr int CNT_SCAN_DRAWS_OP = 8;
 
 // N = max(1, ceil(W Dt / wdt_max)), capped at max_substeps (status bit).
 __device__ __forceinline__ int64_t substep_count_op(const Consts &C, float W, float dt, float wdt_max,
@@ -111,7 +114,7 @@ __device__ __forceinline__ int64_t substep_count_op(const Consts &C, float W, fl
 }
 
 template <int FM, int MODE, bool MLP>
-__global__ void __launch_bounds__(TILE, MLP ? 1 : 2) k_lepton_onepass(OnePassArgs A) {
+__global__ void __launch_bounds__(OP_THREADS, MLP ? 2 : 5) k_lepton_onepass(OnePassArgs A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ BlockTally bt;
   __shared__ long long s_meta[4];
@@ -122,8 +125,8 @@ __global__ void __launch_bounds__(TILE, MLP ? 1 : 2) k_lepton_onepass(OnePassArg
   onepass_layout<FM>(A, MLP, off);
   const float *sR = A.T.R, *sF = A.T.F;
   float *pf = reinterpret_cast<float *>(smem_raw + off[0]);
-  uint64_t *pf_id = reinterpret_cast<uint64_t *>(pf + 2 * NV * TILE);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint64_t *pf_id = reinterpret_cast<uint64_t *>(pf + 2 * NV * OP_THREADS);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;  // wid < OP_WARPS
   const unsigned lt_mask = (1u << lane) - 1u;
   unsigned char *qbase = smem_raw + off[1] + (size_t)wid * QCAP * (4 + 4 * QF + 8);
   uint32_t *q_slot = reinterpret_cast<uint32_t *>(qbase);
@@ -149,7 +152,6 @@ __global__ void __launch_bounds__(TILE, MLP ? 1 : 2) k_lepton_onepass(OnePassArg
   const int64_t T0 = (n0 + TILE - 1) / TILE, T1 = (n1 + TILE - 1) / TILE;
   const int64_t nslots = (T0 + T1) * TILE;
   const float inv_aS = A.C.f_inv_aS, dt = A.C.f_dt, wdt_max = A.C.f_wdt_max;
-  const float wup_dt = A.w_up * dt;
   Tally tl;
   tl.clear();
   uint32_t deferred = 0;  // heavy particles taken by this lane
@@ -255,9 +257,15 @@ __global__ void __launch_bounds__(TILE, MLP ? 1 : 2) k_lepton_onepass(OnePassArg
         }
       } else if (phase == ST_SCAN) {
         if (st == ST_SCAN) {
-          for (int s = 0; s < CNT_SCAN_DRAWS_OP; ++s) {
-            const U4 r = draw(A.C.seed, pid, step_, k, STREAM_EMIT);
-            if (ro.W * dts > unif<float>(r.x)) { wy = r.y; st = ST_PEND; break; }
+          // draws two sub-steps at a time (independent Philox chains run
+          // interleaved); the second is used only if the first has no event
+          const float thr = ro.W * dts;
+          for (int s = 0; s < CNT_SCAN_DRAWS_OP; s += 2) {
+            const U4 ra = draw(A.C.seed, pid, step_, k, STREAM_EMIT);
+            const U4 rb = draw(A.C.seed, pid, step_, k + 1, STREAM_EMIT);
+            if (thr > unif<float>(ra.x)) { wy = ra.y; st = ST_PEND; break; }
+            if (++k >= N) { st = ST_DONE; break; }
+            if (thr > unif<float>(rb.x)) { wy = rb.y; st = ST_PEND; break; }
             if (++k >= N) { st = ST_DONE; break; }
           }
         }
@@ -365,18 +373,18 @@ __global__ void __launch_bounds__(TILE, MLP ? 1 : 2) k_lepton_onepass(OnePassArg
     slot_index(sl, si, i);
     const Sp<float> &S = A.sp[si];
     if (i >= (si ? n1 : n0)) return;
-    float *d = pf + (size_t)b * NV * TILE + t;
+    float *d = pf + (size_t)b * NV * OP_THREADS + t;
     const float *src[12] = {S.x, S.y, S.z, S.px, S.py, S.pz, S.ex, S.ey, S.ez, S.bx, S.by, S.bz};
 #pragma unroll
-    for (int c = 0; c < NV; ++c) cp_async<4>(d + c * TILE, src[c] + i);
-    cp_async<8>(pf_id + b * TILE + t, S.id + i);
+    for (int c = 0; c < NV; ++c) cp_async<4>(d + c * OP_THREADS, src[c] + i);
+    cp_async<8>(pf_id + b * OP_THREADS + t, S.id + i);
   };
-  const int64_t stride = (int64_t)gridDim.x * TILE;
+  const int64_t stride = (int64_t)gridDim.x * OP_THREADS;
   int buf = 0;
-  int64_t slot = blockIdx.x * (int64_t)TILE + threadIdx.x;
+  int64_t slot = blockIdx.x * (int64_t)OP_THREADS + threadIdx.x;
   if (slot < nslots) prefetch(slot, 0);
   cp_async_commit();
-  // nslots is a multiple of TILE: every lane of a warp runs the same
+  // nslots is a multiple of OP_THREADS: every lane of a warp runs the same
   // iterations; the one call of the heavy phase keeps its code once
   for (;;) {
     const bool streaming = slot < nslots;
@@ -393,16 +401,16 @@ __global__ void __launch_bounds__(TILE, MLP ? 1 : 2) k_lepton_onepass(OnePassArg
       float E[3] = {0.f, 0.f, 0.f}, B[3] = {0.f, 0.f, 0.f};
       uint64_t pid = 0;
       if (i < (si ? n1 : n0)) {
-        const float *v = pf + (size_t)buf * NV * TILE + t;
-        float x = v[0], y = v[TILE], z = v[2 * TILE];
-        px = v[3 * TILE]; py = v[4 * TILE]; pz = v[5 * TILE];
+        const float *v = pf + (size_t)buf * NV * OP_THREADS + t;
+        float x = v[0], y = v[OP_THREADS], z = v[2 * OP_THREADS];
+        px = v[3 * OP_THREADS]; py = v[4 * OP_THREADS]; pz = v[5 * OP_THREADS];
         if (FM == FM_PER_PARTICLE) {
-          E[0] = v[6 * TILE]; E[1] = v[7 * TILE]; E[2] = v[8 * TILE];
-          B[0] = v[9 * TILE]; B[1] = v[10 * TILE]; B[2] = v[11 * TILE];
+          E[0] = v[6 * OP_THREADS]; E[1] = v[7 * OP_THREADS]; E[2] = v[8 * OP_THREADS];
+          B[0] = v[9 * OP_THREADS]; B[1] = v[10 * OP_THREADS]; B[2] = v[11 * OP_THREADS];
         } else {
           get_fields<float, FM>(S, A.f, i, x, y, z, E, B);
         }
-        pid = pf_id[buf * TILE + t];
+        pid = pf_id[buf * OP_THREADS + t];
         float g;
         if (MODE != MODE_EMIT) {
           g = boris(px, py, pz, E, B, S.q, dt);
@@ -415,8 +423,11 @@ __global__ void __launch_bounds__(TILE, MLP ? 1 : 2) k_lepton_onepass(OnePassArg
           tl.status |= QED_STATUS_NONFINITE;  // left as it was
         } else {
           const float chi = chi_lepton(px, py, pz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
-          // one sub-step and no event, for sure, from the rate bound and r1
-          const float wdt_up = r_div(wup_dt * chi, g);
+          // one sub-step and no event, for sure, from the rate bound of the
+          // table row at or below ln chi, and r1
+          const float fj = (r_log(chi) - A.T.gl.x0) * A.T.gl.inv_h;
+          const int j = fj >= 0.f ? (fj < (float)(A.T.gl.n - 1) ? (int)fj : A.T.gl.n - 1) : 0;
+          const float wdt_up = r_div(__ldg(A.w_up_row + j) * dt * chi, g);
           bool done = false;
           if (wdt_up <= wdt_max) {
             const U4 r = draw(A.C.seed, pid, step_, 0, STREAM_EMIT);
@@ -497,10 +508,10 @@ cudaError_t launch_onepass_t(qed_ctx *c, const OnePassArgs &a, cudaStream_t st) 
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE, sm);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, OP_THREADS, sm);
   if (e != cudaSuccess) return e;
   per_sm = persistent_blocks_per_sm(c, per_sm);
-  kern<<<c->num_sms * per_sm, TILE, sm, st>>>(a);
+  kern<<<c->num_sms * per_sm, OP_THREADS, sm, st>>>(a);
   c->launches += 1;
   return cudaGetLastError();
 }
@@ -531,7 +542,7 @@ cudaError_t launch_lepton_onepass(qed_ctx *c, const qed_species *s0, const qed_s
   a.o = out_of(c);
   a.step = step;
   a.d_step = c->use_dstep ? c->d_step : nullptr;
-  a.w_up = c->w_up;
+  a.w_up_row = c->w_up_row;
   a.chi_tab_lo = (float)exp(c->gl.lo);
   a.chi_tab_hi = (float)exp(c->gl.hi);
   a.mlp_frag = c->mlp_frag;

@@ -4,9 +4,11 @@ comparison (the classic spectrum overestimates hard photons).
 
 Tolerances: FP32 rates 1e-4 relative, FP64 1e-6 (1e-3 for rates below 1e-8
 of the largest, deep in the xi_min cut's exponential tail); xi from the
-inverse CDF 1e-5 relative for the median draw and 1e-3 at worst (the classic
-CDF approaches 1 only like 1 - xi, which its kappa grid resolves coarsely);
-chi in [1e-3, 3]."""
+inverse CDF 1e-5 relative (both precisions), wherever the rate is not zero
+to within e^-69 (there the cut leaves nothing to sample); chi in [1e-3, 3].
+The classic spectrum's tail near xi = 1 varies like exp(-2 / (3 chi)) with chi,
+so the FP32 classic tables have 10 rows per unit of ln chi (formula I's have
+4)."""
 import numpy as np
 import pytest
 import torch
@@ -25,7 +27,7 @@ def api():
 def test_classic_rate_and_xi_match_oracle(api, orc):
     from paper_1608_06356_gb300 import workloads as W
     rng = np.random.default_rng(21)
-    n = 200
+    n = 2000
     chi = np.exp(rng.uniform(np.log(1e-3), np.log(3.0), n))
     gamma = np.exp(rng.uniform(np.log(10), np.log(1e5), n))
     cfg = orc.make_config(model=orc.MODEL_CLASSIC)
@@ -48,12 +50,10 @@ def test_classic_rate_and_xi_match_oracle(api, orc):
         assert np.all(Wg[~big] <= 2e-8 * Wo.max())
         xg = api.qed_sample_table(ctx, 0, torch.tensor(chi, device="cuda"), torch.tensor(gamma, device="cuda"),
                                   torch.tensor(words.view(np.int32), device="cuda")).cpu().numpy()
-        # the classic CDF approaches 1 only like 1 - xi, so its inverse table
-        # (uniform in kappa = ln(-ln(1 - u))) resolves the spectrum more
-        # coarsely than formula I's: 1e-3 at worst, 1e-5 for the median draw
-        rel = np.abs(xg / xo - 1)
-        assert rel.max() <= 1e-3, (prec, rel.max())
-        assert np.median(rel) <= 1e-5, (prec, np.median(rel))
+        live = Wo > 1e-30 * Wo.max()
+        rel = np.abs(xg / xo - 1)[live]
+        assert live.sum() >= n - 10
+        assert rel.max() <= 1e-5, (prec, rel.max())
 
 
 def test_fig1_classic_overestimates_hard_photons(api):
