@@ -338,36 +338,39 @@ def e2e_arm(api, torch, ctx, H, F, host, steps, step0):
                     "electrons' positions and momenta and the new photons back"}
 
 
-def spectral_error(api, torch, ctx_m, ctx_judge, n_chi=64, gamma=1e4, iters=34):
-    """Deterministic spectral error of the learned sampler: at n_chi values of
-    chi log-spaced over its domain [1e-3, 1e2], the uniform u at each of the 65
-    edges of 64 log bins of xi over [2/gamma, 1] is found by bisection in u
-    (the sampler is monotone in u), giving the sampler's bin probabilities;
-    `ctx_judge`'s inverse table gives the reference ones the same way.  Returns
-    the largest relative error over bins with probability >= 1e-3, and the
-    largest total-variation distance, over all chi."""
-    chis = np.exp(np.linspace(np.log(1e-3), np.log(1e2), n_chi))
-    edges = np.exp(np.linspace(np.log(2.0 / gamma), 0.0, 65))
-    C_ = np.repeat(chis, 65)
-    X = np.tile(edges, n_chi)
+def sampler_edge_u(api, torch, ctx, which, chis, edges, gamma, iters=34):
+    """For each chi of `chis` and each xi of `edges`, the uniform u of the
+    first word whose sample (qed_sample_table `which`: 0 the inverse table, 2
+    the learned sampler) reaches xi, found by bisection over the 2^32 words
+    (the samplers are monotone in u).  Returns u[len(chis), len(edges)]; the
+    differences along a row are the sampler's bin probabilities."""
+    C_ = np.repeat(chis, len(edges))
+    X = np.tile(edges, len(chis))
     chi_d = torch.tensor(C_, device="cuda")
     g_d = torch.full_like(chi_d, gamma)
+    lo = np.zeros(len(C_), dtype=np.int64)
+    hi = np.full(len(C_), 2 ** 32, dtype=np.int64)  # xi(word) >= edge for word >= hi
+    for _ in range(iters):
+        mid = (lo + hi) // 2
+        w = torch.tensor((np.minimum(mid, 2 ** 32 - 1)).astype(np.uint32).view(np.int32), device="cuda")
+        xi = api.qed_sample_table(ctx, which, chi_d, g_d, w).cpu().numpy()
+        below = xi < X
+        lo = np.where(below, mid, lo)
+        hi = np.where(below, hi, mid)
+    return (hi.astype(np.float64) * 2.0 ** -32).reshape(len(chis), len(edges))
 
-    def u_at_edges(ctx, which):
-        lo = np.zeros(len(C_), dtype=np.int64)
-        hi = np.full(len(C_), 2 ** 32, dtype=np.int64)  # xi(word) >= edge for word >= hi
-        for _ in range(iters):
-            mid = (lo + hi) // 2
-            w = torch.tensor((np.minimum(mid, 2 ** 32 - 1)).astype(np.uint32).view(np.int32),
-                             device="cuda")
-            xi = api.qed_sample_table(ctx, which, chi_d, g_d, w).cpu().numpy()
-            below = xi < X
-            lo = np.where(below, mid, lo)
-            hi = np.where(below, hi, mid)
-        return hi.astype(np.float64) * 2.0 ** -32  # u of the first word at or above the edge
 
-    um = u_at_edges(ctx_m, 2).reshape(n_chi, 65)
-    ut = u_at_edges(ctx_judge, 0).reshape(n_chi, 65)
+def spectral_error(api, torch, ctx_m, ctx_judge, n_chi=64, gamma=1e4):
+    """Deterministic spectral error of the learned sampler: at n_chi values of
+    chi log-spaced over its domain [1e-3, 1e2], the bin probabilities of 64 log
+    bins of xi over [2/gamma, 1] that the sampler implies (sampler_edge_u)
+    against those of `ctx_judge`'s FP64-built inverse table.  Returns the
+    largest relative error over bins with probability >= 1e-3 and the largest
+    total-variation distance, over all chi."""
+    chis = np.exp(np.linspace(np.log(1e-3), np.log(1e2), n_chi))
+    edges = np.exp(np.linspace(np.log(2.0 / gamma), 0.0, 65))
+    um = sampler_edge_u(api, torch, ctx_m, 2, chis, edges, gamma)
+    ut = sampler_edge_u(api, torch, ctx_judge, 0, chis, edges, gamma)
     pm, pt = np.diff(um, axis=1), np.diff(ut, axis=1)
     big = pt >= 1e-3
     rel = np.where(big, np.abs(pm - pt) / np.maximum(pt, 1e-300), 0.0)
@@ -375,7 +378,7 @@ def spectral_error(api, torch, ctx_m, ctx_judge, n_chi=64, gamma=1e4, iters=34):
     return {"max_rel_error_bins_p_ge_1e-3": float(rel.max()),
             "median_rel_error_bins_p_ge_1e-3": float(np.median(rel[big])),
             "max_total_variation": float(tv.max()), "chi_nodes": n_chi, "bins": 64,
-            "gamma": gamma, "judge": "FP64 inverse table of the same library (bisection in u)"}
+            "gamma": gamma, "judge": "inverse table of the same library, built in FP64 (bisection in u)"}
 
 
 def sampler_comparison(api, torch, n, ctx_t, ctx_m, reps=5):
@@ -412,7 +415,8 @@ def batched_runs_bench(api, torch, mlp_weights, steps=4):
     """256 independent ensembles of uneven size (log-uniform in [1e3, 1e6]) with
     per-run chi ranges (two sorted log-uniform draws in [0.01, 10]), advanced
     together: eager launches vs one captured CUDA graph per `steps` steps,
-    table and learned samplers."""
+    table and learned samplers, each with the launch sizes (CTAs per SM per
+    kernel group) its autotuner chose on a copy of the runs."""
     from paper_1608_06356_gb300 import workloads as W
     sizes, ranges = W.batched_runs(256, seed=0)
     parts, off = [], 0
@@ -428,11 +432,24 @@ def batched_runs_bench(api, torch, mlp_weights, steps=4):
     out = {"runs": 256, "particles": int(n), "steps": steps}
     for name, sampler in (("table", 0), ("mlp", 1)):
         res = {}
+        tuning = None
         for mode in ("eager", "graph"):
             ctx = api.qed_init_tables(api.config(dt=DT, seed=11, sampler=sampler,
-                                                 max_particles=int(0.4 * n * (steps + 2)) + n))
+                                                 max_particles=int(0.4 * n * (steps + 2)) + n,
+                                                 append_order=APPEND_ORDER))
             if sampler:
                 api.qed_mlp_load(ctx, mlp_weights)
+            if tuning is None:  # launch sizes per kernel group, on disposable copies
+                e = api.Species.empty(2 * n, -1, fields=True, tag=True).load(**host)
+                p = api.Species.empty(n, 1, fields=True, tag=True)
+                g = api.Species.empty(int(0.4 * n * (steps + 2)), 0, fields=True, tag=True)
+                tuning = api.qed_autotune_groups(ctx, e, p, g, F, reps=2)
+                res["tuning"] = {"grid_factor_ctas_per_sm": tuning["grid_factor"],
+                                 "ms_per_step_tuned": tuning["ms_per_step"],
+                                 "ms_per_factor": tuning["ms"]}
+                del e, p, g
+            else:
+                api.qed_set_tuning(ctx, tuning["grid_factor"])
             e = api.Species.empty(2 * n, -1, fields=True, tag=True).load(**host)
             p = api.Species.empty(n, 1, fields=True, tag=True)
             g = api.Species.empty(int(0.4 * n * (steps + 2)), 0, fields=True, tag=True)
@@ -840,7 +857,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=DEFAULT_E2E_STEPS)
     ap.add_argument("--ref-particles", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mlp-train-samples", type=float, default=4e9)
+    ap.add_argument("--mlp-train-samples", type=float, default=1.6e10)
     ap.add_argument("--sampler-bench", type=int, default=1)
     ap.add_argument("--batched-bench", type=int, default=1)
     ap.add_argument("--configs-bench", type=int, default=1)

@@ -337,15 +337,52 @@ int qed_run_batched(qed_ctx *ctx, const qed_species *e, const qed_species *p,
                     const qed_species *g, const qed_fields *f, int64_t step0, int steps,
                     int n_runs, int64_t *d_run_photons, qed_stream_t stream);
 
-/* Autotuner of the persistent launches: times `reps` fused steps (plus
- * qed_compact_fill of the photons) for each persistent-grid occupancy factor 1..max on the given
- * species -- which it advances, so pass a disposable copy -- keeps the
- * fastest factor in the context for all later launches and returns it in
- * *best_factor; per-candidate milliseconds go to ms_out[0..max-1] if non-NULL
- * (host, max 8 entries).  factor 0 = as many CTAs per SM as fit. */
+/* Autotuner of the persistent launches with one factor for every kernel group:
+ * times `reps` fused steps (plus qed_compact_fill of the photons) for each
+ * persistent-grid occupancy factor 1..8 on the given species -- which it
+ * advances, so pass a disposable copy -- keeps the fastest factor in the
+ * context (for every group) for all later launches and returns it in
+ * *best_factor; per-candidate milliseconds go to ms_out[0..7] if non-NULL
+ * (host).  factor 0 = as many CTAs per SM as fit.  qed_autotune_groups tunes
+ * the groups separately. */
 int qed_autotune(qed_ctx *ctx, const qed_species *e, const qed_species *p, const qed_species *g,
                  const qed_fields *f, int reps, int *best_factor, double *ms_out,
                  qed_stream_t stream);
+
+/* Launch tuning by kernel group.  Every step kernel is a persistent launch of
+ * a fixed block size (256 threads; the single-pass lepton kernel 128) whose
+ * grid is the number of SMs times a number of CTAs per SM; that number, up to
+ * what fits, is chosen per group of kernels:
+ *   QED_TUNE_STREAM   lepton streaming: k_lepton_stream, the single-pass
+ *                     lepton kernel, the push-only pass
+ *   QED_TUNE_CHAINS   the ordered path's Method I chains (counting, replay)
+ *   QED_TUNE_ORDER    the ordered path's lists, scans and writing pass
+ *   QED_TUNE_PHOTON   photon streaming and pair passes
+ *   QED_TUNE_COMPACT  stable compaction and the isolated sampler */
+enum { QED_TUNE_STREAM = 0, QED_TUNE_CHAINS = 1, QED_TUNE_ORDER = 2, QED_TUNE_PHOTON = 3,
+       QED_TUNE_COMPACT = 4, QED_TUNE_GROUPS = 5, QED_TUNE_MAX_FACTOR = 8 };
+typedef struct {
+  int grid_factor[QED_TUNE_GROUPS]; /* CTAs per SM per group; 0 = as many as fit */
+  int pad_;
+  double ms_per_step;               /* one fused step + qed_compact_fill of the photons,
+                                       with the chosen factors */
+  double ms[QED_TUNE_GROUPS][QED_TUNE_MAX_FACTOR]; /* per group, per factor 1..8 (the
+                                       other groups at their values then; a factor beyond
+                                       what fits runs as what fits) */
+} qed_tuning;
+
+/* Autotuner by kernel group: for each group in turn (the order above), times
+ * `reps` fused steps plus qed_compact_fill of the photons for every factor that
+ * fits (1..8 CTAs per SM), keeping the best before tuning the next group.  The
+ * species are advanced -- pass disposable copies.  The chosen factors are kept
+ * in the context for all later launches and written, with the timings, to
+ * *out (host).  Synchronous. */
+int qed_autotune_groups(qed_ctx *ctx, const qed_species *e, const qed_species *p,
+                        const qed_species *g, const qed_fields *f, int reps, qed_tuning *out,
+                        qed_stream_t stream);
+
+/* Apply stored factors (grid_factor of *t; ms fields ignored). */
+int qed_set_tuning(qed_ctx *ctx, const qed_tuning *t);
 
 /* Measurement hooks.  qed_profile_begin creates CUDA events (call it outside
  * any timed or captured region) so that each of the next max_steps calls of

@@ -74,6 +74,16 @@ class qed_counters(C.Structure):
                 "status": self.status, "hist": list(self.hist), "deferred": self.deferred}
 
 
+QED_TUNE_GROUPS, QED_TUNE_MAX_FACTOR = 5, 8
+TUNE_GROUP_NAMES = ("stream", "chains", "order", "photon", "compact")
+
+
+class qed_tuning(C.Structure):
+    _fields_ = [("grid_factor", C.c_int * QED_TUNE_GROUPS), ("pad_", C.c_int),
+                ("ms_per_step", C.c_double),
+                ("ms", (C.c_double * QED_TUNE_MAX_FACTOR) * QED_TUNE_GROUPS)]
+
+
 # name -> (restype, argtypes); the exported C ABI, one entry per declaration
 _P = C.c_void_p
 SIGNATURES = {
@@ -111,6 +121,10 @@ SIGNATURES = {
     "qed_autotune": (C.c_int, [_P, C.POINTER(qed_species), C.POINTER(qed_species),
                                C.POINTER(qed_species), C.POINTER(qed_fields), C.c_int,
                                C.POINTER(C.c_int), C.POINTER(C.c_double), _P]),
+    "qed_autotune_groups": (C.c_int, [_P, C.POINTER(qed_species), C.POINTER(qed_species),
+                                      C.POINTER(qed_species), C.POINTER(qed_fields), C.c_int,
+                                      C.POINTER(qed_tuning), _P]),
+    "qed_set_tuning": (C.c_int, [_P, C.POINTER(qed_tuning)]),
     "qed_mlp_load": (C.c_int, [_P, _P, C.c_size_t]),
     "qed_mlp_get": (C.c_int, [_P, _P, C.c_size_t]),
     "qed_mlp_train": (C.c_int, [_P, C.c_int64, C.c_float, C.c_uint64, C.POINTER(C.c_double), _P]),

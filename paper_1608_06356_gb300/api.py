@@ -419,3 +419,25 @@ def qed_autotune(ctx: Context, e: Species, p: Species, g: Species, f, reps: int 
                                  C.byref(g.struct()), C.byref(f), int(reps), C.byref(best), ms,
                                  _stream(stream)), "qed_autotune")
     return best.value, [ms[i] for i in range(8)]
+
+
+def qed_autotune_groups(ctx: Context, e: Species, p: Species, g: Species, f, reps: int = 2,
+                        stream=None) -> dict:
+    """Tune the CTAs per SM of each kernel group on disposable species (they
+    are advanced).  Returns {"grid_factor": {group: factor}, "ms_per_step": ..,
+    "ms": {group: [ms per factor 1..8]}}; the factors stay in the context."""
+    t = B.qed_tuning()
+    B.check(B.lib().qed_autotune_groups(ctx.handle, C.byref(e.struct()), C.byref(p.struct()),
+                                        C.byref(g.struct()), C.byref(f), int(reps), C.byref(t),
+                                        _stream(stream)), "qed_autotune_groups")
+    return {"grid_factor": {n: int(t.grid_factor[k]) for k, n in enumerate(B.TUNE_GROUP_NAMES)},
+            "ms_per_step": t.ms_per_step,
+            "ms": {n: [float(t.ms[k][j]) for j in range(B.QED_TUNE_MAX_FACTOR)]
+                   for k, n in enumerate(B.TUNE_GROUP_NAMES)}}
+
+
+def qed_set_tuning(ctx: Context, grid_factor: dict) -> None:
+    t = B.qed_tuning()
+    for k, n in enumerate(B.TUNE_GROUP_NAMES):
+        t.grid_factor[k] = int(grid_factor.get(n, 0))
+    B.check(B.lib().qed_set_tuning(ctx.handle, C.byref(t)), "qed_set_tuning")

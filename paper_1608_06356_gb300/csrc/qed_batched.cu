@@ -131,6 +131,24 @@ extern "C" int qed_run_batched(qed_ctx *c, const qed_species *e, const qed_speci
   return QED_OK;
 }
 
+// Mean milliseconds of `reps` steps (fused step + hole-filling compaction of
+// the photons) after one untimed step at the current launch sizes.
+static int time_steps(qed_ctx *c, const qed_species *e, const qed_species *p, const qed_species *g,
+                      const qed_fields *f, int reps, int64_t &step, cudaEvent_t a, cudaEvent_t b,
+                      cudaStream_t st, double *per) {
+  int rc = one_step(c, e, p, g, f, step++, st);  // warm-up for this size
+  if (rc != QED_OK) return rc;
+  cudaEventRecord(a, st);
+  for (int r = 0; r < reps && rc == QED_OK; ++r) rc = one_step(c, e, p, g, f, step++, st);
+  cudaEventRecord(b, st);
+  if (rc != QED_OK) return rc;
+  float ms = 0.f;
+  if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess)
+    return QED_ERR_CUDA;
+  *per = ms / reps;
+  return QED_OK;
+}
+
 extern "C" int qed_autotune(qed_ctx *c, const qed_species *e, const qed_species *p,
                             const qed_species *g, const qed_fields *f, int reps, int *best_factor,
                             double *ms_out, qed_stream_t stream) {
@@ -138,24 +156,21 @@ extern "C" int qed_autotune(qed_ctx *c, const qed_species *e, const qed_species 
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t a, b;
   if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return QED_ERR_CUDA;
-  const int saved = c->grid_factor;
+  int saved[QED_TUNE_GROUPS];
+  memcpy(saved, c->grid_factor, sizeof(saved));
   double best_ms = 1e300;
   int best = 0;
   int64_t step = 1000000;
   for (int factor = 1; factor <= 8; ++factor) {
-    c->grid_factor = factor;
-    int rc = one_step(c, e, p, g, f, step++, st);  // warm-up for this size
-    if (rc != QED_OK) { c->grid_factor = saved; return rc; }
-    cudaEventRecord(a, st);
-    for (int r = 0; r < reps && rc == QED_OK; ++r) rc = one_step(c, e, p, g, f, step++, st);
-    cudaEventRecord(b, st);
-    if (rc != QED_OK) { c->grid_factor = saved; return rc; }
-    float ms = 0.f;
-    if (cudaEventSynchronize(b) != cudaSuccess || cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
-      c->grid_factor = saved;
-      return QED_ERR_CUDA;
+    for (int k = 0; k < QED_TUNE_GROUPS; ++k) c->grid_factor[k] = factor;
+    double per = 0.0;
+    const int rc = time_steps(c, e, p, g, f, reps, step, a, b, st, &per);
+    if (rc != QED_OK) {
+      memcpy(c->grid_factor, saved, sizeof(saved));
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+      return rc;
     }
-    const double per = ms / reps;
     if (ms_out) ms_out[factor - 1] = per;
     if (per < best_ms) {
       best_ms = per;
@@ -164,7 +179,55 @@ extern "C" int qed_autotune(qed_ctx *c, const qed_species *e, const qed_species 
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  c->grid_factor = best;
+  for (int k = 0; k < QED_TUNE_GROUPS; ++k) c->grid_factor[k] = best;
   *best_factor = best;
+  return QED_OK;
+}
+
+extern "C" int qed_autotune_groups(qed_ctx *c, const qed_species *e, const qed_species *p,
+                                   const qed_species *g, const qed_fields *f, int reps,
+                                   qed_tuning *out, qed_stream_t stream) {
+  if (!c || !e || !p || !g || !f || reps <= 0 || !out) return QED_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return QED_ERR_CUDA;
+  memset(out, 0, sizeof(*out));
+  int saved[QED_TUNE_GROUPS];
+  memcpy(saved, c->grid_factor, sizeof(saved));
+  int64_t step = 2000000;
+  int rc = QED_OK;
+  double best_ms = 1e300;
+  // coordinate descent: one group at a time, the others at their current best
+  for (int grp = 0; grp < QED_TUNE_GROUPS && rc == QED_OK; ++grp) {
+    int best = 0;
+    double best_g = 1e300;
+    for (int factor = 1; factor <= QED_TUNE_MAX_FACTOR && rc == QED_OK; ++factor) {
+      c->grid_factor[grp] = factor;
+      double per = 0.0;
+      rc = time_steps(c, e, p, g, f, reps, step, a, b, st, &per);
+      if (rc != QED_OK) break;
+      out->ms[grp][factor - 1] = per;
+      if (per < best_g) { best_g = per; best = factor; }
+    }
+    c->grid_factor[grp] = best;
+    best_ms = best_g;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc != QED_OK) {
+    memcpy(c->grid_factor, saved, sizeof(saved));
+    return rc;
+  }
+  memcpy(out->grid_factor, c->grid_factor, sizeof(out->grid_factor));
+  out->ms_per_step = best_ms;
+  return QED_OK;
+}
+
+extern "C" int qed_set_tuning(qed_ctx *c, const qed_tuning *t) {
+  if (!c || !t) return QED_ERR_ARG;
+  for (int k = 0; k < QED_TUNE_GROUPS; ++k) {
+    if (t->grid_factor[k] < 0 || t->grid_factor[k] > 64) return QED_ERR_ARG;
+    c->grid_factor[k] = t->grid_factor[k];
+  }
   return QED_OK;
 }

@@ -66,8 +66,9 @@ struct qed_ctx {
   cudaGraphExec_t graph_exec;
   cudaStream_t capture_stream;  // non-blocking stream the graph is captured on
   unsigned long long graph_key[24];
-  // persistent-grid occupancy factor (0 = as many CTAs per SM as fit)
-  int grid_factor;
+  // persistent-grid occupancy factor per kernel group (QED_TUNE_*; 0 = as
+  // many CTAs per SM as fit)
+  int grid_factor[QED_TUNE_GROUPS];
   // bound of the photon emission rate used by the single-pass lepton kernel:
   // W_rad <= w_up_row[j] chi / gamma for ln chi >= row j of the rate table
   float *w_up_row;  // [gl.n] (device)
@@ -80,11 +81,12 @@ struct qed_ctx {
 namespace qed {
 int build_tables(qed_ctx *c, cudaStream_t st);
 int mlp_alloc(qed_ctx *c);
-// CTAs per SM for a persistent launch: the occupancy limit, capped by the
-// autotuned factor when one is set
-inline int persistent_blocks_per_sm(const qed_ctx *c, int occupancy) {
+// CTAs per SM for a persistent launch of a kernel group: the occupancy limit,
+// capped by the group's autotuned factor when one is set
+inline int persistent_blocks_per_sm(const qed_ctx *c, int occupancy, int group) {
   int b = occupancy < 1 ? 1 : occupancy;
-  if (c->grid_factor > 0 && c->grid_factor < b) b = c->grid_factor;
+  const int f = c->grid_factor[group];
+  if (f > 0 && f < b) b = f;
   return b;
 }
 // Event marks of a profiled fused step: 0 start, 1 after the lepton

@@ -47,7 +47,9 @@ __device__ __forceinline__ float mlp_baseline(float k) {
   return 3.f * k - 2.f * sp;
 }
 
-__device__ __forceinline__ float silu_fast(float x) { return x / (1.f + __expf(-x)); }
+// SiLU with the fast exponential and the fast division (two SFU operations
+// and a multiply; a few ulp, far below the split-BF16 products' 1e-5)
+__device__ __forceinline__ float silu_fast(float x) { return __fdividef(x, 1.f + __expf(-x)); }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -80,7 +82,9 @@ __device__ __forceinline__ float mlp_infer_warp(const uint32_t *frag, const floa
   const float *W1 = fw, *b1 = fw + 128, *b2 = fw + 192, *b3 = fw + 256, *W4 = fw + 320;
   const float b4 = fw[384];
   float out_lo[2], out_hi[2];
-#pragma unroll
+  // the two 16-sample tiles run as a loop (not unrolled): the body is large
+  // and is inlined into the step kernels, whose instruction cache it shares
+#pragma unroll 1
   for (int mt = 0; mt < 2; ++mt) {
     // inputs of rows g and g+8 of this 16-sample tile
     const float xa0 = __shfl_sync(0xffffffffu, x0, mt * 16 + g);

@@ -2021,7 +2021,7 @@ static cudaError_t launch_flag_list(qed_ctx *c, const uint8_t *flags, uint8_t wa
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_heavy_list, TILE, 0);
   if (e != cudaSuccess) return e;
-  per_sm = persistent_blocks_per_sm(c, per_sm);
+  per_sm = persistent_blocks_per_sm(c, per_sm, QED_TUNE_ORDER);
   k_heavy_list<<<c->num_sms * per_sm, TILE, 0, st>>>(h);
   c->launches += 1;
   return cudaGetLastError();
@@ -2032,7 +2032,7 @@ static cudaError_t launch_push(qed_ctx *c, const LeptonArgs<Real> &a, cudaStream
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lepton_push<Real, FM>, TILE, 0);
   if (e != cudaSuccess) return e;
-  per_sm = persistent_blocks_per_sm(c, per_sm);
+  per_sm = persistent_blocks_per_sm(c, per_sm, QED_TUNE_STREAM);
   k_lepton_push<Real, FM><<<c->num_sms * per_sm, TILE, 0, st>>>(a);
   c->launches += 1;
   return cudaGetLastError();
@@ -2042,7 +2042,7 @@ static cudaError_t launch_push(qed_ctx *c, const LeptonArgs<Real> &a, cudaStream
 // forward tables (and, when `mlp` is set, the learned sampler) in shared memory.
 template <class Real, class Kern>
 static cudaError_t launch_tables_kernel(qed_ctx *c, Kern kern, const LeptonArgs<Real> &a, bool mlp,
-                                        cudaStream_t st, size_t extra = 0) {
+                                        int group, cudaStream_t st, size_t extra = 0) {
   size_t sm = sizeof(Real) == 8 ? 0 : lepton_smem<Real>(c);
   if (sm && mlp) sm = ((sm + 15) & ~(size_t)15) + MLP_SMEM_BYTES;
   if (extra) sm = ((sm + 15) & ~(size_t)15) + extra;
@@ -2051,7 +2051,7 @@ static cudaError_t launch_tables_kernel(qed_ctx *c, Kern kern, const LeptonArgs<
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE, sm);
   if (e != cudaSuccess) return e;
-  per_sm = persistent_blocks_per_sm(c, per_sm);
+  per_sm = persistent_blocks_per_sm(c, per_sm, group);
   kern<<<c->num_sms * per_sm, TILE, sm, st>>>(a);
   c->launches += 1;
   return cudaGetLastError();
@@ -2064,7 +2064,7 @@ static cudaError_t launch_plain_kernel(qed_ctx *c, Kern kern, const LeptonArgs<R
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE, 0);
   if (e != cudaSuccess) return e;
-  per_sm = persistent_blocks_per_sm(c, per_sm);
+  per_sm = persistent_blocks_per_sm(c, per_sm, QED_TUNE_ORDER);
   kern<<<c->num_sms * per_sm, TILE, 0, st>>>(a);
   c->launches += 1;
   return cudaGetLastError();
@@ -2111,7 +2111,7 @@ static cudaError_t launch_sub_scan(qed_ctx *c, const int64_t *n_entries, int64_t
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sub_scan, TILE, 0);
   if (e != cudaSuccess) return e;
-  per_sm = persistent_blocks_per_sm(c, per_sm);
+  per_sm = persistent_blocks_per_sm(c, per_sm, QED_TUNE_ORDER);
   k_sub_scan<<<c->num_sms * per_sm, TILE, 0, st>>>(a);
   c->launches += 1;
   return cudaGetLastError();
@@ -2124,20 +2124,23 @@ static cudaError_t launch_sub_scan(qed_ctx *c, const int64_t *n_entries, int64_t
 template <class Real, int FM, int MODE>
 static cudaError_t launch_lepton_t(qed_ctx *c, const LeptonArgs<Real> &a, cudaStream_t st) {
   if (MODE == MODE_PUSH) return launch_push<Real, FM>(c, a, st);
-  cudaError_t e = launch_tables_kernel<Real>(c, k_lepton_stream<Real, FM, MODE>, a, false, st,
-                                             stream_prefetch_bytes<Real, FM>());
+  cudaError_t e = launch_tables_kernel<Real>(c, k_lepton_stream<Real, FM, MODE>, a, false,
+                                             QED_TUNE_STREAM, st, stream_prefetch_bytes<Real, FM>());
   if (e == cudaSuccess) e = prof_mark(c, 1, st);
   if (e == cudaSuccess) e = launch_class_lists(c, a.sp[0].d_n, a.nsp > 1 ? a.sp[1].d_n : nullptr, st);
   if (e == cudaSuccess) e = prof_mark(c, 2, st);
   if (e == cudaSuccess)
     e = a.use_mlp && sizeof(Real) == 4
-            ? launch_tables_kernel<Real>(c, k_substep_count<Real, FM, MODE, true>, a, true, st)
-            : launch_tables_kernel<Real>(c, k_substep_count<Real, FM, MODE, false>, a, false, st);
+            ? launch_tables_kernel<Real>(c, k_substep_count<Real, FM, MODE, true>, a, true,
+                                         QED_TUNE_CHAINS, st)
+            : launch_tables_kernel<Real>(c, k_substep_count<Real, FM, MODE, false>, a, false,
+                                         QED_TUNE_CHAINS, st);
   if (e == cudaSuccess) e = prof_mark(c, 3, st);
   if (e == cudaSuccess) e = launch_sub_scan(c, c->cls_off + NCLS, a.ph.d_n, a.ph.cap, nullptr, 0, st);
   if (e == cudaSuccess) e = prof_mark(c, 4, st);
   if (e == cudaSuccess) e = launch_plain_kernel<Real>(c, k_substep_write_coop<Real, FM, MODE>, a, st);
-  if (e == cudaSuccess) e = launch_tables_kernel<Real>(c, k_substep_replay<Real, FM, MODE>, a, false, st);
+  if (e == cudaSuccess)
+    e = launch_tables_kernel<Real>(c, k_substep_replay<Real, FM, MODE>, a, false, QED_TUNE_CHAINS, st);
   if (e == cudaSuccess) e = prof_mark(c, 5, st);
   return e;
 }
@@ -2207,7 +2210,7 @@ static cudaError_t launch_photon_t(qed_ctx *c, const PhotonArgs<Real> &a, cudaSt
   if (e != cudaSuccess) return e;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_photon_stream<Real, FM>, TILE, sm);
   if (e != cudaSuccess) return e;
-  per_sm = persistent_blocks_per_sm(c, per_sm);
+  per_sm = persistent_blocks_per_sm(c, per_sm, QED_TUNE_PHOTON);
   k_photon_stream<Real, FM><<<c->num_sms * per_sm, TILE, sm, st>>>(a);
   c->launches += 1;
   e = cudaGetLastError();
@@ -2217,7 +2220,7 @@ static cudaError_t launch_photon_t(qed_ctx *c, const PhotonArgs<Real> &a, cudaSt
   // pairs: counting pass, scan (advances both lepton counts), writing pass
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair_count<Real, FM>, TILE, sm);
   if (e != cudaSuccess) return e;
-  per_sm = persistent_blocks_per_sm(c, per_sm);
+  per_sm = persistent_blocks_per_sm(c, per_sm, QED_TUNE_PHOTON);
   k_pair_count<Real, FM><<<c->num_sms * per_sm, TILE, sm, st>>>(a);
   c->launches += 1;
   e = cudaGetLastError();
@@ -2225,7 +2228,7 @@ static cudaError_t launch_photon_t(qed_ctx *c, const PhotonArgs<Real> &a, cudaSt
   if (e != cudaSuccess) return e;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pair_write<Real, FM>, TILE, sm);
   if (e != cudaSuccess) return e;
-  per_sm = persistent_blocks_per_sm(c, per_sm);
+  per_sm = persistent_blocks_per_sm(c, per_sm, QED_TUNE_PHOTON);
   k_pair_write<Real, FM><<<c->num_sms * per_sm, TILE, sm, st>>>(a);
   c->launches += 1;
   return cudaGetLastError();
@@ -2272,7 +2275,7 @@ cudaError_t launch_compact(qed_ctx *c, const qed_species *s, cudaStream_t st) {
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_compact<Real>, COMPACT_TILE, 0);
   if (e != cudaSuccess) return e;
-  per_sm = persistent_blocks_per_sm(c, per_sm);
+  per_sm = persistent_blocks_per_sm(c, per_sm, QED_TUNE_COMPACT);
   k_compact<Real><<<c->num_sms * per_sm, COMPACT_TILE, 0, st>>>(a);
   c->launches += 1;
   return cudaGetLastError();
@@ -2337,7 +2340,7 @@ cudaError_t launch_sample_xi(qed_ctx *c, const float *chi, const float *gamma, f
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sample_xi, TILE, sm);
   if (e != cudaSuccess) return e;
-  per_sm = persistent_blocks_per_sm(c, per_sm);
+  per_sm = persistent_blocks_per_sm(c, per_sm, QED_TUNE_COMPACT);
   k_sample_xi<<<c->num_sms * per_sm, TILE, sm, st>>>(a);
   c->launches += 1;
   return cudaGetLastError();

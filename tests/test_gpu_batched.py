@@ -103,3 +103,30 @@ def test_autotuner_picks_a_factor(api):
     assert 1 <= best <= 8
     assert all(m > 0 for m in ms)
     assert ms[best - 1] == min(ms)
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_group_autotuner_picks_a_factor_per_kernel_group(api, order):
+    """qed_autotune_groups: one factor per kernel group, each the fastest of
+    the factors it timed; the chosen configuration is the one the context
+    keeps, and the steps it runs afterwards give the same particles as an
+    untuned context (launch sizes change no result)."""
+    from paper_1608_06356_gb300 import workloads as W
+    st = _runs(W, [50000, 20000])
+    n = len(st["x"])
+    ctx = api.qed_init_tables(api.config(dt=0.01, seed=2, append_order=order))
+    e, p, g = _species(api, st, n, cap_factor=8)
+    t = api.qed_autotune_groups(ctx, e, p, g, api.Fields.per_particle(), reps=2)
+    for name, f in t["grid_factor"].items():
+        ms = t["ms"][name]
+        assert 1 <= f <= 8 and all(m > 0 for m in ms), name
+        assert ms[f - 1] == min(ms), name
+    assert t["ms_per_step"] == min(t["ms"]["compact"])
+    out = []
+    for c in (ctx, api.qed_init_tables(api.config(dt=0.01, seed=2, append_order=order))):
+        e2, p2, g2 = _species(api, st, n, cap_factor=8)
+        api.qed_step_fused(c, e2, p2, g2, api.Fields.per_particle(), 5)
+        torch.cuda.synchronize()
+        out.append((e2.host(), g2.host()))
+    np.testing.assert_array_equal(out[0][0]["px"], out[1][0]["px"])
+    np.testing.assert_array_equal(np.sort(out[0][1]["id"]), np.sort(out[1][1]["id"]))

@@ -170,3 +170,44 @@ def test_fused_step_with_learned_sampler(api, W=None):
     o0, o1 = np.argsort(i0), np.argsort(i1)
     rel = np.abs(k1[o1] / k0[o0] - 1)
     assert np.median(rel) < 0.01
+
+
+def test_spectral_error_within_1e3_of_the_oracle(api, orc):
+    """The learned sampler after the benchmark's training (1.6e10 samples):
+    at 64 chi nodes over its domain [1e-3, 1e2] (gamma = 1e4), the bin
+    probabilities of 64 log bins of xi over [2/gamma, 1] that it implies --
+    found by bisection in u over the 2^32 words, so no sampling noise enters --
+    against the oracle's exact ones, the quadrature of Eq. (1) between the bin
+    edges normalised above xi_min: the largest relative error over bins with
+    probability >= 1e-3 is at most 1e-3.  The table path is held to 1e-4."""
+    import ctypes as C
+    import bench
+    mlp = _mlp()
+    ctx_tab = api.qed_init_tables(api.config())
+    ctx = api.qed_init_tables(api.config(sampler=1))
+    api.qed_mlp_load(ctx, mlp.init_params(seed=0).astype(np.float32))
+    api.qed_mlp_train(ctx, 16_000_000_000, lr=6e-3, seed=7)
+    gamma = 1e4
+    chis = np.exp(np.linspace(np.log(1e-3), np.log(1e2), 64))
+    edges = np.exp(np.linspace(np.log(2.0 / gamma), 0.0, 65))
+    P = C.POINTER(C.c_double)
+
+    def cum(a, b, chi):
+        a, b, chi = (np.ascontiguousarray(np.broadcast_to(v, np.shape(b)), dtype=np.float64)
+                     for v in (a, b, chi))
+        out = np.zeros_like(b)
+        orc.lib().orc_cum_photon_v(a.ctypes.data_as(P), b.ctypes.data_as(P), chi.ctypes.data_as(P),
+                                   out.ctypes.data_as(P), len(b))
+        return out
+
+    exact = np.zeros((len(chis), 64))
+    for j, c in enumerate(chis):
+        G = cum(0.0, edges, c)
+        G1 = cum(0.0, np.array([1.0]), c)[0]
+        exact[j] = np.diff(G) / (G1 - G[0])
+    big = exact >= 1e-3
+    for ctx_s, which, tol in ((ctx_tab, 0, 1e-4), (ctx, 2, 1e-3)):
+        u = bench.sampler_edge_u(api, torch, ctx_s, which, chis, edges, gamma)
+        rel = np.abs(np.diff(u, axis=1) - exact)[big] / exact[big]
+        print(f"sampler {which}: max {rel.max():.3e} median {np.median(rel):.3e}")
+        assert rel.max() <= tol, (which, rel.max())
