@@ -23,10 +23,11 @@
 //     written).  The others go
 //     to the warp's queue in shared memory (pushed momentum, fields, id,
 //     slot).
-//   heavy phase: when the queue holds 64 particles, the warp runs them with
+//   heavy phase: when the queue holds 32 particles, the warp runs them with
 //     the scheduler of the ordered counting pass -- lanes idle (refilled from
-//     the queue), scanning (up to 4 Method I draws per round) or pending (an
-//     event; the emitting lanes run together): the exact rate and N, the
+//     the queue), scanning (up to 8 Method I draws per round, two per Philox
+//     call) or pending (an event; the emitting lanes run together): the
+//     exact rate and N, the
 //     draws, xi, the recoil, the rate again for the remaining sub-steps.  An
 //     emission round reserves slots for its photons with one atomic on the
 //     photon count and writes them there.  A round runs only when enough
