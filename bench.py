@@ -681,14 +681,15 @@ def config_uniform_ensemble(api, torch, n=1 << 20, steps=200, compact_every=4, c
     B with isotropic directions and magnitudes log-uniform in [10, 2000];
     emission and Breit-Wheeler pairs, FP32 state (FP32 table look-ups, FP64
     chi where it cancels), Dt = 0.01, 200 steps; children inherit their
-    parent's fields.  Dead photons are removed every 4 steps (qed_compact_fill)."""
+    parent's fields; photons appended in any order (the single-pass lepton
+    step).  Dead photons are removed every 4 steps (qed_compact_fill)."""
     from paper_1608_06356_gb300 import workloads as W
     se = W.ensemble(n, seed=0)
     sg = W.ensemble(n, seed=1, photons=True, id0=1 << 32)
     f32 = lambda d: {k: (v.astype(np.float32) if v.dtype.kind == "f" else v) for k, v in d.items()}
     se, sg = f32(se), f32(sg)
     cap = 1 << 25
-    ctx = api.qed_init_tables(api.config(dt=DT, seed=3, max_particles=cap))
+    ctx = api.qed_init_tables(api.config(dt=DT, seed=3, max_particles=cap, append_order=APPEND_ORDER))
     e = api.Species.empty(cap, -1, fields=True).load(**se)
     p = api.Species.empty(cap, 1, fields=True)
     g = api.Species.empty(cap, 0, fields=True).load(**sg)
@@ -736,15 +737,15 @@ def config_3d_cascade(api, torch, steps=28, seed_n=1 << 24, cap=1 << 28, nx=256,
     counter-propagating circularly polarised standing waves of amplitude
     a0 = 800 each, filled on the device at every step's time; 16M electrons at
     rest, uniform in the central 64^3 cells; CIC gather + Boris + emission and
-    pairs with in-place appends into preallocated 256M-slot buffers per species,
-    FP32, Dt = 0.1.  The first `steps` of the 500-step run are timed (a slice):
+    pairs with in-place appends into preallocated 256M-slot buffers per species
+    (photons in any order: the single-pass lepton step), FP32, Dt = 0.1.  The first `steps` of the 500-step run are timed (a slice):
     the particle count grows and the step cost with it.  Grid bytes: the field
     fill (32 B per node written) plus one read of the touched nodes' 32 B."""
     from paper_1608_06356_gb300 import workloads as W
     dx = 2 * np.pi / 32
     st = W.cascade_seed(seed_n, seed=0, nx=nx, dx=dx)
     st = {k: (v.astype(np.float32) if v.dtype.kind == "f" else v) for k, v in st.items()}
-    ctx = api.qed_init_tables(api.config(dt=dt, seed=9, max_particles=cap))
+    ctx = api.qed_init_tables(api.config(dt=dt, seed=9, max_particles=cap, append_order=APPEND_ORDER))
     e = api.Species.empty(cap, -1).load(**st)
     p = api.Species.empty(cap, 1)
     g = api.Species.empty(cap, 0)

@@ -361,27 +361,52 @@ int qed_autotune(qed_ctx *ctx, const qed_species *e, const qed_species *p, const
  *   QED_TUNE_COMPACT  stable compaction and the isolated sampler */
 enum { QED_TUNE_STREAM = 0, QED_TUNE_CHAINS = 1, QED_TUNE_ORDER = 2, QED_TUNE_PHOTON = 3,
        QED_TUNE_COMPACT = 4, QED_TUNE_GROUPS = 5, QED_TUNE_MAX_FACTOR = 8 };
+
+/* Scheduling of the Method I chains of the deferred leptons, run a warp at a
+ * time with lanes in states (idle, rate, scanning, event pending) and one
+ * state per round (the single-pass kernel's heavy phase, and the ordered
+ * counting pass).  0 = the default, in brackets:
+ *   QED_SCHED_EMIT_LANES     an emission round waits for this many lanes with
+ *                            an event, 1..32 [16] (both paths)
+ *   QED_SCHED_ROUND_LANES    a rate or scanning round of the single pass runs
+ *                            with at least this many lanes, 1..32 [8]
+ *   QED_SCHED_SCAN_DRAWS     Method I sub-steps drawn per lane per scanning
+ *                            round, 2..16, even [4] (both paths; the single
+ *                            pass draws four at a time)
+ *   QED_SCHED_SCAN_LEFT      a scanning round of the single pass ends when
+ *                            fewer lanes are still drawing, 1..32 [8]
+ *   QED_SCHED_QUEUE_TRIGGER  queued deferred leptons that start a heavy phase
+ *                            of the single pass, 1..33 [32]
+ * The results (particles, photons, counters) do not depend on them. */
+enum { QED_SCHED_EMIT_LANES = 0, QED_SCHED_ROUND_LANES = 1, QED_SCHED_SCAN_DRAWS = 2,
+       QED_SCHED_SCAN_LEFT = 3, QED_SCHED_QUEUE_TRIGGER = 4, QED_SCHED_PARAMS = 5,
+       QED_SCHED_MAX_CANDIDATES = 6 };
 typedef struct {
   int grid_factor[QED_TUNE_GROUPS]; /* CTAs per SM per group; 0 = as many as fit */
-  int pad_;
+  int sched[QED_SCHED_PARAMS];      /* chain scheduling (QED_SCHED_*); 0 = default */
   double ms_per_step;               /* one fused step + qed_compact_fill of the photons,
-                                       with the chosen factors */
+                                       with the chosen values */
   double ms[QED_TUNE_GROUPS][QED_TUNE_MAX_FACTOR]; /* per group, per factor 1..8 (the
                                        other groups at their values then; a factor beyond
                                        what fits runs as what fits) */
+  int sched_tried[QED_SCHED_PARAMS][QED_SCHED_MAX_CANDIDATES]; /* candidate values of each
+                                       scheduling parameter, in the order tried (0 = none) */
+  double sched_ms[QED_SCHED_PARAMS][QED_SCHED_MAX_CANDIDATES]; /* their times */
 } qed_tuning;
 
-/* Autotuner by kernel group: for each group in turn (the order above), times
- * `reps` fused steps plus qed_compact_fill of the photons for every factor that
- * fits (1..8 CTAs per SM), keeping the best before tuning the next group.  The
- * species are advanced -- pass disposable copies.  The chosen factors are kept
- * in the context for all later launches and written, with the timings, to
- * *out (host).  Synchronous. */
+/* Autotuner by kernel group and chain scheduling: for each group in turn (the
+ * order above), times `reps` fused steps plus qed_compact_fill of the photons
+ * for every factor that fits (1..8 CTAs per SM), keeping the best before
+ * tuning the next group; then each scheduling parameter in turn over a fixed
+ * list of candidates.  The species are advanced -- pass disposable copies.
+ * The chosen values are kept in the context for all later launches and
+ * written, with the timings, to *out (host).  Synchronous. */
 int qed_autotune_groups(qed_ctx *ctx, const qed_species *e, const qed_species *p,
                         const qed_species *g, const qed_fields *f, int reps, qed_tuning *out,
                         qed_stream_t stream);
 
-/* Apply stored factors (grid_factor of *t; ms fields ignored). */
+/* Apply stored values (grid_factor and sched of *t; the timing fields are
+ * ignored).  QED_ERR_ARG, and nothing applied, if a value is out of range. */
 int qed_set_tuning(qed_ctx *ctx, const qed_tuning *t);
 
 /* Measurement hooks.  qed_profile_begin creates CUDA events (call it outside

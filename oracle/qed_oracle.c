@@ -634,7 +634,8 @@ static void emit_photon(const orc_config *cfg, const orc_species *s, int64_t i, 
 /* One lepton: gather, Boris push, then the photon event generator.  Emitted
  * photons go to *out in emission order.
  * Method I (default): W_rad with sub-steps N = max(1, ceil(W Dt / 0.2)); in
- *   sub-step k a photon is emitted if W Dt/N > r1.
+ *   sub-step k a photon is emitted if W Dt/N > r1, with r1 and r2 words 0 and
+ *   1 (k even) or 2 and 3 (k odd) of the emission draw of sub index k / 2.
  * Methods II and III (the paper's alternatives, text around Fig. 2): the
  *   particle carries a cumulative probability P_cum and a random number r3
  *   taken when it first needs one (Philox word 3 of its emission draw).  Each
@@ -680,10 +681,13 @@ static void lepton_one(const orc_config *cfg, const orc_fields *f, orc_species *
   double dts = cfg->dt / (double)N;
   *substeps += N;
   for (int64_t k = 0; k < N; ++k) {
+    /* sub-steps 2j and 2j+1 share the draw (id, step, j, emission): r1, r2
+     * are its words 0, 1 for the even sub-step and 2, 3 for the odd one */
     uint32_t r[4];
-    orc_draw(cfg->seed, s->id[i], step, k, ORC_STREAM_EMIT, r);
-    if (!(W * dts > orc_u(r[0]))) continue;
-    emit_photon(cfg, s, i, step, k, chi, orc_u(r[1]), orc_uc(r[1]), E, B, p, &g, out);
+    orc_draw(cfg->seed, s->id[i], step, k / 2, ORC_STREAM_EMIT, r);
+    const uint32_t *w = r + 2 * (k % 2);
+    if (!(W * dts > orc_u(w[0]))) continue;
+    emit_photon(cfg, s, i, step, k, chi, orc_u(w[1]), orc_uc(w[1]), E, B, p, &g, out);
     chi = orc_chi_lepton(p, E, B, cfg->a_S);
     W = orc_rate_photon(cfg, chi, g);
   }

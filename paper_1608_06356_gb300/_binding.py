@@ -76,12 +76,16 @@ class qed_counters(C.Structure):
 
 QED_TUNE_GROUPS, QED_TUNE_MAX_FACTOR = 5, 8
 TUNE_GROUP_NAMES = ("stream", "chains", "order", "photon", "compact")
+QED_SCHED_PARAMS, QED_SCHED_MAX_CANDIDATES = 5, 6
+SCHED_NAMES = ("emit_lanes", "round_lanes", "scan_draws", "scan_left", "queue_trigger")
 
 
 class qed_tuning(C.Structure):
-    _fields_ = [("grid_factor", C.c_int * QED_TUNE_GROUPS), ("pad_", C.c_int),
+    _fields_ = [("grid_factor", C.c_int * QED_TUNE_GROUPS), ("sched", C.c_int * QED_SCHED_PARAMS),
                 ("ms_per_step", C.c_double),
-                ("ms", (C.c_double * QED_TUNE_MAX_FACTOR) * QED_TUNE_GROUPS)]
+                ("ms", (C.c_double * QED_TUNE_MAX_FACTOR) * QED_TUNE_GROUPS),
+                ("sched_tried", (C.c_int * QED_SCHED_MAX_CANDIDATES) * QED_SCHED_PARAMS),
+                ("sched_ms", (C.c_double * QED_SCHED_MAX_CANDIDATES) * QED_SCHED_PARAMS)]
 
 
 # name -> (restype, argtypes); the exported C ABI, one entry per declaration

@@ -423,21 +423,31 @@ def qed_autotune(ctx: Context, e: Species, p: Species, g: Species, f, reps: int 
 
 def qed_autotune_groups(ctx: Context, e: Species, p: Species, g: Species, f, reps: int = 2,
                         stream=None) -> dict:
-    """Tune the CTAs per SM of each kernel group on disposable species (they
-    are advanced).  Returns {"grid_factor": {group: factor}, "ms_per_step": ..,
-    "ms": {group: [ms per factor 1..8]}}; the factors stay in the context."""
+    """Tune the CTAs per SM of each kernel group, then the Method I chain
+    scheduling, on disposable species (they are advanced).  Returns
+    {"grid_factor": {group: factor}, "sched": {parameter: value},
+    "ms_per_step": .., "ms": {group: [ms per factor 1..8]},
+    "sched_ms": {parameter: {value: ms}}}; the values stay in the context."""
     t = B.qed_tuning()
     B.check(B.lib().qed_autotune_groups(ctx.handle, C.byref(e.struct()), C.byref(p.struct()),
                                         C.byref(g.struct()), C.byref(f), int(reps), C.byref(t),
                                         _stream(stream)), "qed_autotune_groups")
     return {"grid_factor": {n: int(t.grid_factor[k]) for k, n in enumerate(B.TUNE_GROUP_NAMES)},
+            "sched": {n: int(t.sched[k]) for k, n in enumerate(B.SCHED_NAMES)},
             "ms_per_step": t.ms_per_step,
             "ms": {n: [float(t.ms[k][j]) for j in range(B.QED_TUNE_MAX_FACTOR)]
-                   for k, n in enumerate(B.TUNE_GROUP_NAMES)}}
+                   for k, n in enumerate(B.TUNE_GROUP_NAMES)},
+            "sched_ms": {n: {int(t.sched_tried[k][j]): float(t.sched_ms[k][j])
+                             for j in range(B.QED_SCHED_MAX_CANDIDATES) if t.sched_tried[k][j]}
+                         for k, n in enumerate(B.SCHED_NAMES)}}
 
 
-def qed_set_tuning(ctx: Context, grid_factor: dict) -> None:
+def qed_set_tuning(ctx: Context, grid_factor: dict, sched: dict | None = None) -> None:
+    """Set the CTAs per SM of kernel groups ({group: factor}) and the chain
+    scheduling ({parameter: value}); absent entries and 0 mean the default."""
     t = B.qed_tuning()
     for k, n in enumerate(B.TUNE_GROUP_NAMES):
         t.grid_factor[k] = int(grid_factor.get(n, 0))
+    for k, n in enumerate(B.SCHED_NAMES):
+        t.sched[k] = int((sched or {}).get(n, 0))
     B.check(B.lib().qed_set_tuning(ctx.handle, C.byref(t)), "qed_set_tuning")

@@ -192,8 +192,9 @@ extern "C" int qed_autotune_groups(qed_ctx *c, const qed_species *e, const qed_s
   cudaEvent_t a, b;
   if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return QED_ERR_CUDA;
   memset(out, 0, sizeof(*out));
-  int saved[QED_TUNE_GROUPS];
+  int saved[QED_TUNE_GROUPS], saved_sched[QED_SCHED_PARAMS];
   memcpy(saved, c->grid_factor, sizeof(saved));
+  memcpy(saved_sched, c->sched, sizeof(saved_sched));
   int64_t step = 2000000;
   int rc = QED_OK;
   double best_ms = 1e300;
@@ -212,22 +213,46 @@ extern "C" int qed_autotune_groups(qed_ctx *c, const qed_species *e, const qed_s
     c->grid_factor[grp] = best;
     best_ms = best_g;
   }
+  // then the chain scheduling, one parameter at a time over fixed candidates
+  // (the first of each list is its default)
+  static const int cand[QED_SCHED_PARAMS][QED_SCHED_MAX_CANDIDATES] = {
+      {16, 8, 12, 20, 24, 0}, {8, 4, 12, 16, 0, 0}, {4, 2, 8, 12, 0, 0},
+      {8, 1, 4, 12, 16, 0},   {32, 16, 24, 33, 0, 0}};
+  for (int k = 0; k < QED_SCHED_PARAMS && rc == QED_OK; ++k) {
+    int best = cand[k][0];
+    double best_k = 1e300;
+    for (int j = 0; j < QED_SCHED_MAX_CANDIDATES && cand[k][j] && rc == QED_OK; ++j) {
+      c->sched[k] = cand[k][j];
+      double per = 0.0;
+      rc = time_steps(c, e, p, g, f, reps, step, a, b, st, &per);
+      if (rc != QED_OK) break;
+      out->sched_tried[k][j] = cand[k][j];
+      out->sched_ms[k][j] = per;
+      if (per < best_k) { best_k = per; best = cand[k][j]; }
+    }
+    c->sched[k] = best;
+    if (best_k < best_ms) best_ms = best_k;
+  }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (rc != QED_OK) {
     memcpy(c->grid_factor, saved, sizeof(saved));
+    memcpy(c->sched, saved_sched, sizeof(saved_sched));
     return rc;
   }
   memcpy(out->grid_factor, c->grid_factor, sizeof(out->grid_factor));
+  memcpy(out->sched, c->sched, sizeof(out->sched));
   out->ms_per_step = best_ms;
   return QED_OK;
 }
 
 extern "C" int qed_set_tuning(qed_ctx *c, const qed_tuning *t) {
   if (!c || !t) return QED_ERR_ARG;
-  for (int k = 0; k < QED_TUNE_GROUPS; ++k) {
+  for (int k = 0; k < QED_TUNE_GROUPS; ++k)
     if (t->grid_factor[k] < 0 || t->grid_factor[k] > 64) return QED_ERR_ARG;
-    c->grid_factor[k] = t->grid_factor[k];
-  }
+  for (int k = 0; k < QED_SCHED_PARAMS; ++k)
+    if (!sched_valid(k, t->sched[k])) return QED_ERR_ARG;
+  memcpy(c->grid_factor, t->grid_factor, sizeof(c->grid_factor));
+  memcpy(c->sched, t->sched, sizeof(c->sched));
   return QED_OK;
 }

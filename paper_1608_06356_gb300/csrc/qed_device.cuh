@@ -38,6 +38,15 @@ __device__ __forceinline__ U4 draw(uint64_t seed, uint64_t id, int64_t step, int
   return philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
 }
 
+// Method I words of an emission chain: sub-steps 2j and 2j+1 share the draw
+// (id, step, j, emission); sub-step 2j takes r1 and r2 from its words 0 and 1,
+// sub-step 2j+1 from its words 2 and 3.
+struct EmitWords { uint32_t r1, r2; };
+__device__ __forceinline__ EmitWords emit_words(uint64_t seed, uint64_t id, int64_t step, int64_t k) {
+  const U4 r = draw(seed, id, step, k >> 1, STREAM_EMIT);
+  return (k & 1) ? EmitWords{r.z, r.w} : EmitWords{r.x, r.y};
+}
+
 // u = (w + 1/2) 2^-32 in (0,1) and its complement (~w + 1/2) 2^-32.
 template <class Real> __device__ __forceinline__ Real unif(uint32_t w);
 template <> __device__ __forceinline__ double unif<double>(uint32_t w) {

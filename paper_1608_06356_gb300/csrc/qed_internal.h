@@ -69,6 +69,8 @@ struct qed_ctx {
   // persistent-grid occupancy factor per kernel group (QED_TUNE_*; 0 = as
   // many CTAs per SM as fit)
   int grid_factor[QED_TUNE_GROUPS];
+  // Method I chain scheduling (QED_SCHED_*; 0 = default)
+  int sched[QED_SCHED_PARAMS];
   // bound of the photon emission rate used by the single-pass lepton kernel:
   // W_rad <= w_up_row[j] chi / gamma for ln chi >= row j of the rate table
   float *w_up_row;  // [gl.n] (device)
@@ -88,6 +90,30 @@ inline int persistent_blocks_per_sm(const qed_ctx *c, int occupancy, int group) 
   const int f = c->grid_factor[group];
   if (f > 0 && f < b) b = f;
   return b;
+}
+// Defaults of the chain-scheduling parameters (QED_SCHED_*), and a
+// parameter of the context or its default.
+constexpr int SCHED_DEF_EMIT_LANES = 16, SCHED_DEF_ROUND_LANES = 8, SCHED_DEF_SCAN_DRAWS = 4,
+              SCHED_DEF_SCAN_LEFT = 8, SCHED_DEF_QUEUE_TRIGGER = 32;
+inline int sched_default(int k) {
+  switch (k) {
+    case QED_SCHED_EMIT_LANES: return SCHED_DEF_EMIT_LANES;
+    case QED_SCHED_ROUND_LANES: return SCHED_DEF_ROUND_LANES;
+    case QED_SCHED_SCAN_DRAWS: return SCHED_DEF_SCAN_DRAWS;
+    case QED_SCHED_SCAN_LEFT: return SCHED_DEF_SCAN_LEFT;
+    default: return SCHED_DEF_QUEUE_TRIGGER;
+  }
+}
+inline int sched_param(const qed_ctx *c, int k) {
+  const int v = c->sched[k];
+  return v > 0 ? v : sched_default(k);
+}
+// Is v a valid value (0 = default) of scheduling parameter k?
+inline bool sched_valid(int k, int v) {
+  static const int hi[QED_SCHED_PARAMS] = {32, 32, 16, 32, 33};
+  if (v == 0) return true;
+  if (v < 1 || v > hi[k]) return false;
+  return k != QED_SCHED_SCAN_DRAWS || (v >= 2 && v % 2 == 0);
 }
 // Event marks of a profiled fused step: 0 start, 1 after the lepton
 // streaming pass, 2 after the class list, 3 after the counting pass, 4 after

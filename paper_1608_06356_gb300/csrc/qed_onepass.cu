@@ -23,12 +23,15 @@
 //     written).  The others go
 //     to the warp's queue in shared memory (pushed momentum, fields, id,
 //     slot).
-//   heavy phase: when the queue holds 32 particles, the warp runs them with
-//     the scheduler of the ordered counting pass -- lanes idle (refilled from
-//     the queue), scanning (up to 8 Method I draws per round, two per Philox
-//     call) or pending (an event; the emitting lanes run together): the
-//     exact rate and N, the
-//     draws, xi, the recoil, the rate again for the remaining sub-steps.  An
+//   heavy phase: when the queue holds 32 particles (a scheduling parameter,
+//     as are the lane counts below), the warp runs them with
+//     a per-warp scheduler of lane states -- idle; rate (chi and the exact
+//     rate, and N for a new particle; idle lanes are refilled from the queue
+//     at the start of such a round); scanning (Method I draws, two
+//     independent Philox chains interleaved, up to 8 per round, the round
+//     ending early when fewer than 8 lanes are still drawing); or pending (an
+//     event; the emitting lanes run together: xi, the recoil, the photon;
+//     then the rate again for the remaining sub-steps).  An
 //     emission round reserves slots for its photons with one atomic on the
 //     photon count and writes them there.  A round runs only when enough
 //     lanes are in its state (16 for an emission, 8 otherwise); when none can,
@@ -53,9 +56,7 @@ namespace {
 constexpr int OP_THREADS = 128;
 constexpr int OP_WARPS = OP_THREADS / 32;
 constexpr int QCAP = 64;       // queue entries per warp
-constexpr int QTRIG = 32;      // a heavy phase starts when the queue holds this many
-constexpr int QEXIT = QCAP - 32;  // ... and may end once it holds at most this many
-constexpr int MIN_LANES = 8;   // below this many lanes a round is deferred (lanes parked)
+constexpr int QEXIT = QCAP - 32;  // a heavy phase may end once the queue holds at most this many
 constexpr int QF = 9;          // queue floats per entry: px py pz ex ey ez bx by bz
 constexpr int PF = 17;         // parked floats per lane
 constexpr int PU = 9;          // parked words per lane
@@ -74,6 +75,13 @@ struct OnePassArgs {
   float chi_tab_lo, chi_tab_hi;  // chi range of the rate tables
   const uint32_t *mlp_frag;
   const float *mlp_w;
+  // chain scheduling (QED_SCHED_*): an emission round waits for emit_lanes
+  // lanes with an event, a rate or scanning round runs with at least
+  // round_lanes lanes, a scanning round draws scan_iters times four
+  // sub-steps per lane and ends early when fewer than scan_left lanes are
+  // still drawing; a heavy phase starts when the queue holds qtrig entries
+  // (qtrig - 1 + 32 <= QCAP)
+  int emit_lanes, round_lanes, scan_iters, scan_left, qtrig;
 };
 
 // dynamic shared memory: prefetch buffers, per-warp queues and park areas
@@ -101,11 +109,6 @@ template <int FM> __host__ __device__ size_t onepass_layout(const OnePassArgs &a
 enum { ST_IDLE = 0, ST_RATE = 1, ST_SCAN = 2, ST_PEND = 3, ST_DONE = 4, ST_PEND_NET = 5 };
 constexpr int CNT_MIN_NET = 24;  // lanes an emission round through the network waits for
 
-// heavy-phase scheduling (as in the ordered counting pass): an emission round
-// waits for this many pending lanes; a scanning round draws up to this many
-// sub-steps per lane
-constexpr int CNT_MIN_EMIT_OP = 16;
-constexpr int CNT_SCAN_DRAWS_OP = 8;
 
 // N = max(1, ceil(W Dt / wdt_max)), capped at max_substeps (status bit).
 __device__ __forceinline__ int64_t substep_count_op(const Consts &C, float W, float dt, float wdt_max,
@@ -120,8 +123,15 @@ __device__ __forceinline__ int64_t substep_count_op(const Consts &C, float W, fl
   return (int64_t)nn;
 }
 
-template <int FM, int MODE, bool MLP>
+// DEF: the default chain scheduling as compile-time constants (the runtime
+// values cost ~3.5% of the kernel's time); otherwise the values in A.
+template <int FM, int MODE, bool MLP, bool DEF>
 __global__ void __launch_bounds__(OP_THREADS, MLP ? 3 : 5) k_lepton_onepass(OnePassArgs A) {
+  const int emit_lanes = DEF ? SCHED_DEF_EMIT_LANES : A.emit_lanes;
+  const int round_lanes = DEF ? SCHED_DEF_ROUND_LANES : A.round_lanes;
+  const int scan_iters = DEF ? (SCHED_DEF_SCAN_DRAWS + 3) / 4 : A.scan_iters;
+  const int scan_left = DEF ? SCHED_DEF_SCAN_LEFT : A.scan_left;
+  const int qtrig = DEF ? SCHED_DEF_QUEUE_TRIGGER : A.qtrig;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ BlockTally bt;
   __shared__ long long s_meta[4];
@@ -208,29 +218,27 @@ __global__ void __launch_bounds__(OP_THREADS, MLP ? 3 : 5) k_lepton_onepass(OneP
       const unsigned scan = __ballot_sync(0xFFFFFFFFu, st == ST_SCAN);
       const unsigned pend = __ballot_sync(0xFFFFFFFFu, st == ST_PEND);
       const unsigned pnet = MLP ? __ballot_sync(0xFFFFFFFFu, st == ST_PEND_NET) : 0u;
-      const bool more = qn > 0;
       const int ni = __popc(idle), nr = __popc(rate), ns = __popc(scan), np = __popc(pend);
       const int nn = __popc(pnet);
+      // idle lanes are refilled from the queue at the start of a rate round
+      const int take = min(qn, ni);
       // a round runs only with enough lanes in its state; otherwise the warp
       // goes back to streaming (once the queue has room for another slice)
       // and the chains wait, parked, for the next heavy phase -- except in
       // the final drain, which runs whatever is left
       int phase;
-      if (np >= CNT_MIN_EMIT_OP) phase = ST_PEND;
+      if (np >= emit_lanes) phase = ST_PEND;
       else if (MLP && nn >= CNT_MIN_NET) phase = ST_PEND_NET;
-      else if (nr >= MIN_LANES) phase = ST_RATE;
-      else if (more && ni >= MIN_LANES) phase = ST_IDLE;
-      else if (ns >= MIN_LANES) phase = ST_SCAN;
+      else if (nr + take >= round_lanes) phase = ST_RATE;
+      else if (ns >= round_lanes) phase = ST_SCAN;
       else if (!final_drain && qn <= QEXIT) break;
-      else if (more && ni) phase = ST_IDLE;
-      else if (nr) phase = ST_RATE;
+      else if (nr + take) phase = ST_RATE;
       else if (ns) phase = ST_SCAN;
       else if (np) phase = ST_PEND;
       else if (MLP && nn) phase = ST_PEND_NET;
       else break;
-      if (phase == ST_IDLE) {
+      if (phase == ST_RATE) {
         // refill: idle lanes take queue entries from the top, in lane order
-        const int take = min(qn, ni);
         if (st == ST_IDLE) {
           const int r = __popc(idle & lt_mask);
           if (r < take) {
@@ -253,7 +261,6 @@ __global__ void __launch_bounds__(OP_THREADS, MLP ? 3 : 5) k_lepton_onepass(OneP
           }
         }
         qn -= take;
-      } else if (phase == ST_RATE) {
         // chi (Eq. 2) and the exact rate; a new particle also gets N
         if (st == ST_RATE) {
           chi = chi_lepton(px, py, pz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
@@ -267,24 +274,38 @@ __global__ void __launch_bounds__(OP_THREADS, MLP ? 3 : 5) k_lepton_onepass(OneP
           st = ST_SCAN;
         }
       } else if (phase == ST_SCAN) {
-        if (st == ST_SCAN) {
-          // draws two sub-steps at a time (independent Philox chains run
-          // interleaved); the second is used only if the first has no event
-          const float thr = ro.W * dts;
-          for (int s = 0; s < CNT_SCAN_DRAWS_OP; s += 2) {
-            const U4 ra = draw(A.C.seed, pid, step_, k, STREAM_EMIT);
-            const U4 rb = draw(A.C.seed, pid, step_, k + 1, STREAM_EMIT);
-            if (thr > unif<float>(ra.x)) { wy = ra.y; st = ST_PEND; break; }
-            if (++k >= N) { st = ST_DONE; break; }
-            if (thr > unif<float>(rb.x)) { wy = rb.y; st = ST_PEND; break; }
-            if (++k >= N) { st = ST_DONE; break; }
+        // draws two sub-steps at a time (independent Philox chains run
+        // interleaved; the second is used only if the first has no event),
+        // for as long as enough lanes are still drawing: the others keep
+        // their state for a later round
+        const float thr = ro.W * dts;
+        const bool was_scan = st == ST_SCAN;
+        bool drawing = was_scan;
+        for (int it = 0; it < scan_iters; ++it) {
+          if (drawing) {
+            // sub-steps 2j .. 2j+3 from the draws j and j+1 (words 0-1 and
+            // 2-3 of each); a chain at an odd sub-step starts at 2j+1
+            const int64_t j = k >> 1;
+            const U4 ra = draw(A.C.seed, pid, step_, j, STREAM_EMIT);
+            const U4 rb = draw(A.C.seed, pid, step_, j + 1, STREAM_EMIT);
+            const uint32_t w1[4] = {ra.x, ra.z, rb.x, rb.z}, w2[4] = {ra.y, ra.w, rb.y, rb.w};
+            const int q0 = (int)(k & 1);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              if (q >= q0 && st == ST_SCAN) {
+                if (thr > unif<float>(w1[q])) { wy = w2[q]; st = ST_PEND; }
+                else if (++k >= N) { st = ST_DONE; }
+              }
+            }
+            drawing = st == ST_SCAN;
           }
-          if (MLP && st == ST_PEND && N == 1) {  // does the network give this xi?
-            const float kap = photon_kappa(ro.kmin, unif<float>(wy), unif<float>(~wy));
-            const float lchi = chi > 0.f ? logf(chi) : MLP_L_LO - 1.f;
-            if (lchi >= MLP_L_LO && lchi <= MLP_L_HI && kap >= MLP_K_LO && kap <= MLP_K_HI)
-              st = ST_PEND_NET;
-          }
+          if (__popc(__ballot_sync(0xFFFFFFFFu, drawing)) < scan_left) break;
+        }
+        if (MLP && was_scan && st == ST_PEND && N == 1) {  // does the network give this xi?
+          const float kap = photon_kappa(ro.kmin, unif<float>(wy), unif<float>(~wy));
+          const float lchi = chi > 0.f ? logf(chi) : MLP_L_LO - 1.f;
+          if (lchi >= MLP_L_LO && lchi <= MLP_L_HI && kap >= MLP_K_LO && kap <= MLP_K_HI)
+            st = ST_PEND_NET;
         }
       } else {
         // emission by every lane with an event of this round's kind (warp-
@@ -487,7 +508,7 @@ __global__ void __launch_bounds__(OP_THREADS, MLP ? 3 : 5) k_lepton_onepass(OneP
     } else {
       cp_async_wait<0>();
     }
-    if (qn >= QTRIG || !streaming) {
+    if (qn >= qtrig || !streaming) {
       __syncwarp();  // queue entries and the pushed state written above are visible to the warp
       heavy_phase(!streaming);
     }
@@ -525,7 +546,9 @@ template <int FM, int MODE, bool MLP>
 cudaError_t launch_onepass_t(qed_ctx *c, const OnePassArgs &a, cudaStream_t st) {
   size_t off[5];
   const size_t sm = onepass_layout<FM>(a, MLP, off);
-  auto kern = k_lepton_onepass<FM, MODE, MLP>;
+  bool dflt = true;
+  for (int k = 0; k < QED_SCHED_PARAMS; ++k) dflt = dflt && sched_param(c, k) == sched_default(k);
+  auto kern = dflt ? k_lepton_onepass<FM, MODE, MLP, true> : k_lepton_onepass<FM, MODE, MLP, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
@@ -568,6 +591,11 @@ cudaError_t launch_lepton_onepass(qed_ctx *c, const qed_species *s0, const qed_s
   a.chi_tab_hi = (float)exp(c->gl.hi);
   a.mlp_frag = c->mlp_frag;
   a.mlp_w = c->mlp_w;
+  a.emit_lanes = sched_param(c, QED_SCHED_EMIT_LANES);
+  a.round_lanes = sched_param(c, QED_SCHED_ROUND_LANES);
+  a.scan_iters = (sched_param(c, QED_SCHED_SCAN_DRAWS) + 3) / 4;
+  a.scan_left = sched_param(c, QED_SCHED_SCAN_LEFT);
+  a.qtrig = min(sched_param(c, QED_SCHED_QUEUE_TRIGGER), QCAP - 31);
   const bool mlp = c->cfg.sampler == QED_SAMPLER_MLP && c->mlp_ready;
   if (mode == MODE_EMIT)
     return mlp ? launch_onepass_m<MODE_EMIT, true>(c, a, f->mode, st)

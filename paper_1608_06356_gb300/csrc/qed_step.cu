@@ -75,6 +75,7 @@ template <class Real> struct LeptonArgs {
   const uint32_t *mlp_frag; // learned inverse CDF (used when use_mlp)
   const float *mlp_w;
   int use_mlp;
+  int emit_lanes, scan_draws;  // chain scheduling (QED_SCHED_EMIT_LANES, _SCAN_DRAWS)
 };
 
 
@@ -327,9 +328,10 @@ constexpr int REC = SUB_REC;
 // (drawing sub-steps) or pending (an event found, its emission not yet done).
 enum { LS_IDLE = 0, LS_SCAN = 1, LS_PEND = 2 };
 constexpr int CNT_CHUNK = 64;       // entries per queue chunk of a warp
-constexpr int CNT_MIN_EMIT = 16;    // an emission round waits for this many lanes ...
-constexpr int CNT_MIN_INIT = 20;    // ... a refill round for this many idle lanes
-constexpr int CNT_SCAN_DRAWS = 4;   // draws per lane per scanning round
+// An emission round waits for A.emit_lanes lanes with an event, a refill
+// round for CNT_MIN_INIT idle lanes; a scanning round draws A.scan_draws
+// sub-steps per lane.
+constexpr int CNT_MIN_INIT = 20;
 
 // A class-list entry's particle after the push.  Entry e >= 0 is staging
 // record e (written by the streaming pass, which has also stored the pushed
@@ -498,7 +500,7 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 && !MLP ? 3 : 2) k_sub
     // enough lanes wait for it, refills once enough lanes are idle, else
     // draws; the fall-backs guarantee progress
     int phase;
-    if (__popc(pend) >= CNT_MIN_EMIT) phase = LS_PEND;
+    if (__popc(pend) >= A.emit_lanes) phase = LS_PEND;
     else if (more && __popc(idle) >= CNT_MIN_INIT) phase = LS_IDLE;
     else if (scan) phase = LS_SCAN;
     else if (pend) phase = LS_PEND;
@@ -544,11 +546,17 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 && !MLP ? 3 : 2) k_sub
       }
       next += __popc(idle);
     } else if (phase == LS_SCAN) {
-      // Method I draws until an event or the last sub-step
+      // Method I draws until an event or the last sub-step; one Philox call
+      // gives the words of two sub-steps (2j and 2j+1)
       if (state == LS_SCAN) {
-        for (int s = 0; s < CNT_SCAN_DRAWS; ++s) {
-          const U4 r = draw(A.C.seed, pid, step_, k, STREAM_EMIT);
-          if (ro.W * dts > unif<Real>(r.x)) { wy = r.y; state = LS_PEND; break; }
+        const Real thr = ro.W * dts;
+        for (int s = 0; s < A.scan_draws; s += 2) {
+          const U4 r = draw(A.C.seed, pid, step_, k >> 1, STREAM_EMIT);
+          if (!(k & 1)) {
+            if (thr > unif<Real>(r.x)) { wy = r.y; state = LS_PEND; break; }
+            if (++k >= N) { finish(); break; }
+          }
+          if (thr > unif<Real>(r.z)) { wy = r.w; state = LS_PEND; break; }
           if (++k >= N) { finish(); break; }
         }
       }
@@ -872,9 +880,9 @@ __global__ void __launch_bounds__(TILE, 2) k_substep_replay(LeptonArgs<Real> A) 
     const Real dts = dt / (Real)N;
     uint32_t j = 0;
     for (int64_t kk = 0; kk < N && j < cnt; ++kk) {
-      U4 r = draw(A.C.seed, P.id, step_, kk, STREAM_EMIT);
-      if (!forced && !(ro.W * dts > unif<Real>(r.x))) continue;
-      XiOut<Real> xo = photon_xi(A.T.Y, A.T, ro.l, chi, ro.kmin, unif<Real>(r.y), unif<Real>(~r.y), dummy);
+      const EmitWords r = emit_words(A.C.seed, P.id, step_, kk);
+      if (!forced && !(ro.W * dts > unif<Real>(r.r1))) continue;
+      XiOut<Real> xo = photon_xi(A.T.Y, A.T, ro.l, chi, ro.kmin, unif<Real>(r.r2), unif<Real>(~r.r2), dummy);
       Real g2 = g * xo.omxi, eph = g * xo.xi;
       if (g2 < (Real)1) { g2 = (Real)1; eph = g - (Real)1; }
       put(j++, eph, kk);
@@ -1798,6 +1806,7 @@ struct SampleArgs {
   const uint32_t *mlp_frag;
   const float *mlp_w;
   int use_mlp;
+  int emit_lanes, scan_draws;  // chain scheduling (QED_SCHED_EMIT_LANES, _SCAN_DRAWS)
 };
 
 __global__ void __launch_bounds__(TILE) k_sample_xi(SampleArgs A) {
@@ -2196,6 +2205,8 @@ cudaError_t launch_lepton(qed_ctx *c, const qed_species *s0, const qed_species *
   a.mlp_frag = c->mlp_frag;
   a.mlp_w = c->mlp_w;
   a.use_mlp = c->cfg.sampler == QED_SAMPLER_MLP && c->mlp_ready;
+  a.emit_lanes = sched_param(c, QED_SCHED_EMIT_LANES);
+  a.scan_draws = sched_param(c, QED_SCHED_SCAN_DRAWS);
   a.d_step = c->use_dstep ? c->d_step : nullptr;
   if (mode == MODE_PUSH) return launch_lepton_m<Real, MODE_PUSH>(c, a, f->mode, st);
   if (mode == MODE_EMIT) return launch_lepton_m<Real, MODE_EMIT>(c, a, f->mode, st);

@@ -52,6 +52,8 @@ def test_struct_layouts_match_c(qlib, tmp_path):
                  sizeof(qed_fields), sizeof(qed_counters));
           printf("%zu %zu %zu %zu\\n", offsetof(qed_config, seed), offsetof(qed_species, d_n),
                  offsetof(qed_fields, grid), offsetof(qed_counters, hist));
+          printf("%zu %zu %zu %zu\\n", sizeof(qed_tuning), offsetof(qed_tuning, sched),
+                 offsetof(qed_tuning, ms_per_step), offsetof(qed_tuning, sched_ms));
           return 0;
         }"""))
     exe = tmp_path / "sz"
@@ -60,8 +62,10 @@ def test_struct_layouts_match_c(qlib, tmp_path):
     B = qlib
     assert [int(v) for v in out[:4]] == [C.sizeof(B.qed_config), C.sizeof(B.qed_species),
                                          C.sizeof(B.qed_fields), C.sizeof(B.qed_counters)]
-    assert [int(v) for v in out[4:]] == [B.qed_config.seed.offset, B.qed_species.d_n.offset,
-                                         B.qed_fields.grid.offset, B.qed_counters.hist.offset]
+    assert [int(v) for v in out[4:8]] == [B.qed_config.seed.offset, B.qed_species.d_n.offset,
+                                          B.qed_fields.grid.offset, B.qed_counters.hist.offset]
+    assert [int(v) for v in out[8:]] == [C.sizeof(B.qed_tuning), B.qed_tuning.sched.offset,
+                                         B.qed_tuning.ms_per_step.offset, B.qed_tuning.sched_ms.offset]
 
 
 def test_config_defaults_and_strerror(qlib):

@@ -121,7 +121,12 @@ def test_group_autotuner_picks_a_factor_per_kernel_group(api, order):
         ms = t["ms"][name]
         assert 1 <= f <= 8 and all(m > 0 for m in ms), name
         assert ms[f - 1] == min(ms), name
-    assert t["ms_per_step"] == min(t["ms"]["compact"])
+    for name, v in t["sched"].items():
+        tried = t["sched_ms"][name]
+        assert len(tried) >= 3 and all(m > 0 for m in tried.values()), name
+        assert tried[v] == min(tried.values()), name
+    assert t["ms_per_step"] == min([min(t["ms"]["compact"])] +
+                                   [min(v.values()) for v in t["sched_ms"].values()])
     out = []
     for c in (ctx, api.qed_init_tables(api.config(dt=0.01, seed=2, append_order=order))):
         e2, p2, g2 = _species(api, st, n, cap_factor=8)
@@ -130,3 +135,44 @@ def test_group_autotuner_picks_a_factor_per_kernel_group(api, order):
         out.append((e2.host(), g2.host()))
     np.testing.assert_array_equal(out[0][0]["px"], out[1][0]["px"])
     np.testing.assert_array_equal(np.sort(out[0][1]["id"]), np.sort(out[1][1]["id"]))
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_chain_scheduling_changes_no_result(api, order):
+    """The Method I chain-scheduling parameters (lanes per round, draws per
+    round, queue trigger) at their extremes give the same particles, photons
+    and counters as the defaults."""
+    from paper_1608_06356_gb300 import workloads as W
+    st = _runs(W, [40000, 30000])
+    n = len(st["x"])
+    out = []
+    for sched in ({}, {"emit_lanes": 1, "round_lanes": 1, "scan_draws": 2, "scan_left": 1,
+                       "queue_trigger": 1},
+                  {"emit_lanes": 32, "round_lanes": 32, "scan_draws": 16, "scan_left": 32,
+                   "queue_trigger": 33}):
+        ctx = api.qed_init_tables(api.config(dt=0.02, seed=4, append_order=order))
+        api.qed_set_tuning(ctx, {}, sched)
+        e, p, g = _species(api, st, n, cap_factor=8)
+        for s in range(2):
+            api.qed_step_fused(ctx, e, p, g, api.Fields.per_particle(), 7 + s)
+        torch.cuda.synchronize()
+        c = api.qed_read_counters(ctx)
+        assert c["status"] & ~2 == 0
+        out.append((e.host(), p.host(), g.host(), c))
+    for o in out[1:]:
+        for a, b in zip(out[0][:3], o[:3]):
+            ia, ib = np.argsort(a["id"], kind="stable"), np.argsort(b["id"], kind="stable")
+            for k in a:
+                np.testing.assert_array_equal(a[k][ia], b[k][ib], err_msg=k)
+        for k in ("emit_events", "pair_events", "substeps", "dropped", "hist"):
+            assert out[0][3][k] == o[3][k], k
+    assert out[0][3]["emit_events"] > 1000
+
+
+def test_set_tuning_rejects_out_of_range_values(api):
+    ctx = api.qed_init_tables(api.config())
+    for bad in ({"emit_lanes": 33}, {"scan_draws": 3}, {"scan_draws": 18}, {"queue_trigger": 34},
+                {"round_lanes": -1}):
+        with pytest.raises(RuntimeError):
+            api.qed_set_tuning(ctx, {}, bad)
+    api.qed_set_tuning(ctx, {"stream": 2}, {"scan_draws": 8})

@@ -369,6 +369,69 @@ def test_method_I_small_step_rate(orc):
         assert abs(lc.events - n * wdt) < 4 * sd + 1
 
 
+def test_method_I_words_of_each_substep(orc):
+    # Sub-steps 2j and 2j+1 of an emission chain share the draw (id, step, j,
+    # emission): r1 and r2 are its words 0 and 1 for the even sub-step, 2 and
+    # 3 for the odd one.  With the push off (qed_emit's counterpart), each
+    # lepton's first photon must come from the first sub-step whose r1 lies
+    # below W Dt/N, have the energy gamma xi(r2) of that sub-step's r2 (Eq. 7),
+    # and carry the photon-id draw of that sub-step.  A chain read with one
+    # draw per sub-step (or with the odd sub-steps' words swapped) fails.
+    chi, gamma = 2.0, 1000.0
+    B = chi * orc.A_S_1UM / math.sqrt(gamma**2 - 1)
+    W = orc.rate_photon(orc.make_config(), chi, gamma)[0]
+    N = 7
+    cfg = orc.make_config(dt=N * 0.2 / W * 0.999, seed=77)
+    n, step = 200, 5
+    e = _electrons(orc, n, gamma, tag=False)
+    g = orc.Species(4 * N * n, 0.0, with_alive=True)
+    f = orc.uniform_fields([0, 0, 0], [B, 0, 0])
+    W0 = orc.rate_photon(cfg, orc.chi_lepton(np.array([0, 0, math.sqrt(gamma**2 - 1)]),
+                                             np.zeros(3), np.array([B, 0, 0]), cfg.a_S), gamma)[0]
+    assert math.ceil(W0 * cfg.dt / 0.2) == N
+    orc.emit(cfg, f, e, g, step)
+    key = np.array([cfg.seed & 0xFFFFFFFF, cfg.seed >> 32], dtype=np.uint32)
+
+    def words(stream, sub):
+        ctr = np.zeros((n, 4), dtype=np.uint32)
+        ctr[:, 0] = np.arange(n, dtype=np.uint32)
+        ctr[:, 2] = step
+        ctr[:, 3] = (sub << 2) | stream
+        return orc.philox(ctr, np.tile(key, (n, 1)))
+
+    thr = W0 * cfg.dt / N
+    first = np.full(n, -1)
+    r2w = np.zeros(n, dtype=np.uint64)
+    for k in range(N - 1, -1, -1):
+        w = words(0, k // 2)
+        r1, _ = orc.uniform_from_word(w[:, 2 * (k % 2)])
+        hit = thr > r1
+        first[hit] = k
+        r2w[hit] = w[hit, 2 * (k % 2) + 1]
+    ids = g.view("id")[: g.n]
+    # the photons in parent order (one parent per lepton id, emission order)
+    eph = np.sqrt(g.view("px") ** 2 + g.view("py") ** 2 + g.view("pz") ** 2)[: g.n]
+    emitted = first >= 0
+    assert 0.3 * n < emitted.sum() < n
+    pid_words = {k: words(2, k) for k in range(N)}
+    pos = 0
+    for i in range(n):
+        if not emitted[i]:
+            continue
+        k = first[i]
+        want = int(pid_words[k][i, 0]) | (int(pid_words[k][i, 1]) << 32)
+        assert int(ids[pos]) == want, (i, k)
+        u2, c2 = orc.uniform_from_word(np.array([r2w[i]]))
+        xi = orc.sample_photon(cfg, np.array([chi]), np.array([gamma]), u2, c2)[0]
+        assert abs(eph[pos] - gamma * xi) <= 1e-9 * gamma
+        # skip this lepton's later photons (their rate follows the recoil)
+        own = {int(pid_words[kk][i, 0]) | (int(pid_words[kk][i, 1]) << 32) for kk in range(N)}
+        pos += 1
+        while pos < g.n and int(ids[pos]) in own:
+            pos += 1
+    assert pos == g.n
+
+
 def test_capacity_drops_in_order_and_compact(orc):
     cfg = orc.make_config(dt=0.05, seed=3)
     n = 300
