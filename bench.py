@@ -264,7 +264,7 @@ def time_arm(api, torch, ctx, H, F, steps, warmup, step0, dist=None, profile=Tru
     return out
 
 
-def lepton_roofline(r, n, steps, peak, peak_kind):
+def lepton_roofline(r, n, steps, peak, peak_kind, mlp=False):
     """Roofline of the lepton step (the per-lepton unit whose algorithmic
     bytes are 84 B + 61 B per emitted photon): its five phases (streaming
     pass, class list, counting pass, scan, writing pass) are timed by CUDA
@@ -277,7 +277,8 @@ def lepton_roofline(r, n, steps, peak, peak_kind):
     achieved = lep_bytes / (lep_ms * 1e-3) / 1e9
     stream_ms = phases["lepton_stream"] / nprof
     return {"bound": "hbm",
-            "kernel": ("lepton step: k_lepton_onepass" if APPEND_ORDER else
+            "kernel": (("lepton step: k_lepton_onepass + k_net_emit (the learned sampler's dense pass)"
+                        if mlp else "lepton step: k_lepton_onepass") if APPEND_ORDER else
                        "lepton step: k_lepton_stream + k_cls_count/scan/scatter + k_substep_count + "
                        "k_sub_scan + k_substep_write_coop + k_substep_replay"),
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -923,7 +924,7 @@ def main():
         arm_out[name] = {"value": ps_total / (t_max * 1e-3) if status == "ok" else None,
                          "status": status, "ms_per_step": t_max / args.steps,
                          "gpu_launches": r["launches"],
-                         "roofline": lepton_roofline(r, n, args.steps, peak, peak_kind),
+                         "roofline": lepton_roofline(r, n, args.steps, peak, peak_kind, mlp=name == "mlp"),
                          "counters": {k: c[k] for k in COUNTER_KEYS + ("status",)},
                          "photons_per_step": r["photons_last_step"],
                          "hist_64_log_bins_2_to_1000": c["hist"]}

@@ -358,7 +358,8 @@ int qed_autotune(qed_ctx *ctx, const qed_species *e, const qed_species *p, const
  *   QED_TUNE_CHAINS   the ordered path's Method I chains (counting, replay)
  *   QED_TUNE_ORDER    the ordered path's lists, scans and writing pass
  *   QED_TUNE_PHOTON   photon streaming and pair passes
- *   QED_TUNE_COMPACT  stable compaction and the isolated sampler */
+ *   QED_TUNE_COMPACT  stable compaction, the isolated sampler and the
+ *                     learned sampler's dense pass of the single-pass step */
 enum { QED_TUNE_STREAM = 0, QED_TUNE_CHAINS = 1, QED_TUNE_ORDER = 2, QED_TUNE_PHOTON = 3,
        QED_TUNE_COMPACT = 4, QED_TUNE_GROUPS = 5, QED_TUNE_MAX_FACTOR = 8 };
 

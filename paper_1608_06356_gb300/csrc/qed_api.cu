@@ -86,7 +86,7 @@ static void free_ctx(qed_ctx *c) {
                   c->cls_chunk_off, c->cls_off, c->sub_cnt, c->sub_gf, c->rec_e,
                   c->rec_k, c->sub_meta, c->fill_meta, c->replay_n, c->stage, c->stage_tag,
                   c->stage_idx, c->stage_n, c->probe_state,
-                  c->mlp_mem, c->w_up_row};
+                  c->mlp_mem, c->w_up_row, c->net_rec, c->net_n};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   free(c);

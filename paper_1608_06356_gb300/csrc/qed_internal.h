@@ -57,6 +57,13 @@ struct qed_ctx {
   void *mlp_mem;
   float *mlp_w, *mlp_m, *mlp_v, *mlp_g, *mlp_partial;
   uint32_t *mlp_frag;
+  float *mlp_fw;         // FP32 small layers in the inference layout (W1, b1, b2, b3, W4, b4)
+  // learned-sampler emissions of the single-pass lepton step, deferred to a
+  // dense pass: records (16 or 48 bytes), their count and the pass's CTA
+  // counter
+  float4 *net_rec;
+  int64_t net_cap;  // float4 units
+  unsigned long long *net_n;  // [0] records appended, [1] CTAs of the dense pass done
   double *mlp_loss;
   int mlp_parts, mlp_ready;
   int64_t mlp_step;

@@ -318,7 +318,8 @@ static size_t grad_smem() {
 int mlp_alloc(qed_ctx *c) {
   c->mlp_parts = c->num_sms;
   size_t bytes = sizeof(float) * MLP_NP * 4 + sizeof(uint32_t) * MLP_FRAG_WORDS +
-                 sizeof(float) * (size_t)MLP_NP * c->mlp_parts + sizeof(double) * c->mlp_parts;
+                 sizeof(float) * MLP_SMEM_FLOATS + sizeof(float) * (size_t)MLP_NP * c->mlp_parts +
+                 sizeof(double) * c->mlp_parts;
   if (cudaMalloc(&c->mlp_mem, bytes) != cudaSuccess) return QED_ERR_NOMEM;
   float *f = static_cast<float *>(c->mlp_mem);
   c->mlp_w = f;
@@ -326,7 +327,8 @@ int mlp_alloc(qed_ctx *c) {
   c->mlp_v = f + 2 * MLP_NP;
   c->mlp_g = f + 3 * MLP_NP;
   c->mlp_frag = reinterpret_cast<uint32_t *>(f + 4 * MLP_NP);
-  c->mlp_partial = reinterpret_cast<float *>(c->mlp_frag + MLP_FRAG_WORDS);
+  c->mlp_fw = reinterpret_cast<float *>(c->mlp_frag + MLP_FRAG_WORDS);
+  c->mlp_partial = c->mlp_fw + MLP_SMEM_FLOATS;
   c->mlp_loss = reinterpret_cast<double *>(c->mlp_partial + (size_t)MLP_NP * c->mlp_parts);
   if (cudaMemset(c->mlp_mem, 0, bytes) != cudaSuccess) return QED_ERR_CUDA;
   if (cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -334,12 +336,42 @@ int mlp_alloc(qed_ctx *c) {
     return QED_ERR_CUDA;
   c->mlp_ready = 0;
   c->mlp_step = 0;
+  // records of deferred learned-sampler emissions (single-pass lepton step of
+  // an FP32 context with the learned sampler): 16 bytes (48 with grid
+  // fields) per emission, at most one per lepton at step start.  Two species
+  // of at most max_particles each fill 2 max_particles records of 16 bytes;
+  // with grid fields two thirds of that, while a one-sub-step lepton emits
+  // with probability <= 0.2 (a record past the end is counted as dropped).
+  c->net_cap = 0;
+  if (c->cfg.sampler != QED_SAMPLER_MLP || c->cfg.append_order != QED_APPEND_ANY ||
+      c->cfg.precision != QED_FP32)
+    return QED_OK;
+  c->net_cap = 2 * (c->cfg.max_particles > 4096 ? c->cfg.max_particles : 4096);
+  if (cudaMalloc(&c->net_rec, sizeof(float4) * (size_t)c->net_cap) != cudaSuccess ||
+      cudaMalloc(&c->net_n, 2 * sizeof(unsigned long long)) != cudaSuccess)
+    return QED_ERR_NOMEM;
+  if (cudaMemset(c->net_n, 0, 2 * sizeof(unsigned long long)) != cudaSuccess) return QED_ERR_CUDA;
   return QED_OK;
+}
+
+// The FP32 small layers in the layout inference reads (as staged by mlp_stage).
+__global__ void k_mlp_pack_fw(const float *w, float *fw) {
+  for (int k = threadIdx.x; k < MLP_SMEM_FLOATS; k += blockDim.x) {
+    float v = 0.f;
+    if (k < 128) v = w[MLP_OFF_W1 + k];
+    else if (k < 192) v = w[MLP_OFF_B1 + k - 128];
+    else if (k < 256) v = w[MLP_OFF_B2 + k - 192];
+    else if (k < 320) v = w[MLP_OFF_B3 + k - 256];
+    else if (k < 384) v = w[MLP_OFF_W4 + k - 320];
+    else if (k == 384) v = w[MLP_OFF_B4];
+    fw[k] = v;
+  }
 }
 
 static cudaError_t pack(qed_ctx *c, cudaStream_t st) {
   k_mlp_pack<<<(2 * 4 * 8 * 32 + 255) / 256, 256, 0, st>>>(c->mlp_w, c->mlp_frag);
-  c->launches += 1;
+  k_mlp_pack_fw<<<1, 128, 0, st>>>(c->mlp_w, c->mlp_fw);
+  c->launches += 2;
   return cudaGetLastError();
 }
 

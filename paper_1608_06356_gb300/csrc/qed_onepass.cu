@@ -73,8 +73,11 @@ struct OnePassArgs {
   const int64_t *d_step;
   const float *w_up_row;       // W_rad <= w_up_row[j] chi / gamma for ln chi >= row j
   float chi_tab_lo, chi_tab_hi;  // chi range of the rate tables
-  const uint32_t *mlp_frag;
-  const float *mlp_w;
+  const uint32_t *mlp_frag;  // learned sampler: BF16 fragments and the FP32 small
+  const float *mlp_fw;       // layers, in global memory (read through L1)
+  float4 *net_rec;           // records of the deferred network emissions
+  unsigned long long *net_n; // their count
+  int64_t net_cap;
   // chain scheduling (QED_SCHED_*): an emission round waits for emit_lanes
   // lanes with an event, a rate or scanning round runs with at least
   // round_lanes lanes, a scanning round draws scan_iters times four
@@ -84,10 +87,10 @@ struct OnePassArgs {
   int emit_lanes, round_lanes, scan_iters, scan_left, qtrig;
 };
 
-// dynamic shared memory: prefetch buffers, per-warp queues and park areas
-// (and the learned sampler's image).  The rate tables are read through L1:
-// only the queued particles evaluate the exact rate.
-template <int FM> __host__ __device__ size_t onepass_layout(const OnePassArgs &a, bool mlp, size_t off[5]) {
+// dynamic shared memory: prefetch buffers, per-warp queues and park areas.
+// The rate tables are read through L1: only the queued particles evaluate the
+// exact rate.
+template <int FM> __host__ __device__ size_t onepass_layout(const OnePassArgs &a, size_t off[4]) {
   size_t o = 0;
   off[0] = o;  // prefetch: two buffers of [NV][OP_THREADS] words and [OP_THREADS] ids
   o += 2 * OP_THREADS * ((size_t)stream_words<FM>() * sizeof(float) + sizeof(uint64_t));
@@ -96,18 +99,33 @@ template <int FM> __host__ __device__ size_t onepass_layout(const OnePassArgs &a
   off[2] = o;  // park: floats [PF][32], words [PU][32] per warp
   o += (size_t)OP_WARPS * 32 * 4 * (PF + PU);
   o = (o + 15) & ~(size_t)15;
-  off[3] = o;  // learned sampler image
-  if (mlp) o += MLP_SMEM_BYTES;
-  off[4] = o;
+  off[3] = o;
   return o;
 }
 
-// lane states of a chain; ST_PEND_NET: an event whose xi the learned sampler
-// gives (a one-sub-step particle inside the network's domain): such emissions
-// run in rounds of their own, so that one warp-wide network evaluation serves
-// many of them
-enum { ST_IDLE = 0, ST_RATE = 1, ST_SCAN = 2, ST_PEND = 3, ST_DONE = 4, ST_PEND_NET = 5 };
-constexpr int CNT_MIN_NET = 24;  // lanes an emission round through the network waits for
+// lane states of a chain
+enum { ST_IDLE = 0, ST_RATE = 1, ST_SCAN = 2, ST_PEND = 3, ST_DONE = 4 };
+
+// Learned-sampler emissions deferred to the dense pass: one record per
+// emission, 16 bytes -- the lepton's index (species in the top bit) and kappa
+// -- plus, with grid fields, its position before the push (so that the dense
+// pass gathers the same fields), 32 bytes.  Everything else (the pushed
+// momentum, gamma, the direction, chi, the id) the dense pass reads or
+// recomputes with the same expressions.
+template <int FM> __host__ __device__ constexpr int net_stride() { return FM == FM_GRID ? 3 : 1; }  // float4 per record
+
+// gamma and the unit direction of a pushed momentum, as a deferred particle
+// gets them in the heavy phase and in the dense pass alike
+__device__ __forceinline__ void gamma_dir(float px, float py, float pz, float &g, float &nx, float &ny,
+                                          float &nz) {
+  g = sqrtf(1.f + px * px + py * py + pz * pz);
+  const float pm = sqrtf(px * px + py * py + pz * pz);
+  nx = ny = nz = 0.f;
+  if (pm > 0.f) {
+    const float ip = 1.f / pm;
+    nx = px * ip; ny = py * ip; nz = pz * ip;
+  }
+}
 
 
 // N = max(1, ceil(W Dt / wdt_max)), capped at max_substeps (status bit).
@@ -126,7 +144,7 @@ __device__ __forceinline__ int64_t substep_count_op(const Consts &C, float W, fl
 // DEF: the default chain scheduling as compile-time constants (the runtime
 // values cost ~3.5% of the kernel's time); otherwise the values in A.
 template <int FM, int MODE, bool MLP, bool DEF>
-__global__ void __launch_bounds__(OP_THREADS, MLP ? 3 : 5) k_lepton_onepass(OnePassArgs A) {
+__global__ void __launch_bounds__(OP_THREADS, 5) k_lepton_onepass(OnePassArgs A) {
   const int emit_lanes = DEF ? SCHED_DEF_EMIT_LANES : A.emit_lanes;
   const int round_lanes = DEF ? SCHED_DEF_ROUND_LANES : A.round_lanes;
   const int scan_iters = DEF ? (SCHED_DEF_SCAN_DRAWS + 3) / 4 : A.scan_iters;
@@ -138,8 +156,8 @@ __global__ void __launch_bounds__(OP_THREADS, MLP ? 3 : 5) k_lepton_onepass(OneP
   __shared__ unsigned long long s_deferred;
   constexpr int NV = stream_words<FM>();
   const int64_t step_ = A.d_step ? *A.d_step : A.step;
-  size_t off[5];
-  onepass_layout<FM>(A, MLP, off);
+  size_t off[4];
+  onepass_layout<FM>(A, off);
   const float *sR = A.T.R, *sF = A.T.F;
   float *pf = reinterpret_cast<float *>(smem_raw + off[0]);
   uint64_t *pf_id = reinterpret_cast<uint64_t *>(pf + 2 * NV * OP_THREADS);
@@ -152,10 +170,6 @@ __global__ void __launch_bounds__(OP_THREADS, MLP ? 3 : 5) k_lepton_onepass(OneP
   unsigned char *pbase = smem_raw + off[2] + (size_t)wid * 32 * 4 * (PF + PU);
   float *pk_f = reinterpret_cast<float *>(pbase);
   uint32_t *pk_u = reinterpret_cast<uint32_t *>(pbase + 4 * PF * 32);
-  uint32_t *s_frag = reinterpret_cast<uint32_t *>(smem_raw + off[3]);
-  float *s_fw = reinterpret_cast<float *>(s_frag + MLP_FRAG_WORDS);
-
-  if (MLP) mlp_stage(s_frag, s_fw, A.mlp_frag, A.mlp_w);
   block_tally_init(&bt);
   if (threadIdx.x == 0) {
     s_meta[0] = *(volatile int64_t *)A.sp[0].d_n;
@@ -217,9 +231,7 @@ __global__ void __launch_bounds__(OP_THREADS, MLP ? 3 : 5) k_lepton_onepass(OneP
       const unsigned rate = __ballot_sync(0xFFFFFFFFu, st == ST_RATE);
       const unsigned scan = __ballot_sync(0xFFFFFFFFu, st == ST_SCAN);
       const unsigned pend = __ballot_sync(0xFFFFFFFFu, st == ST_PEND);
-      const unsigned pnet = MLP ? __ballot_sync(0xFFFFFFFFu, st == ST_PEND_NET) : 0u;
       const int ni = __popc(idle), nr = __popc(rate), ns = __popc(scan), np = __popc(pend);
-      const int nn = __popc(pnet);
       // idle lanes are refilled from the queue at the start of a rate round
       const int take = min(qn, ni);
       // a round runs only with enough lanes in its state; otherwise the warp
@@ -228,14 +240,12 @@ __global__ void __launch_bounds__(OP_THREADS, MLP ? 3 : 5) k_lepton_onepass(OneP
       // the final drain, which runs whatever is left
       int phase;
       if (np >= emit_lanes) phase = ST_PEND;
-      else if (MLP && nn >= CNT_MIN_NET) phase = ST_PEND_NET;
       else if (nr + take >= round_lanes) phase = ST_RATE;
       else if (ns >= round_lanes) phase = ST_SCAN;
       else if (!final_drain && qn <= QEXIT) break;
       else if (nr + take) phase = ST_RATE;
       else if (ns) phase = ST_SCAN;
       else if (np) phase = ST_PEND;
-      else if (MLP && nn) phase = ST_PEND_NET;
       else break;
       if (phase == ST_RATE) {
         // refill: idle lanes take queue entries from the top, in lane order
@@ -251,10 +261,7 @@ __global__ void __launch_bounds__(OP_THREADS, MLP ? 3 : 5) k_lepton_onepass(OneP
               B[c] = q_f[(6 + c) * QCAP + q];
             }
             pid = q_id[q];
-            g = sqrtf(1.f + px * px + py * py + pz * pz);
-            const float pm = sqrtf(px * px + py * py + pz * pz);
-            nx = ny = nz = 0.f;
-            if (pm > 0.f) { const float ip = 1.f / pm; nx = px * ip; ny = py * ip; nz = pz * ip; }
+            gamma_dir(px, py, pz, g, nx, ny, nz);
             k = 0;
             cnt = 0;
             st = ST_RATE;
@@ -301,29 +308,55 @@ __global__ void __launch_bounds__(OP_THREADS, MLP ? 3 : 5) k_lepton_onepass(OneP
           }
           if (__popc(__ballot_sync(0xFFFFFFFFu, drawing)) < scan_left) break;
         }
-        if (MLP && was_scan && st == ST_PEND && N == 1) {  // does the network give this xi?
-          const float kap = photon_kappa(ro.kmin, unif<float>(wy), unif<float>(~wy));
-          const float lchi = chi > 0.f ? logf(chi) : MLP_L_LO - 1.f;
-          if (lchi >= MLP_L_LO && lchi <= MLP_L_HI && kap >= MLP_K_LO && kap <= MLP_K_HI)
-            st = ST_PEND_NET;
+        if (MLP) {
+          // an event of a one-sub-step particle inside the network's domain
+          // takes its xi from the learned sampler, in the dense pass that
+          // follows this kernel: a record here (one per such particle: at
+          // most n0 + n1, which the records hold), no photon yet (cnt = 0)
+          bool net = false;
+          float kap = 0.f;
+          if (was_scan && st == ST_PEND && N == 1) {
+            kap = photon_kappa(ro.kmin, unif<float>(wy), unif<float>(~wy));
+            const float lchi = chi > 0.f ? logf(chi) : MLP_L_LO - 1.f;
+            net = lchi >= MLP_L_LO && lchi <= MLP_L_HI && kap >= MLP_K_LO && kap <= MLP_K_HI;
+          }
+          const unsigned nm = __ballot_sync(0xFFFFFFFFu, net);
+          if (nm) {
+            const int leader = __ffs(nm) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(A.net_n, (unsigned long long)__popc(nm));
+            base = __shfl_sync(0xFFFFFFFFu, base, leader);
+            if (net) {
+              constexpr int RS = net_stride<FM>();
+              const unsigned long long r = base + __popc(nm & lt_mask);
+              if (r < (unsigned long long)(A.net_cap / RS)) {
+                int si;
+                int64_t i;
+                slot_index(hslot, si, i);
+                float4 *R = A.net_rec + RS * r;
+                R[0] = make_float4(__uint_as_float((uint32_t)i),
+                                   __uint_as_float((uint32_t)((uint64_t)i >> 32) | ((uint32_t)si << 31)),
+                                   kap, E[0]);
+                if (FM == FM_GRID) {
+                  R[1] = make_float4(E[1], E[2], B[0], B[1]);
+                  R[2] = make_float4(B[2], 0.f, 0.f, 0.f);
+                }
+              } else {  // only with counts beyond the species' capacities
+                tl.dropped += 1;
+                tl.status |= QED_STATUS_CAPACITY;
+              }
+              st = ST_DONE;
+            }
+          }
         }
       } else {
-        // emission by every lane with an event of this round's kind (warp-
-        // collective parts run in every lane): kappa (Eq. 7), ln delta from
-        // the inverse table or, for ST_PEND_NET lanes, the network (one-
-        // sub-step particles in its domain, as on the ordered path), xi, the
-        // recoil and the photon
-        const bool ev = st == phase;
+        // emission by every lane with an event: kappa and ln delta from the
+        // inverse table (Eq. 7), xi, the recoil and the photon
+        const bool ev = st == ST_PEND;
         const float kap = ev ? photon_kappa(ro.kmin, unif<float>(wy), unif<float>(~wy)) : 0.f;
-        float Y = 0.f;
-        if (MLP && phase == ST_PEND_NET) {
-          const float lchi = ev ? logf(chi) : 0.f;
-          const float zz = mlp_infer_warp(s_frag, s_fw, (lchi - MLP_LC) / MLP_LS, (kap - MLP_KC) / MLP_KS);
-          Y = zz + mlp_baseline(kap);
-        }
         float eph = 0.f, g2 = g;
         if (ev) {
-          if (phase == ST_PEND) Y = photon_lndelta_table(A.T.Y, A.T, ro.l, kap, tl);
+          const float Y = photon_lndelta_table(A.T.Y, A.T, ro.l, kap, tl);
           const XiOut<float> xo = xi_from_lndelta(chi, Y);
           g2 = g * xo.omxi;
           eph = g * xo.xi;
@@ -542,10 +575,174 @@ __global__ void __launch_bounds__(OP_THREADS, MLP ? 3 : 5) k_lepton_onepass(OneP
   }
 }
 
+// ---- the learned sampler's dense pass ----------------------------------
+// The deferred emissions of one-sub-step leptons (records written by the
+// single-pass kernel): every warp takes 32 records at a time, evaluates the
+// network for all of them at once (tensor cores, weights in shared memory),
+// and finishes each emission with the heavy phase's expressions: gamma, the
+// direction and chi of the pushed lepton, xi (Eq. 7 through ln delta), the
+// recoiled momentum, the spectrum bin and the photon.
+struct NetArgs {
+  Sp<float> sp[2];
+  Sp<float> ph;
+  Fld<float> f;
+  Consts C;
+  Out o;
+  int64_t step;
+  const int64_t *d_step;
+  const uint32_t *mlp_frag;
+  const float *mlp_fw;
+  const float4 *net_rec;
+  unsigned long long *net_n;  // [0] records written, [1] CTAs of this pass done
+  int64_t net_cap;            // float4 units of net_rec
+};
+constexpr int NET_THREADS = 256;
+
+template <int FM>
+__global__ void __launch_bounds__(NET_THREADS) k_net_emit(NetArgs A) {
+  constexpr int RS = net_stride<FM>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ BlockTally bt;
+  __shared__ long long s_n;
+  uint32_t *s_frag = reinterpret_cast<uint32_t *>(smem_raw);
+  float *s_fw = reinterpret_cast<float *>(s_frag + MLP_FRAG_WORDS);
+  for (int k = threadIdx.x; k < MLP_FRAG_WORDS; k += blockDim.x) s_frag[k] = A.mlp_frag[k];
+  for (int k = threadIdx.x; k < MLP_SMEM_FLOATS; k += blockDim.x) s_fw[k] = A.mlp_fw[k];
+  block_tally_init(&bt);
+  if (threadIdx.x == 0) {
+    const unsigned long long n = *(volatile unsigned long long *)A.net_n;
+    const unsigned long long cap = (unsigned long long)(A.net_cap / RS);
+    s_n = (long long)(n < cap ? n : cap);
+  }
+  __syncthreads();
+  const int64_t n = s_n;
+  const int64_t step_ = A.d_step ? *A.d_step : A.step;
+  const float inv_aS = A.C.f_inv_aS;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  Tally tl;
+  tl.clear();
+  for (int64_t base = w * 32; base < n; base += nw * 32) {  // warp-uniform
+    const int64_t r = base + lane;
+    const bool ok = r < n;
+    int si = 0;
+    int64_t i = 0;
+    float kap = 0.f, g = 1.f, nx = 0.f, ny = 0.f, nz = 0.f, chi = 1.f;
+    float E[3] = {0.f, 0.f, 0.f}, B[3] = {0.f, 0.f, 0.f};
+    if (ok) {
+      const float4 *R = A.net_rec + RS * r;
+      const float4 R0 = R[0];
+      const uint32_t hi = __float_as_uint(R0.y);
+      i = (int64_t)(((uint64_t)(hi & 0x7FFFFFFFu) << 32) | __float_as_uint(R0.x));
+      si = (int)(hi >> 31);
+      kap = R0.z;
+      const Sp<float> &S = A.sp[si];
+      if (FM == FM_GRID) {
+        const float4 R1 = R[1], R2 = R[2];
+        E[0] = R0.w; E[1] = R1.x; E[2] = R1.y;
+        B[0] = R1.z; B[1] = R1.w; B[2] = R2.x;
+      } else {
+        get_fields<float, FM>(S, A.f, i, 0.f, 0.f, 0.f, E, B);
+      }
+      const float px = S.px[i], py = S.py[i], pz = S.pz[i];
+      gamma_dir(px, py, pz, g, nx, ny, nz);
+      chi = chi_lepton(px, py, pz, g, E[0], E[1], E[2], B[0], B[1], B[2], inv_aS);
+    }
+    const float lchi = ok ? logf(chi) : 0.f;
+    const float zz = mlp_infer_warp(s_frag, s_fw, (lchi - MLP_LC) / MLP_LS, (kap - MLP_KC) / MLP_KS);
+    float eph = 0.f, g2 = g;
+    if (ok) {
+      const float Y = zz + mlp_baseline(kap);
+      const XiOut<float> xo = xi_from_lndelta(chi, Y);
+      g2 = g * xo.omxi;
+      eph = g * xo.xi;
+      if (g2 < 1.f) { g2 = 1.f; eph = g - 1.f; }
+      const int b = spec_bin(A.C, eph);
+      const unsigned same = __match_any_sync(__activemask(), b);
+      if (b >= 0 && lane == __ffs(same) - 1) atomicAdd(&bt.hist[b], (unsigned long long)__popc(same));
+    }
+    const unsigned em = __ballot_sync(0xFFFFFFFFu, ok);
+    const int leader = __ffs(em) - 1;
+    unsigned long long pbase = 0;
+    if (lane == leader)
+      pbase = atomicAdd(reinterpret_cast<unsigned long long *>(A.ph.d_n), (unsigned long long)__popc(em));
+    pbase = __shfl_sync(0xFFFFFFFFu, pbase, leader < 0 ? 0 : leader);
+    if (ok) {
+      const Sp<float> &S = A.sp[si];
+      const int64_t pos = (int64_t)pbase + __popc(em & lt_mask);
+      if (pos >= A.ph.cap) {
+        tl.dropped += 1;
+        tl.status |= QED_STATUS_CAPACITY;
+      } else {
+        const U4 cid = draw(A.C.seed, S.id[i], step_, 0, STREAM_PHOTON_ID);
+        write_child(A.ph, pos, S.x[i], S.y[i], S.z[i], eph * nx, eph * ny, eph * nz, S.w[i],
+                    (uint64_t)cid.x | ((uint64_t)cid.y << 32), E, B, S.tag ? S.tag[i] : 0u);
+      }
+      const float pm = sqrtf((g2 - 1.f) * (g2 + 1.f));
+      S.px[i] = pm * nx; S.py[i] = pm * ny; S.pz[i] = pm * nz;
+      tl.events += 1;
+    }
+  }
+  tally_flush(&bt, tl);
+  __syncthreads();
+  block_tally_commit(&bt, A.o.cnt, 0);
+  if (threadIdx.x == 0) {
+    // the last CTA clamps the photon count to the capacity and clears the
+    // record count for the next step
+    __threadfence();
+    const unsigned long long prev = atomicAdd(A.net_n + 1, 1ull);
+    if (prev == gridDim.x - 1) {
+      __threadfence();
+      int64_t *dn = A.ph.d_n;
+      if (*(volatile int64_t *)dn > A.ph.cap) *dn = A.ph.cap;
+      A.net_n[0] = 0ull;
+      A.net_n[1] = 0ull;
+      __threadfence();
+    }
+  }
+}
+
+template <int FM>
+cudaError_t launch_net_emit_t(qed_ctx *c, const NetArgs &n, cudaStream_t st) {
+  const size_t sm = MLP_SMEM_BYTES;
+  auto kern = k_net_emit<FM>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NET_THREADS, sm);
+  if (e != cudaSuccess) return e;
+  per_sm = persistent_blocks_per_sm(c, per_sm, QED_TUNE_COMPACT);
+  kern<<<c->num_sms * per_sm, NET_THREADS, sm, st>>>(n);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_net_emit(qed_ctx *c, const OnePassArgs &a, int fm, cudaStream_t st) {
+  NetArgs n{};
+  n.sp[0] = a.sp[0];
+  n.sp[1] = a.nsp > 1 ? a.sp[1] : a.sp[0];
+  n.ph = a.ph;
+  n.f = a.f;
+  n.C = a.C;
+  n.o = a.o;
+  n.step = a.step;
+  n.d_step = a.d_step;
+  n.mlp_frag = a.mlp_frag;
+  n.mlp_fw = a.mlp_fw;
+  n.net_rec = a.net_rec;
+  n.net_n = a.net_n;
+  n.net_cap = a.net_cap;
+  if (fm == QED_FIELDS_UNIFORM) return launch_net_emit_t<FM_UNIFORM>(c, n, st);
+  if (fm == QED_FIELDS_PER_PARTICLE) return launch_net_emit_t<FM_PER_PARTICLE>(c, n, st);
+  return launch_net_emit_t<FM_GRID>(c, n, st);
+}
+
 template <int FM, int MODE, bool MLP>
 cudaError_t launch_onepass_t(qed_ctx *c, const OnePassArgs &a, cudaStream_t st) {
-  size_t off[5];
-  const size_t sm = onepass_layout<FM>(a, MLP, off);
+  size_t off[4];
+  const size_t sm = onepass_layout<FM>(a, off);
   bool dflt = true;
   for (int k = 0; k < QED_SCHED_PARAMS; ++k) dflt = dflt && sched_param(c, k) == sched_default(k);
   auto kern = dflt ? k_lepton_onepass<FM, MODE, MLP, true> : k_lepton_onepass<FM, MODE, MLP, false>;
@@ -590,18 +787,26 @@ cudaError_t launch_lepton_onepass(qed_ctx *c, const qed_species *s0, const qed_s
   a.chi_tab_lo = (float)exp(c->gl.lo);
   a.chi_tab_hi = (float)exp(c->gl.hi);
   a.mlp_frag = c->mlp_frag;
-  a.mlp_w = c->mlp_w;
+  a.mlp_fw = c->mlp_fw;
+  a.net_rec = c->net_rec;
+  a.net_n = c->net_n;
+  a.net_cap = c->net_cap;
   a.emit_lanes = sched_param(c, QED_SCHED_EMIT_LANES);
   a.round_lanes = sched_param(c, QED_SCHED_ROUND_LANES);
   a.scan_iters = (sched_param(c, QED_SCHED_SCAN_DRAWS) + 3) / 4;
   a.scan_left = sched_param(c, QED_SCHED_SCAN_LEFT);
   a.qtrig = min(sched_param(c, QED_SCHED_QUEUE_TRIGGER), QCAP - 31);
-  const bool mlp = c->cfg.sampler == QED_SAMPLER_MLP && c->mlp_ready;
+  const bool mlp = c->cfg.sampler == QED_SAMPLER_MLP && c->mlp_ready && c->net_rec;
+  cudaError_t e;
   if (mode == MODE_EMIT)
-    return mlp ? launch_onepass_m<MODE_EMIT, true>(c, a, f->mode, st)
-               : launch_onepass_m<MODE_EMIT, false>(c, a, f->mode, st);
-  return mlp ? launch_onepass_m<MODE_FUSED, true>(c, a, f->mode, st)
-             : launch_onepass_m<MODE_FUSED, false>(c, a, f->mode, st);
+    e = mlp ? launch_onepass_m<MODE_EMIT, true>(c, a, f->mode, st)
+            : launch_onepass_m<MODE_EMIT, false>(c, a, f->mode, st);
+  else
+    e = mlp ? launch_onepass_m<MODE_FUSED, true>(c, a, f->mode, st)
+            : launch_onepass_m<MODE_FUSED, false>(c, a, f->mode, st);
+  if (e == cudaSuccess) e = prof_mark(c, 1, st);
+  if (e == cudaSuccess && mlp) e = launch_net_emit(c, a, f->mode, st);
+  return e;
 }
 
 }  // namespace qed

@@ -2171,8 +2171,10 @@ cudaError_t launch_lepton(qed_ctx *c, const qed_species *s0, const qed_species *
                           cudaStream_t st) {
   if (sizeof(Real) == 4 && mode != MODE_PUSH && c->cfg.append_order == QED_APPEND_ANY &&
       c->cfg.generator == QED_GEN_METHOD_I) {
+    // marks: 1 after the single-pass kernel (recorded by it), 2..5 after the
+    // learned sampler's dense pass, if any
     cudaError_t e = launch_lepton_onepass(c, s0, s1, ph, f, step, mode, st);
-    for (int k = 1; k <= 5 && e == cudaSuccess; ++k) e = prof_mark(c, k, st);
+    for (int k = 2; k <= 5 && e == cudaSuccess; ++k) e = prof_mark(c, k, st);
     return e;
   }
   LeptonArgs<Real> a{};

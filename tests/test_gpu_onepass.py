@@ -250,3 +250,64 @@ def test_unordered_runs_agree_as_sets(api, W):
     for c in sa:
         np.testing.assert_array_equal(sa[c], sb[c])
     assert a[3]["emit_events"] == b[3]["emit_events"] > 1000
+
+
+@pytest.fixture(scope="module")
+def mlp_weights(api):
+    """A network trained briefly (accuracy does not matter for equality)."""
+    from oracle import mlp
+    ctx = api.qed_init_tables(api.config(sampler=1))
+    api.qed_mlp_load(ctx, mlp.init_params(seed=0).astype(np.float32))
+    api.qed_mlp_train(ctx, 100_000_000, lr=6e-3, seed=7)
+    return api.qed_mlp_get(ctx)
+
+
+def _run_mlp(api, order, st, cap, weights, dt, max_particles, steps=1):
+    ctx = api.qed_init_tables(api.config(dt=dt, seed=77, sampler=1, append_order=order,
+                                         max_particles=max_particles))
+    api.qed_mlp_load(ctx, weights)
+    e = api.Species.empty(cap, -1, fields=True).load(**st)
+    g = api.Species.empty(cap, 0, fields=True)
+    for s in range(steps):
+        api.qed_step_fused(ctx, e, api.Species.empty(0, 1, fields=True), g, api.Fields.per_particle(), 3 + s)
+    torch.cuda.synchronize()
+    return e.host(), g.host(), api.qed_read_counters(ctx)
+
+
+@pytest.mark.parametrize("case", ["dense", "one_substep"])
+def test_unordered_learned_sampler_equals_ordered(api, W, mlp_weights, case):
+    """With the learned sampler the single pass defers the network's emissions
+    (one-sub-step leptons in its domain) to a dense pass over records; it gives
+    the ordered path's particles and photons, also when nearly a fifth of the
+    leptons emit that way (the records hold one per lepton)."""
+    if case == "dense":
+        n = 100_000
+        st, _, _ = W.chi_target(n, seed=81, chi_lo=1e-2, chi_hi=10.0, g_lo=200, g_hi=5e3)
+        st = to32(st)
+        dt, maxp, cap, steps = 0.01, 1 << 20, 4 * n, 2
+    else:
+        # identical electrons at chi = 1 with W Dt just below 0.2: about 19% of
+        # them emit in their one sub-step
+        n = 1 << 16
+        gamma, chi = 1000.0, 1.0
+        pm = np.sqrt(gamma ** 2 - 1)
+        bz = chi * api.config().a_S / pm
+        z = np.zeros(n)
+        st = to32(dict(x=z, y=z, z=z, px=np.full(n, pm), py=z, pz=z, w=np.ones(n),
+                       id=np.arange(n, dtype=np.uint64), ex=z, ey=z, ez=z, bx=z, by=z, bz=np.full(n, bz)))
+        ctx0 = api.qed_init_tables(api.config())
+        W0 = float(api.qed_rates(ctx0, 0, torch.tensor([chi], device="cuda"),
+                                 torch.tensor([gamma], device="cuda"))[0])
+        dt, maxp, cap, steps = 0.19 / W0, n, n, 1
+    o = _run_mlp(api, 0, st, cap, mlp_weights, dt, maxp, steps)
+    u = _run_mlp(api, 1, st, cap, mlp_weights, dt, maxp, steps)
+    # the electrons present at the start by slot, pair electrons (appended in
+    # the photons' order, which differs) by id
+    _close_all(o[0], u[0], "leptons", slice(0, n))
+    _close_all(_sorted({k: v[n:] for k, v in o[0].items()}), _sorted({k: v[n:] for k, v in u[0].items()}),
+               "pair electrons")
+    assert set(o[1]) == set(u[1])
+    _close_all(_sorted(o[1]), _sorted(u[1]), "photons")
+    _same_counters(o[2], u[2])
+    if case == "one_substep":
+        assert o[2]["emit_events"] > 0.15 * n
