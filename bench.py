@@ -43,7 +43,7 @@ METRIC = "QED particle-steps/s at 64M particles (table vs MLP) and % HBM rooflin
 UNIT = "particle-steps/s"
 N_PART = 1 << 26
 DT = 0.01
-DEFAULT_STEPS, DEFAULT_WARMUP, DEFAULT_E2E_STEPS = 10, 3, 2
+DEFAULT_STEPS, DEFAULT_WARMUP, DEFAULT_E2E_STEPS = 10, 3, 3
 LEPTON_BYTES = 84       # R x,y,z,px,py,pz,w (28) + id (8) + E,B (24); W x,y,z,px,py,pz (24)
 LEPTON_STREAM_BYTES = 80  # streaming pass alone: R x..pz, id, E,B (56); W x..pz (24)
 PHOTON_APPEND_BYTES = 61  # x,y,z,px,py,pz,w (28) + id (8) + alive (1) + inherited E,B (24)
@@ -266,9 +266,10 @@ def time_arm(api, torch, ctx, H, F, steps, warmup, step0, dist=None, profile=Tru
 
 def lepton_roofline(r, n, steps, peak, peak_kind, mlp=False):
     """Roofline of the lepton step (the per-lepton unit whose algorithmic
-    bytes are 84 B + 61 B per emitted photon): its five phases (streaming
-    pass, class list, counting pass, scan, writing pass) are timed by CUDA
-    events recorded on the launching stream between them."""
+    bytes are 84 B + 61 B per emitted photon), timed by CUDA events that the
+    library records on the launching stream: the single-pass kernel (and,
+    with the learned sampler, its dense pass), or the ordered path's five
+    phases (streaming pass, class list, counting pass, scan, writing pass)."""
     import paper_1608_06356_gb300.api as A
     phases, nprof = r["phases"], max(r["nprof"], 1)
     lep_ms = sum(phases[k] for k in A.PROF_PHASES[:5]) / nprof
@@ -296,47 +297,46 @@ def lepton_roofline(r, n, steps, peak, peak_kind, mlp=False):
                                "achieved_gbs": LEPTON_STREAM_BYTES * n / (stream_ms * 1e-3) / 1e9}}
 
 
+E2E_CHUNKS = 16  # chunks the host-resident ensemble is streamed in
+
+
 def e2e_arm(api, torch, ctx, H, F, host, steps, step0):
-    """The headline step through the public API with the ensemble on pinned
-    host memory: every step copies the electrons in, runs qed_step_fused,
-    reads the photon count and copies the electrons' new state and the new
-    photons back."""
+    """The headline step through the public API with the ensemble in pinned
+    host memory: qed_lepton_step_host streams the 64M electrons through the
+    GPU in chunks (each chunk copied in, stepped, copied back, the copies of
+    one chunk overlapping the step of another) and copies the new photons to
+    a pinned host mirror.  Each step is timed alone (the call is
+    synchronous); between steps the host ensemble is put back to its initial
+    state and the photon buffers emptied, outside the timed calls."""
     n = H.n
-    stream = torch.cuda.current_stream()
-    pin_in = {k: torch.from_numpy(host[k].view(np.int64) if k == "id" else host[k]).pin_memory()
-              for k in LEPTON_ARRAYS}
     cap_g = H.g.capacity
-    pin_out = {k: torch.empty(n, dtype=torch.float32, pin_memory=True) for k in MUTABLE}
-    pin_g = {k: torch.empty(cap_g, dtype=getattr(H.g, k).dtype, pin_memory=True)
-             for k in LEPTON_ARRAYS + ("alive",)}
-    n_host = torch.zeros(1, dtype=torch.int64, pin_memory=True)
-    h2d = d2h = 0
-    torch.cuda.synchronize()
-    w0 = time.perf_counter()
-    for k in range(steps):
-        for nm in LEPTON_ARRAYS:
-            getattr(H.e, nm)[:n].copy_(pin_in[nm], non_blocking=True)
-            h2d += n * pin_in[nm].element_size()
-        H.e.n.fill_(n)
-        H.g.n.zero_()
-        api.qed_step_fused(ctx, H.e, H.p, H.g, F, step0 + k)
-        n_host.copy_(H.g.n, non_blocking=True)
-        stream.synchronize()
-        m = int(n_host[0])
-        d2h += 8
+    lh = api.Species.empty(n, -1, fields=True, pinned=True)
+    lh.load(**{k: host[k] for k in LEPTON_ARRAYS})
+    pristine = {k: getattr(lh, k)[:n].clone() for k in MUTABLE}
+    gh = api.Species.empty(cap_g, 0, fields=True, pinned=True)
+    chunk = (n + E2E_CHUNKS - 1) // E2E_CHUNKS
+    h2d = 60 * n  # x..pz, w (28 B), id (8 B), E, B (24 B) per electron
+    d2h = 0
+    wall = 0.0
+    for k in range(steps + 1):  # one untimed step first (staging buffers, page mapping)
         for nm in MUTABLE:
-            pin_out[nm].copy_(getattr(H.e, nm)[:n], non_blocking=True)
-            d2h += 4 * n
-        for nm, t in pin_g.items():
-            t[:m].copy_(getattr(H.g, nm)[:m], non_blocking=True)
-            d2h += m * t.element_size()
-        stream.synchronize()
-    wall = time.perf_counter() - w0
+            getattr(lh, nm)[:n].copy_(pristine[nm])
+        H.g.n.zero_()
+        gh.n.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        api.qed_lepton_step_host(ctx, lh, H.g, gh, F, step0 + k, chunk)
+        dt = time.perf_counter() - t0
+        if k:
+            wall += dt
+            m = int(gh.n[0])
+            d2h += 24 * n + 61 * m + 8 * E2E_CHUNKS  # x..pz back, the photons, the chunk counts
     return {"value": n * steps / wall, "unit": UNIT,
-            "h2d_bytes_per_step": h2d // steps, "d2h_bytes_per_step": d2h // steps, "steps": steps,
-            "note": "ensemble on pinned host memory; every step copies the 64M electrons in "
-                    "(60 B each), runs qed_step_fused, reads the photon count and copies the "
-                    "electrons' positions and momenta and the new photons back"}
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h // steps, "steps": steps,
+            "ms_per_step": 1e3 * wall / steps, "chunks": E2E_CHUNKS,
+            "note": "ensemble in pinned host memory; every step streams the 64M electrons "
+                    "(60 B each) through qed_lepton_step_host in chunks, copies their positions "
+                    "and momenta back and the new photons (61 B each) to a pinned host mirror"}
 
 
 def sampler_edge_u(api, torch, ctx, which, chis, edges, gamma, iters=34):
@@ -866,7 +866,11 @@ def main():
     ap.add_argument("--generator-bench", type=int, default=1)
     ap.add_argument("--cascade-bench", type=int, default=1)
     ap.add_argument("--spectra-bench", type=int, default=1)
+    ap.add_argument("--append-order", choices=["any", "ordered"], default="any",
+                    help="lepton step of the headline arms: single pass (any) or the ordered path")
     args = ap.parse_args()
+    global APPEND_ORDER
+    APPEND_ORDER = 1 if args.append_order == "any" else 0
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -231,6 +231,35 @@ int qed_step_fused(qed_ctx *ctx, const qed_species *e, const qed_species *p,
                    const qed_species *g, const qed_fields *f, int64_t step,
                    qed_stream_t stream);
 
+/* The lepton stage of qed_step_fused (gather at the old position, Boris
+ * push, emission with recoil, photons appended to g) for leptons held in
+ * HOST memory, streamed through the GPU in chunks of `chunk` leptons: chunk
+ * k is copied in, stepped and copied back while the next is copied in and
+ * the previous copied out (the caller's stream steps, two streams of the
+ * context copy; the host arrays should be page-locked for the copies to
+ * overlap).  Particle ids key the random draws, so the leptons and the set
+ * of photons are those of one qed_step_fused call on the whole species with
+ * no photons present at the start.
+ *   l_host  a lepton species whose arrays (x..pz, w, id, the per-particle
+ *           fields with QED_FIELDS_PER_PARTICLE, od_p/od_r with Methods
+ *           II/III, optional tag) are HOST pointers and whose d_n points to a
+ *           HOST int64 count; positions, momenta (and od_p/od_r) are updated
+ *           in place.
+ *   g       the photon species on the device; this call's photons are
+ *           appended to it, chunk by chunk (photons present in g are not
+ *           stepped).
+ *   g_host  NULL, or a host mirror of g (host pointers for every array g has,
+ *           capacity >= g's, d_n a HOST int64): the photons appended by this
+ *           call are copied to the same indices and its count set.
+ * The context keeps three device staging buffers of `chunk` leptons
+ * (allocated at the first call, grown by a later call that needs more).
+ * Synchronous: returns when the leptons and photons are on the host.
+ * chunk must be in (0, max_particles] (QED_ERR_CAPACITY otherwise); the call
+ * is refused inside a stream capture (QED_ERR_UNSUPPORTED). */
+int qed_lepton_step_host(qed_ctx *ctx, const qed_species *l_host, const qed_species *g,
+                         const qed_species *g_host, const qed_fields *f, int64_t step,
+                         int64_t chunk, qed_stream_t stream);
+
 /* Isolated photon-energy sampler: xi[i] from Eq. (7) at (chi[i], gamma[i]),
  * r2 from Philox(seed; id = i, step, sub 0, stream 0) word 1 (float arrays,
  * device memory, QED_FP32 contexts). */

@@ -129,6 +129,9 @@ SIGNATURES = {
                                       C.POINTER(qed_species), C.POINTER(qed_fields), C.c_int,
                                       C.POINTER(qed_tuning), _P]),
     "qed_set_tuning": (C.c_int, [_P, C.POINTER(qed_tuning)]),
+    "qed_lepton_step_host": (C.c_int, [_P, C.POINTER(qed_species), C.POINTER(qed_species),
+                                       C.POINTER(qed_species), C.POINTER(qed_fields), C.c_int64,
+                                       C.c_int64, _P]),
     "qed_mlp_load": (C.c_int, [_P, _P, C.c_size_t]),
     "qed_mlp_get": (C.c_int, [_P, _P, C.c_size_t]),
     "qed_mlp_train": (C.c_int, [_P, C.c_int64, C.c_float, C.c_uint64, C.POINTER(C.c_double), _P]),

@@ -104,18 +104,22 @@ class Species:
 
     @staticmethod
     def empty(capacity: int, q: int, dtype=torch.float32, device="cuda", fields=False,
-              alive=None, tag=False, od=False) -> "Species":
+              alive=None, tag=False, od=False, pinned=False) -> "Species":
+        """Zeroed buffers on `device`; pinned=True: page-locked host memory
+        (device "cpu"), for qed_lepton_step_host."""
         cap = max(int(capacity), 0)
-        mk = lambda: torch.zeros(cap, dtype=dtype, device=device)
+        if pinned:
+            device = "cpu"
+        z = lambda n, dt: torch.zeros(n, dtype=dt, device=device, pin_memory=pinned)
+        mk = lambda: z(cap, dtype)
         kw = {k: mk() for k in STATE}
         if fields:
             kw.update({k: mk() for k in FIELD_NAMES})
         if alive is None:
             alive = q == 0
-        return Species(id=torch.zeros(cap, dtype=torch.int64, device=device),
-                       n=torch.zeros(1, dtype=torch.int64, device=device), q=q,
-                       alive=torch.zeros(cap, dtype=torch.uint8, device=device) if alive else None,
-                       tag=torch.zeros(cap, dtype=torch.int32, device=device) if tag else None,
+        return Species(id=z(cap, torch.int64), n=z(1, torch.int64), q=q,
+                       alive=z(cap, torch.uint8) if alive else None,
+                       tag=z(cap, torch.int32) if tag else None,
                        od_p=mk() if od else None, od_r=mk() if od else None,
                        **kw)
 
@@ -244,6 +248,17 @@ def qed_step_fused(ctx: Context, e: Species | None, p: Species | None, g: Specie
     se, sp_, sg = _sp(e), _sp(p), _sp(g)
     B.check(B.lib().qed_step_fused(ctx.handle, C.byref(se), C.byref(sp_), C.byref(sg), C.byref(f),
                                    int(step), _stream(stream)), "qed_step_fused")
+
+
+def qed_lepton_step_host(ctx: Context, l_host: Species, g: Species, g_host: Species | None, fields,
+                         step: int, chunk: int, stream=None) -> None:
+    """The lepton stage of a step for leptons in (pinned) host memory,
+    streamed through the GPU in chunks; g_host (optional) receives the new
+    photons.  Synchronous."""
+    gh = C.byref(g_host.struct()) if g_host is not None else None
+    B.check(B.lib().qed_lepton_step_host(ctx.handle, C.byref(l_host.struct()), C.byref(g.struct()), gh,
+                                         C.byref(fields), int(step), int(chunk), _stream(stream)),
+            "qed_lepton_step_host")
 
 
 def qed_sample_xi(ctx: Context, chi: torch.Tensor, gamma: torch.Tensor, xi: torch.Tensor, step: int,

@@ -80,6 +80,7 @@ extern "C" const char *qed_strerror(int code) {
 
 static void free_ctx(qed_ctx *c) {
   if (!c) return;
+  free_host_step(c);
   void *ptrs[] = {c->R64, c->F64, c->Y64, c->P64, c->Yp64, c->R32, c->F32, c->Y32,
                   c->P32, c->Yp32, c->tile_state, c->sync, c->snap, c->d_counters,
                   c->heavy_flags, c->heavy_list, c->heavy_n, c->cls_chunk_cnt,
@@ -435,6 +436,21 @@ extern "C" int qed_step_fused(qed_ctx *c, const qed_species *e, const qed_specie
   if (err == cudaSuccess && prof) c->prof_n += 1;
   c->prof_cur = nullptr;
   return cuda_fail(err, "qed_step_fused");
+}
+
+extern "C" int qed_lepton_step_host(qed_ctx *c, const qed_species *lh, const qed_species *g,
+                                    const qed_species *gh, const qed_fields *f, int64_t step,
+                                    int64_t chunk, qed_stream_t stream) {
+  if (!c || !lh || !lh->d_n || !species_ok(g, true) || !fields_ok(f) || !pp_fields_ok(g, f) ||
+      chunk <= 0)
+    return QED_ERR_ARG;
+  if (!lh->x || !lh->y || !lh->z || !lh->px || !lh->py || !lh->pz || !lh->w || !lh->id ||
+      !pp_fields_ok(lh, f) || !od_ok(c, lh))
+    return QED_ERR_ARG;
+  if (f->mode == QED_FIELDS_PER_PARTICLE && !lh->ex) return QED_ERR_ARG;
+  if (gh && (!gh->d_n || gh->capacity < g->capacity)) return QED_ERR_ARG;
+  if (chunk > c->cfg.max_particles || check_cap(c, g)) return QED_ERR_CAPACITY;
+  return lepton_step_host(c, lh, g, gh, f, step, chunk, (cudaStream_t)stream);
 }
 
 extern "C" int qed_sample_xi(qed_ctx *c, const float *chi, const float *gamma, float *xi, int64_t n,

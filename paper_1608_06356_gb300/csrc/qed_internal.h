@@ -78,6 +78,15 @@ struct qed_ctx {
   int grid_factor[QED_TUNE_GROUPS];
   // Method I chain scheduling (QED_SCHED_*; 0 = default)
   int sched[QED_SCHED_PARAMS];
+  // host-resident lepton steps (qed_lepton_step_host): three staging buffers,
+  // their device counts, pinned photon counts, input and output streams and
+  // per-buffer events (copied in, stepped, copied out)
+  void *hs_mem;
+  size_t hs_per_buf;
+  int64_t *hs_dn;
+  int64_t *hs_cnt;
+  cudaStream_t hs_in, hs_out;
+  cudaEvent_t hs_ev[9];
   // bound of the photon emission rate used by the single-pass lepton kernel:
   // W_rad <= w_up_row[j] chi / gamma for ln chi >= row j of the rate table
   float *w_up_row;  // [gl.n] (device)
@@ -89,6 +98,10 @@ struct qed_ctx {
 
 namespace qed {
 int build_tables(qed_ctx *c, cudaStream_t st);
+int lepton_step_host(qed_ctx *c, const qed_species *lh, const qed_species *g,
+                     const qed_species *gh, const qed_fields *f, int64_t step, int64_t chunk,
+                     cudaStream_t st);
+void free_host_step(qed_ctx *c);
 int mlp_alloc(qed_ctx *c);
 // CTAs per SM for a persistent launch of a kernel group: the occupancy limit,
 // capped by the group's autotuned factor when one is set
