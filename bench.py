@@ -47,6 +47,10 @@ DEFAULT_STEPS, DEFAULT_WARMUP, DEFAULT_E2E_STEPS = 10, 3, 3
 LEPTON_BYTES = 84       # R x,y,z,px,py,pz,w (28) + id (8) + E,B (24); W x,y,z,px,py,pz (24)
 LEPTON_STREAM_BYTES = 80  # streaming pass alone: R x..pz, id, E,B (56); W x..pz (24)
 PHOTON_APPEND_BYTES = 61  # x,y,z,px,py,pz,w (28) + id (8) + alive (1) + inherited E,B (24)
+# DRAM bytes of one k_lepton_onepass launch of the headline workload (2^26 electrons, table
+# sampler), dram__bytes_read.sum + dram__bytes_write.sum = 4.14 + 2.40 GB from one ncu capture
+# of the full-size run (profiles/dram_lepton_onepass_64M.txt); reported only for that workload
+LEPTON_ONEPASS_TRAFFIC_64M = 6.54e9
 # photons a fresh electron of the headline ensemble emits per step: the mean of
 # W_rad Dt over the ensemble is 0.184 (an upper bound of the mean event count);
 # the photon buffer holds 1.6x that
@@ -284,9 +288,11 @@ def lepton_roofline(r, n, steps, peak, peak_kind, mlp=False):
                        "k_sub_scan + k_substep_write_coop + k_substep_replay"),
             "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "peak_source": f"{peak_kind} HBM copy (MEASURED_PEAKS.json hbm_gbs)",
-            "traffic": None,
-            "traffic_note": "per-launch DRAM bytes of the lepton kernels are in profiles/ "
-                            "(ncu capture of the same kernels at 4M electrons, scaled by units)",
+            "traffic": (LEPTON_ONEPASS_TRAFFIC_64M if APPEND_ORDER and not mlp and n == N_PART else None),
+            "traffic_note": ("dram__bytes_read.sum + dram__bytes_write.sum of one launch, ncu capture "
+                             "of this workload (profiles/dram_lepton_onepass_64M.txt)"
+                             if APPEND_ORDER and not mlp and n == N_PART else
+                             "not captured for this kernel and size"),
             "bytes_per_launch": lep_bytes, "ms_per_launch": lep_ms,
             "algorithmic_bytes": "84 B per lepton + 61 B per emitted photon",
             "emitted_per_step": emitted,
