@@ -3,11 +3,12 @@
 Headline workload (one step = one qed_step_fused pass): 2^26 = 64M electrons
 with chi log-uniform in [1e-3, 1e2] and gamma log-uniform in [1e2, 1e4],
 per-particle fields (B perpendicular to p, |B| = chi a_S/|p|, E = 0),
-Dt = 0.01 / omega0, FP32 state.  Every step starts from the same ensemble:
-the electrons' positions and momenta are restored from a device copy and the
-photon buffer is emptied before the step (both inside the timed region), so
-each step advances exactly 64M electrons and the work per step does not
-drift with the step count.  Two arms on identical inputs: the table sampler
+Dt = 0.01 / omega0, FP32 state.  Every step starts from the same momenta:
+they are restored from a device copy and the photon buffer is emptied before
+the step (inside the timed region); the positions keep advancing, which with
+per-particle fields changes nothing the step computes.  So each step
+advances exactly 64M electrons and the work per step does not drift with the
+step count.  Two arms on identical inputs: the table sampler
 and the learned sampler (network trained here on the device).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
@@ -43,7 +44,7 @@ METRIC = "QED particle-steps/s at 64M particles (table vs MLP) and % HBM rooflin
 UNIT = "particle-steps/s"
 N_PART = 1 << 26
 DT = 0.01
-DEFAULT_STEPS, DEFAULT_WARMUP, DEFAULT_E2E_STEPS = 10, 3, 3
+DEFAULT_STEPS, DEFAULT_WARMUP, DEFAULT_E2E_STEPS = 10, 3, 5
 LEPTON_BYTES = 84       # R x,y,z,px,py,pz,w (28) + id (8) + E,B (24); W x,y,z,px,py,pz (24)
 LEPTON_STREAM_BYTES = 80  # streaming pass alone: R x..pz, id, E,B (56); W x..pz (24)
 PHOTON_APPEND_BYTES = 61  # x,y,z,px,py,pz,w (28) + id (8) + alive (1) + inherited E,B (24)
@@ -66,8 +67,9 @@ def workload_desc(n):
     return {"workload": f"chi-target ensemble of {n} electrons (chi log-uniform [1e-3,1e2], gamma "
                         "log-uniform [1e2,1e4], per-particle B perp p, E=0, Dt=0.01), one fused step "
                         "(gather+Boris+chi+rate+Method I sub-steps+xi+recoil+photon append; photon "
-                        "stage empty) per step; every step starts from the same ensemble (positions "
-                        "and momenta restored from a device copy, photon buffer emptied, both timed)",
+                        "stage empty) per step; every step starts from the same momenta (restored "
+                        "from a device copy, photon buffer emptied, both timed; positions keep "
+                        "advancing, which with per-particle fields changes no chi or rate)",
             "particles_per_step": n, "dt": DT, "precision": "fp32 state, fp64 chi where it cancels",
             "append_order": "any (single-pass lepton kernel; photons as a set identical to the "
                             "ordered path's)" if APPEND_ORDER else "ordered",
@@ -211,9 +213,14 @@ LEPTON_ARRAYS = ("x", "y", "z", "px", "py", "pz", "w", "id", "ex", "ey", "ez", "
 
 class Headline:
     """The headline ensemble on the device: electrons whose positions and
-    momenta live in one [6, capacity] block, a pristine copy of them, and the
-    positron and photon buffers.  `restore()` puts the ensemble back into its
-    initial state (six device copies and three count writes)."""
+    momenta live in one [6, capacity] block, a pristine copy of the momenta,
+    and the positron and photon buffers.  `restore()` puts the momenta back
+    into their initial state (three device copies) and empties the photon
+    and positron buffers, before every step.  The positions keep advancing:
+    with per-particle fields they enter neither chi nor the rates, so every
+    step does the same work."""
+
+    RESTORED = ("px", "py", "pz")
 
     def __init__(self, api, torch, n, host):
         cap_e, cap_p, cap_g, self.max_particles = capacities(n)
@@ -224,16 +231,16 @@ class Headline:
         for r, k in enumerate(MUTABLE):
             setattr(e, k, self.blk[r])
         e.load(**host)
-        self.pristine = self.blk[:, :n].clone()
+        self.rows = [MUTABLE.index(k) for k in self.RESTORED]
+        self.pristine = self.blk[self.rows, :n].clone()
         self.e = e
         self.p = api.Species.empty(cap_p, +1, fields=True)
         self.g = api.Species.empty(cap_g, 0, fields=True)
 
     def restore(self):
-        # one contiguous device copy per array (a 2-D strided copy of the
-        # [6, n] block runs at about half the bandwidth)
-        for r in range(len(MUTABLE)):
-            self.blk[r, :self.n].copy_(self.pristine[r])
+        # one contiguous device copy per array
+        for q, r in enumerate(self.rows):
+            self.blk[r, :self.n].copy_(self.pristine[q])
         self.e.n.fill_(self.n)
         self.p.n.zero_()
         self.g.n.zero_()
@@ -326,8 +333,9 @@ def e2e_arm(api, torch, ctx, H, F, host, steps, step0):
     chunk = (n + E2E_CHUNKS - 1) // E2E_CHUNKS
     h2d = 60 * n  # x..pz, w (28 B), id (8 B), E, B (24 B) per electron
     d2h = 0
-    wall = 0.0
-    for k in range(steps + 1):  # one untimed step first (staging buffers, page mapping)
+    times = []
+    warm = 2  # untimed steps first (staging buffers, first use of the pinned pages)
+    for k in range(steps + warm):
         for nm in MUTABLE:
             getattr(lh, nm)[:n].copy_(pristine[nm])
         H.g.n.zero_()
@@ -336,13 +344,15 @@ def e2e_arm(api, torch, ctx, H, F, host, steps, step0):
         t0 = time.perf_counter()
         api.qed_lepton_step_host(ctx, lh, H.g, gh, F, step0 + k, chunk)
         dt = time.perf_counter() - t0
-        if k:
-            wall += dt
+        if k >= warm:
+            times.append(dt)
             m = int(gh.n[0])
             d2h += 24 * n + 61 * m + 8 * E2E_CHUNKS  # x..pz back, the photons, the chunk counts
+    wall = sum(times)
     return {"value": n * steps / wall, "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h // steps, "steps": steps,
-            "ms_per_step": 1e3 * wall / steps, "chunks": E2E_CHUNKS,
+            "ms_per_step": 1e3 * wall / steps, "ms_each_step": [round(1e3 * t, 2) for t in times],
+            "chunks": E2E_CHUNKS,
             "note": "ensemble in pinned host memory; every step streams the 64M electrons "
                     "(60 B each) through qed_lepton_step_host in chunks, copies their positions "
                     "and momenta back and the new photons (61 B each) to a pinned host mirror"}
@@ -455,11 +465,13 @@ def batched_runs_bench(api, torch, mlp_weights, steps=4):
                 g = api.Species.empty(int(0.4 * n * (steps + 2)), 0, fields=True, tag=True)
                 tuning = api.qed_autotune_groups(ctx, e, p, g, F, reps=2)
                 res["tuning"] = {"grid_factor_ctas_per_sm": tuning["grid_factor"],
+                                 "chain_scheduling": tuning["sched"],
                                  "ms_per_step_tuned": tuning["ms_per_step"],
-                                 "ms_per_factor": tuning["ms"]}
+                                 "ms_per_factor": tuning["ms"],
+                                 "ms_per_scheduling_value": tuning["sched_ms"]}
                 del e, p, g
             else:
-                api.qed_set_tuning(ctx, tuning["grid_factor"])
+                api.qed_set_tuning(ctx, tuning["grid_factor"], tuning["sched"])
             e = api.Species.empty(2 * n, -1, fields=True, tag=True).load(**host)
             p = api.Species.empty(n, 1, fields=True, tag=True)
             g = api.Species.empty(int(0.4 * n * (steps + 2)), 0, fields=True, tag=True)
