@@ -189,7 +189,30 @@ struct Consts {
   // the same constants in single precision, so that the FP32 path does no FP64 work
   float f_dt, f_wdt_max, f_xi_min_energy, f_chi_pair_min, f_spec_lo, f_spec_scale, f_inv_aS,
       f_alpha_aS;
+  // Philox round keys of the seed: rk[2r] = k0 + r 0x9E3779B9, rk[2r+1] = k1 + r 0xBB67AE85
+  uint32_t rk[20];
 };
+
+// A draw of the context's streams: philox4x32_10 with the round keys taken
+// from Consts (kernel parameters, so each key is an operand of the xor, not a
+// running sum).
+__device__ __forceinline__ U4 draw(const Consts &C, uint64_t id, int64_t step, int64_t sub,
+                                   uint32_t stream) {
+  U4 c{(uint32_t)id, (uint32_t)(id >> 32), (uint32_t)step,
+       (uint32_t)(((uint64_t)sub << 2) | stream)};
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = U4{hi1 ^ c.y ^ C.rk[2 * r], lo1, hi0 ^ c.w ^ C.rk[2 * r + 1], lo0};
+  }
+  return c;
+}
+
+__device__ __forceinline__ EmitWords emit_words(const Consts &C, uint64_t id, int64_t step, int64_t k) {
+  const U4 r = draw(C, id, step, k >> 1, STREAM_EMIT);
+  return (k & 1) ? EmitWords{r.z, r.w} : EmitWords{r.x, r.y};
+}
 
 // Constant in the working precision.
 template <class Real> __device__ __forceinline__ Real sel(double d, float f);

@@ -293,8 +293,8 @@ __global__ void __launch_bounds__(OP_THREADS, 5) k_lepton_onepass(OnePassArgs A)
             // sub-steps 2j .. 2j+3 from the draws j and j+1 (words 0-1 and
             // 2-3 of each); a chain at an odd sub-step starts at 2j+1
             const int64_t j = k >> 1;
-            const U4 ra = draw(A.C.seed, pid, step_, j, STREAM_EMIT);
-            const U4 rb = draw(A.C.seed, pid, step_, j + 1, STREAM_EMIT);
+            const U4 ra = draw(A.C, pid, step_, j, STREAM_EMIT);
+            const U4 rb = draw(A.C, pid, step_, j + 1, STREAM_EMIT);
             const uint32_t w1[4] = {ra.x, ra.z, rb.x, rb.z}, w2[4] = {ra.y, ra.w, rb.y, rb.w};
             const int q0 = (int)(k & 1);
 #pragma unroll
@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(OP_THREADS, 5) k_lepton_onepass(OnePassArgs A)
             int64_t i;
             slot_index(hslot, si, i);
             const Sp<float> &S = A.sp[si];
-            const U4 cid = draw(A.C.seed, pid, step_, k, STREAM_PHOTON_ID);
+            const U4 cid = draw(A.C, pid, step_, k, STREAM_PHOTON_ID);
             write_child(A.ph, pos, S.x[i], S.y[i], S.z[i], eph * nx, eph * ny, eph * nz, S.w[i],
                         (uint64_t)cid.x | ((uint64_t)cid.y << 32), E, B, S.tag ? S.tag[i] : 0u);
           }
@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(OP_THREADS, 5) k_lepton_onepass(OnePassArgs A)
           const float wdt_up = r_div(__ldg(A.w_up_row + j) * dt * chi, g);
           bool done = false;
           if (wdt_up <= wdt_max) {
-            const U4 r = draw(A.C.seed, pid, step_, 0, STREAM_EMIT);
+            const U4 r = draw(A.C, pid, step_, 0, STREAM_EMIT);
             done = !(wdt_up > unif<float>(r.x));
           }
           if (done) {
@@ -676,7 +676,7 @@ __global__ void __launch_bounds__(NET_THREADS) k_net_emit(NetArgs A) {
         tl.dropped += 1;
         tl.status |= QED_STATUS_CAPACITY;
       } else {
-        const U4 cid = draw(A.C.seed, S.id[i], step_, 0, STREAM_PHOTON_ID);
+        const U4 cid = draw(A.C, S.id[i], step_, 0, STREAM_PHOTON_ID);
         write_child(A.ph, pos, S.x[i], S.y[i], S.z[i], eph * nx, eph * ny, eph * nz, S.w[i],
                     (uint64_t)cid.x | ((uint64_t)cid.y << 32), E, B, S.tag ? S.tag[i] : 0u);
       }

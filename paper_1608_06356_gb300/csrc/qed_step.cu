@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 3 : 2) k_lepton_stre
           // (II) or P_cum > r3 (III); r3 is word 3 of the emission draw when
           // not drawn yet.  The emission itself (and the new P_cum, r3) is the
           // counting pass's, as a one-sub-step particle with an event.
-          const U4 r = draw(A.C.seed, pid, step_, 0, STREAM_EMIT);
+          const U4 r = draw(A.C, pid, step_, 0, STREAM_EMIT);
           Real r3 = S.od_r[i];
           const bool fresh = !(r3 > (Real)0);
           if (fresh) r3 = unif<Real>(r.w);
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 3 : 2) k_lepton_stre
           const Real q = r_div(wdt, wdt_max);
           flag = q <= (Real)3 ? 2 : (q <= (Real)7 ? 3 : (q <= (Real)15 ? 4 : 5));
         } else {
-          U4 r = draw(A.C.seed, pid, step_, 0, STREAM_EMIT);
+          U4 r = draw(A.C, pid, step_, 0, STREAM_EMIT);
           if (wdt > unif<Real>(r.x)) flag = 1;  // one sub-step with an event
         }
         if (flag == 0) {
@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 && !MLP ? 3 : 2) k_sub
           if (A.C.generator != GEN_METHOD_I) {
             // Methods II/III: the streaming pass found the event; one photon,
             // its xi from word 1 of the step's emission draw
-            const U4 r = draw(A.C.seed, pid, step_, 0, STREAM_EMIT);
+            const U4 r = draw(A.C, pid, step_, 0, STREAM_EMIT);
             N = 1;
             dts = dt;
             wy = r.y;
@@ -551,7 +551,7 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 && !MLP ? 3 : 2) k_sub
       if (state == LS_SCAN) {
         const Real thr = ro.W * dts;
         for (int s = 0; s < A.scan_draws; s += 2) {
-          const U4 r = draw(A.C.seed, pid, step_, k >> 1, STREAM_EMIT);
+          const U4 r = draw(A.C, pid, step_, k >> 1, STREAM_EMIT);
           if (!(k & 1)) {
             if (thr > unif<Real>(r.x)) { wy = r.y; state = LS_PEND; break; }
             if (++k >= N) { finish(); break; }
@@ -716,7 +716,7 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 4 : 2) k_substep_wri
         tl.status |= QED_STATUS_CAPACITY;
         continue;
       }
-      const U4 cid = draw(A.C.seed, pid, step_, kk, STREAM_PHOTON_ID);
+      const U4 cid = draw(A.C, pid, step_, kk, STREAM_PHOTON_ID);
       write_child(A.ph, out, x, y, z, eph * ux, eph * uy, eph * uz, w,
                   (uint64_t)cid.x | ((uint64_t)cid.y << 32), E, B, ptag);
     }
@@ -865,7 +865,7 @@ __global__ void __launch_bounds__(TILE, 2) k_substep_replay(LeptonArgs<Real> A) 
         tl.status |= QED_STATUS_CAPACITY;
         return;
       }
-      U4 cid = draw(A.C.seed, P.id, step_, kk, STREAM_PHOTON_ID);
+      U4 cid = draw(A.C, P.id, step_, kk, STREAM_PHOTON_ID);
       write_child(A.ph, out, P.x, P.y, P.z, eph * nx, eph * ny, eph * nz, P.w,
                   (uint64_t)cid.x | ((uint64_t)cid.y << 32), P.E, P.B, P.tag);
     };
@@ -880,7 +880,7 @@ __global__ void __launch_bounds__(TILE, 2) k_substep_replay(LeptonArgs<Real> A) 
     const Real dts = dt / (Real)N;
     uint32_t j = 0;
     for (int64_t kk = 0; kk < N && j < cnt; ++kk) {
-      const EmitWords r = emit_words(A.C.seed, P.id, step_, kk);
+      const EmitWords r = emit_words(A.C, P.id, step_, kk);
       if (!forced && !(ro.W * dts > unif<Real>(r.r1))) continue;
       XiOut<Real> xo = photon_xi(A.T.Y, A.T, ro.l, chi, ro.kmin, unif<Real>(r.r2), unif<Real>(~r.r2), dummy);
       Real g2 = g * xo.omxi, eph = g * xo.xi;
@@ -1245,7 +1245,7 @@ __global__ void __launch_bounds__(TILE, sizeof(Real) == 4 ? 4 : 2) k_photon_stre
         pid = A.ph.id[i];
       } else if (ro.W > (Real)0) {  // (most soft photons have W = 0: no id read)
         pid = A.ph.id[i];
-        U4 r = draw(A.C.seed, pid, step_, 0, STREAM_PAIR);
+        U4 r = draw(A.C, pid, step_, 0, STREAM_PAIR);
         if (wdt > unif<Real>(r.x)) flag = 1;
       }
       if (k > (Real)0) {
@@ -1375,7 +1375,7 @@ __device__ __forceinline__ uint32_t pair_chain(const PhotonArgs<Real> &A, const 
   }
   const Real dts = dt / (Real)N;
   for (int64_t s = 0; s < N; ++s) {
-    U4 r = draw(A.C.seed, P.id, step_, s, STREAM_PAIR);
+    U4 r = draw(A.C, P.id, step_, s, STREAM_PAIR);
     if (!(ro.W * dts > unif<Real>(r.x))) continue;
     XiOut<Real> xo = pair_xi(A.T.Yp, A.T, ro.l, unif<Real>(r.y), unif<Real>(~r.y));
     ge = xo.xi * P.k;
@@ -1473,7 +1473,7 @@ __global__ void __launch_bounds__(TILE) k_pair_write(PhotonArgs<Real> A) {
     }
     const Real ik = (Real)1 / P.k;
     const Real nx = P.px * ik, ny = P.py * ik, nz = P.pz * ik;
-    const U4 cid = draw(A.C.seed, P.id, step_, ks, STREAM_PAIR_ID);
+    const U4 cid = draw(A.C, P.id, step_, ks, STREAM_PAIR_ID);
     const Real pe = m_sqrt((ge - (Real)1) * (ge + (Real)1));
     const Real pp = m_sqrt((gp - (Real)1) * (gp + (Real)1));
     if (ne + off < A.el.cap)
@@ -1829,7 +1829,7 @@ __global__ void __launch_bounds__(TILE) k_sample_xi(SampleArgs A) {
     const bool active = i < A.n;
     float chi = active ? __ldcs(A.chi + i) : 1.f, g = active ? __ldcs(A.gamma + i) : 1e3f;
     RateOut<float> ro = photon_rate(sR, sF, A.T, A.C, chi, g, tl);
-    U4 r = draw(A.C.seed, (uint64_t)i, A.step, 0, STREAM_EMIT);
+    U4 r = draw(A.C, (uint64_t)i, A.step, 0, STREAM_EMIT);
     const float kap = photon_kappa(ro.kmin, unif<float>(r.y), unif<float>(~r.y));
     float Y = 0.f;
     bool in_mlp = false;
@@ -2004,6 +2004,10 @@ Consts consts_of(const qed_ctx *c) {
   k.f_spec_scale = (float)k.spec_scale;
   k.f_inv_aS = (float)k.inv_aS;
   k.f_alpha_aS = (float)k.alpha_aS;
+  for (int r = 0; r < 10; ++r) {
+    k.rk[2 * r] = (uint32_t)k.seed + (uint32_t)r * 0x9E3779B9u;
+    k.rk[2 * r + 1] = (uint32_t)(k.seed >> 32) + (uint32_t)r * 0xBB67AE85u;
+  }
   return k;
 }
 
