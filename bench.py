@@ -962,6 +962,15 @@ def main():
     e2e = None
     if args.e2e_steps > 0 and status == "ok":
         e2e = e2e_arm(api, torch, ctx_t, H, F, host, args.e2e_steps, 10_000)
+        if world > 1:  # whole job: all ranks' particle-steps over the slowest rank's time
+            wall_ms, ps = reduce_over_ranks(dist, e2e["ms_per_step"] * args.e2e_steps,
+                                            float(n * args.e2e_steps), "cuda")
+            e2e["value"] = ps / (wall_ms * 1e-3)
+            e2e["ms_per_step"] = wall_ms / args.e2e_steps
+            nb = torch.tensor([e2e["h2d_bytes_per_step"], e2e["d2h_bytes_per_step"]],
+                              dtype=torch.float64, device="cuda")
+            dist.all_reduce(nb, op=dist.ReduceOp.SUM)
+            e2e["h2d_bytes_per_step"], e2e["d2h_bytes_per_step"] = int(nb[0]), int(nb[1])
     del host
 
     extra = {}
