@@ -44,14 +44,14 @@ METRIC = "QED particle-steps/s at 64M particles (table vs MLP) and % HBM rooflin
 UNIT = "particle-steps/s"
 N_PART = 1 << 26
 DT = 0.01
-DEFAULT_STEPS, DEFAULT_WARMUP, DEFAULT_E2E_STEPS = 10, 3, 5
+DEFAULT_STEPS, DEFAULT_WARMUP, DEFAULT_E2E_STEPS = 10, 3, 10
 LEPTON_BYTES = 84       # R x,y,z,px,py,pz,w (28) + id (8) + E,B (24); W x,y,z,px,py,pz (24)
 LEPTON_STREAM_BYTES = 80  # streaming pass alone: R x..pz, id, E,B (56); W x..pz (24)
 PHOTON_APPEND_BYTES = 61  # x,y,z,px,py,pz,w (28) + id (8) + alive (1) + inherited E,B (24)
 # DRAM bytes of one k_lepton_onepass launch of the headline workload (2^26 electrons, table
-# sampler), dram__bytes_read.sum + dram__bytes_write.sum = 4.15 + 2.42 GB from one ncu capture
+# sampler), dram__bytes_read.sum + dram__bytes_write.sum = 4.17 + 2.42 GB from one ncu capture
 # of the full-size run (profiles/dram_lepton_onepass_64M.txt); reported only for that workload
-LEPTON_ONEPASS_TRAFFIC_64M = 6.57e9
+LEPTON_ONEPASS_TRAFFIC_64M = 6.59e9
 # photons a fresh electron of the headline ensemble emits per step: the mean of
 # W_rad Dt over the ensemble is 0.184 (an upper bound of the mean event count);
 # the photon buffer holds 1.6x that

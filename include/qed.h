@@ -399,9 +399,9 @@ enum { QED_TUNE_STREAM = 0, QED_TUNE_CHAINS = 1, QED_TUNE_ORDER = 2, QED_TUNE_PH
  *   QED_SCHED_EMIT_LANES     an emission round waits for this many lanes with
  *                            an event, 1..32 [16] (both paths)
  *   QED_SCHED_ROUND_LANES    a rate or scanning round of the single pass runs
- *                            with at least this many lanes, 1..32 [8]
+ *                            with at least this many lanes, 1..32 [12]
  *   QED_SCHED_SCAN_DRAWS     Method I sub-steps drawn per lane per scanning
- *                            round, 2..16, even [4] (both paths; the single
+ *                            round, 2..16, even [8] (both paths; the single
  *                            pass draws four at a time)
  *   QED_SCHED_SCAN_LEFT      a scanning round of the single pass ends when
  *                            fewer lanes are still drawing, 1..32 [8]

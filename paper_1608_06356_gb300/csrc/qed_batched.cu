@@ -216,7 +216,7 @@ extern "C" int qed_autotune_groups(qed_ctx *c, const qed_species *e, const qed_s
   // then the chain scheduling, one parameter at a time over fixed candidates
   // (the first of each list is its default)
   static const int cand[QED_SCHED_PARAMS][QED_SCHED_MAX_CANDIDATES] = {
-      {16, 8, 12, 20, 24, 0}, {8, 4, 12, 16, 0, 0}, {4, 2, 8, 12, 0, 0},
+      {16, 8, 12, 20, 24, 0}, {12, 4, 8, 16, 0, 0}, {8, 2, 4, 12, 0, 0},
       {8, 1, 4, 12, 16, 0},   {32, 16, 24, 33, 0, 0}};
   for (int k = 0; k < QED_SCHED_PARAMS && rc == QED_OK; ++k) {
     int best = cand[k][0];

@@ -113,7 +113,7 @@ inline int persistent_blocks_per_sm(const qed_ctx *c, int occupancy, int group) 
 }
 // Defaults of the chain-scheduling parameters (QED_SCHED_*), and a
 // parameter of the context or its default.
-constexpr int SCHED_DEF_EMIT_LANES = 16, SCHED_DEF_ROUND_LANES = 8, SCHED_DEF_SCAN_DRAWS = 4,
+constexpr int SCHED_DEF_EMIT_LANES = 16, SCHED_DEF_ROUND_LANES = 12, SCHED_DEF_SCAN_DRAWS = 8,
               SCHED_DEF_SCAN_LEFT = 8, SCHED_DEF_QUEUE_TRIGGER = 32;
 inline int sched_default(int k) {
   switch (k) {

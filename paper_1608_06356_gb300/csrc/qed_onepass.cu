@@ -27,14 +27,14 @@
 //     as are the lane counts below), the warp runs them with
 //     a per-warp scheduler of lane states -- idle; rate (chi and the exact
 //     rate, and N for a new particle; idle lanes are refilled from the queue
-//     at the start of such a round); scanning (Method I draws, two
-//     independent Philox chains interleaved, up to 8 per round, the round
-//     ending early when fewer than 8 lanes are still drawing); or pending (an
+//     at the start of such a round); scanning (Method I draws, four per
+//     iteration from two independent Philox calls, up to 8 per round, the
+//     round ending early when fewer than 8 lanes are still drawing); or pending (an
 //     event; the emitting lanes run together: xi, the recoil, the photon;
 //     then the rate again for the remaining sub-steps).  An
 //     emission round reserves slots for its photons with one atomic on the
 //     photon count and writes them there.  A round runs only when enough
-//     lanes are in its state (16 for an emission, 8 otherwise); when none can,
+//     lanes are in its state (16 for an emission, 12 otherwise); when none can,
 //     the warp goes back to streaming and the chains still running are parked
 //     in shared memory, to be resumed (with new entries) by the next heavy
 //     phase.  After the last slice the queue is drained.
