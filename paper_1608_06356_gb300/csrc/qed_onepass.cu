@@ -5,8 +5,8 @@
 // What is computed is the ordered path's: per lepton, field gather, Boris
 // push, chi_e (Eq. 2), W_rad (Eq. 1 above the xi_min cut), N = max(1,
 // ceil(W Dt / 0.2)) sub-steps of Method I with Philox draws keyed by (id,
-// step, sub-step), xi from the inverse CDF (Eq. 7) on an event, the recoil
-// and the photon.  Every particle, photon id and photon energy is the same as
+// step, sub-step / 2) -- one draw serves two sub-steps --, xi from the inverse
+// CDF (Eq. 7) on an event, the recoil and the photon.  Every particle, photon id and photon energy is the same as
 // on the ordered path; only the order of the appended photons differs (it
 // depends on the scheduling of the warps), so the photon buffer is the same
 // set in another order.
@@ -38,6 +38,9 @@
 //     the warp goes back to streaming and the chains still running are parked
 //     in shared memory, to be resumed (with new entries) by the next heavy
 //     phase.  After the last slice the queue is drained.
+//   learned sampler: an event of a one-sub-step lepton inside the network's
+//     domain ends its chain with a 16-byte record instead of an emission; the
+//     dense pass k_net_emit (below) finishes those emissions, 32 per warp.
 // No particle waits on another and nothing is staged in global memory: a
 // particle is read once and its slot written once or twice (the pushed state,
 // then the recoiled momentum of one that emitted, shortly after, while the
