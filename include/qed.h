@@ -253,9 +253,12 @@ int qed_step_fused(qed_ctx *ctx, const qed_species *e, const qed_species *p,
  *           call are copied to the same indices and its count set.
  * The context keeps three device staging buffers of `chunk` leptons
  * (allocated at the first call, grown by a later call that needs more).
- * Synchronous: returns when the leptons and photons are on the host.
- * chunk must be in (0, max_particles] (QED_ERR_CAPACITY otherwise); the call
- * is refused inside a stream capture (QED_ERR_UNSUPPORTED). */
+ * Synchronous: returns when the leptons and photons are on the host.  The
+ * context's counters accumulate over the chunks as over one step.  Calls on
+ * one context share its staging buffers and must not overlap (other threads
+ * included).  chunk must be in (0, max_particles] (QED_ERR_CAPACITY
+ * otherwise); the call is refused inside a stream capture
+ * (QED_ERR_UNSUPPORTED). */
 int qed_lepton_step_host(qed_ctx *ctx, const qed_species *l_host, const qed_species *g,
                          const qed_species *g_host, const qed_fields *f, int64_t step,
                          int64_t chunk, qed_stream_t stream);
