@@ -347,7 +347,7 @@ def e2e_arm(api, torch, ctx, H, F, host, steps, step0):
         if k >= warm:
             times.append(dt)
             m = int(gh.n[0])
-            d2h += 24 * n + 61 * m + 8 * E2E_CHUNKS  # x..pz back, the photons, the chunk counts
+            d2h += 24 * n + 61 * m + 8  # x..pz back, the photons, the photon count
     wall = sum(times)
     return {"value": n * steps / wall, "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h // steps, "steps": steps,

@@ -250,7 +250,12 @@ int qed_step_fused(qed_ctx *ctx, const qed_species *e, const qed_species *p,
  *           stepped).
  *   g_host  NULL, or a host mirror of g (host pointers for every array g has,
  *           capacity >= g's, d_n a HOST int64): the photons appended by this
- *           call are copied to the same indices and its count set.
+ *           call are copied to the same indices and its count set.  When the
+ *           device can map every mirror array (page-locked memory from the
+ *           CUDA runtime), a kernel on the output stream copies each chunk's
+ *           photons through the mapped pointers and the host waits only at
+ *           the end; otherwise the host reads each chunk's photon count and
+ *           queues the copies while the next chunk runs.
  * The context keeps three device staging buffers of `chunk` leptons
  * (allocated at the first call, grown by a later call that needs more).
  * Synchronous: returns when the leptons and photons are on the host.  The

@@ -7,9 +7,12 @@
 // previous chunk has been copied out), stepped on the caller's stream -- the
 // same launches as qed_step_fused's lepton stage, appending photons to the
 // device photon species -- and its positions and momenta copied back on the
-// output stream.  The photons a chunk appended are copied to the host mirror
-// of the photon species once its count is known on the host, which happens
-// while the next chunk is already queued.  Particle ids key the random
+// output stream.  The photons a chunk appended go to the host mirror of the
+// photon species on the output stream too: by a copy kernel that reads the
+// chunk's range on the device and writes through host-mapped pointers, so
+// that every chunk is queued at once and the host waits only at the end (or,
+// for mirror memory the device cannot map, by copies whose ranges the host
+// reads after each chunk).  Particle ids key the random
 // streams, so chunking changes no result, only the order of the photons
 // (chunks in order; within a chunk as the lepton step appends them).
 #include <cstdio>
@@ -33,6 +36,51 @@ int cuda_fail(cudaError_t e, const char *what) {
 }
 
 __global__ void k_set_count(int64_t *d_n, int64_t v) { *d_n = v; }
+__global__ void k_mark_count(int64_t *dst, const int64_t *src) { *dst = *src; }
+
+// Copy of the photons appended by one chunk, [*lo, *hi) clamped to the
+// capacity, from the device photon species to its host mirror through
+// host-mapped pointers: the range is read on the device, so no host round
+// trip is needed between the chunks.
+constexpr int MAX_PARRAYS = 16;
+struct PhotonCopy {
+  const char *src[MAX_PARRAYS];
+  char *dst[MAX_PARRAYS];
+  int esz[MAX_PARRAYS];
+  int wide[MAX_PARRAYS];  // 16: both bases 16-byte aligned; 4: 4-byte aligned; else bytes
+  int np;
+  const int64_t *lo, *hi;
+  int64_t cap;
+};
+
+__global__ void __launch_bounds__(256) k_copy_photons(PhotonCopy A) {
+  int64_t lo = *A.lo, hi = *A.hi;
+  lo = lo < A.cap ? lo : A.cap;
+  hi = hi < A.cap ? hi : A.cap;
+  if (hi <= lo) return;
+  const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+  for (int a = 0; a < A.np; ++a) {
+    const int64_t b0 = lo * A.esz[a], b1 = hi * A.esz[a];
+    if (A.esz[a] % 4 || A.wide[a] < 4) {  // bytes (alive flags, or unaligned bases)
+      for (int64_t q = b0 + t0; q < b1; q += nt) A.dst[a][q] = A.src[a][q];
+      continue;
+    }
+    // 4-byte words up to a 16-byte boundary, 16-byte words, 4-byte words after
+    const int64_t m0 = (b0 + 15) & ~(int64_t)15, m1 = b1 & ~(int64_t)15;
+    if (m0 >= m1 || A.wide[a] < 16) {
+      for (int64_t q = b0 / 4 + t0; q < b1 / 4; q += nt)
+        reinterpret_cast<uint32_t *>(A.dst[a])[q] = reinterpret_cast<const uint32_t *>(A.src[a])[q];
+      continue;
+    }
+    for (int64_t q = b0 / 4 + t0; q < m0 / 4; q += nt)
+      reinterpret_cast<uint32_t *>(A.dst[a])[q] = reinterpret_cast<const uint32_t *>(A.src[a])[q];
+    for (int64_t q = m0 / 16 + t0; q < m1 / 16; q += nt)
+      reinterpret_cast<uint4 *>(A.dst[a])[q] = reinterpret_cast<const uint4 *>(A.src[a])[q];
+    for (int64_t q = m1 / 4 + t0; q < b1 / 4; q += nt)
+      reinterpret_cast<uint32_t *>(A.dst[a])[q] = reinterpret_cast<const uint32_t *>(A.src[a])[q];
+  }
+}
 
 // One array of the lepton species as the host step moves it: host pointer,
 // bytes per element, device staging offset, and whether it is copied back.
@@ -126,7 +174,7 @@ int ensure_host_step(qed_ctx *c, size_t per_buf) {
     for (int i = 0; i < 3 * NBUF; ++i)
       if (cudaEventCreateWithFlags(&c->hs_ev[i], cudaEventDisableTiming) != cudaSuccess)
         return QED_ERR_CUDA;
-    if (cudaMalloc(&c->hs_dn, NBUF * sizeof(int64_t)) != cudaSuccess) return QED_ERR_NOMEM;
+    if (cudaMalloc(&c->hs_dn, (2 * NBUF + 1) * sizeof(int64_t)) != cudaSuccess) return QED_ERR_NOMEM;
     if (cudaHostAlloc(reinterpret_cast<void **>(&c->hs_cnt), 2 * NBUF * sizeof(int64_t),
                       cudaHostAllocDefault) != cudaSuccess)
       return QED_ERR_NOMEM;
@@ -174,12 +222,43 @@ int lepton_step_host(qed_ctx *c, const qed_species *lh, const qed_species *g,
     return QED_ERR_UNSUPPORTED;
   int rc = ensure_host_step(c, per_buf);
   if (rc != QED_OK) return rc;
+  // The photons go to the host mirror by a copy kernel writing through
+  // host-mapped pointers when every mirror array is mapped (page-locked
+  // memory allocated by the CUDA runtime is); otherwise by copies whose
+  // ranges the host reads after each chunk.
+  PhotonCopy pc{};
+  bool mapped = gh != nullptr && np > 0;
+  for (int a = 0; a < np && mapped; ++a) {
+    void *dp = nullptr;
+    if (cudaHostGetDevicePointer(&dp, phost[a], 0) != cudaSuccess) {
+      mapped = false;
+      cudaGetLastError();  // clear the error of the query
+      break;
+    }
+    pc.src[a] = static_cast<const char *>(pdev[a]);
+    pc.dst[a] = static_cast<char *>(dp);
+    pc.esz[a] = (int)pesz[a];
+    const uintptr_t al = reinterpret_cast<uintptr_t>(pdev[a]) | reinterpret_cast<uintptr_t>(dp);
+    pc.wide[a] = al % 16 == 0 ? 16 : al % 4 == 0 ? 4 : 1;
+  }
+  pc.np = np;
+  pc.cap = g->capacity;
+  constexpr int R = NBUF + 1;  // device ring of photon counts after each chunk
+  int64_t *ring = c->hs_dn + NBUF;
   cudaEvent_t *in_done = c->hs_ev, *comp_done = c->hs_ev + NBUF, *out_done = c->hs_ev + 2 * NBUF;
   int64_t *cnt = c->hs_cnt;  // [0, NBUF): photon count after chunk k (slot k % NBUF); [NBUF]: at start
-  cudaError_t e = cudaMemcpyAsync(cnt + NBUF, g->d_n, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaError_t e = cudaSuccess;
+  int64_t m_done = 0;  // (host-read ranges) photons already on the host mirror
+  if (mapped) {
+    k_mark_count<<<1, 1, 0, st>>>(ring, g->d_n);
+    c->launches += 1;
+    e = cudaGetLastError();
+  } else {
+    e = cudaMemcpyAsync(cnt + NBUF, g->d_n, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    m_done = cnt[NBUF];
+  }
   if (e != cudaSuccess) return cuda_fail(e, "qed_lepton_step_host");
-  int64_t m_done = cnt[NBUF];  // photons already copied to the host mirror (or present at start)
   const int64_t gcap = g->capacity;
   auto copy_photons = [&](int64_t upto) -> cudaError_t {
     upto = upto < gcap ? upto : gcap;
@@ -211,39 +290,58 @@ int lepton_step_host(qed_ctx *c, const qed_species *lh, const qed_species *g,
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaEventRecord(in_done[b], c->hs_in);
-    // step on the caller's stream
+    // step on the caller's stream, then the photon count after it
     if (e == cudaSuccess) e = cudaStreamWaitEvent(st, in_done[b], 0);
     if (e == cudaSuccess)
       e = f64 ? launch_lepton<double>(c, &sb, nullptr, g, f, step, MODE_FUSED_, st)
               : launch_lepton<float>(c, &sb, nullptr, g, f, step, MODE_FUSED_, st);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(cnt + b, g->d_n, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) {
+      if (mapped) {
+        k_mark_count<<<1, 1, 0, st>>>(ring + (k + 1) % R, g->d_n);
+        c->launches += 1;
+        e = cudaGetLastError();
+      } else {
+        e = cudaMemcpyAsync(cnt + b, g->d_n, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+      }
+    }
     if (e == cudaSuccess) e = cudaEventRecord(comp_done[b], st);
-    // out: the updated positions and momenta (and event-generator state)
+    // out: the updated positions and momenta (and event-generator state), and
+    // with mapped mirrors the chunk's photons
     if (e == cudaSuccess) e = cudaStreamWaitEvent(c->hs_out, comp_done[b], 0);
     for (int a = 0; a < nl && e == cudaSuccess; ++a)
       if (L[a].back)
         e = cudaMemcpyAsync(L[a].host + (size_t)off * L[a].esz, base + L[a].off, (size_t)nk * L[a].esz,
                             cudaMemcpyDeviceToHost, c->hs_out);
+    if (e == cudaSuccess && mapped) {
+      // ring slot k % R is rewritten only by chunk k + NBUF, whose input copy
+      // waits for this buffer's out_done (recorded after this copy)
+      pc.lo = ring + k % R;
+      pc.hi = ring + (k + 1) % R;
+      k_copy_photons<<<2 * c->num_sms, 256, 0, c->hs_out>>>(pc);
+      c->launches += 1;
+      e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = cudaEventRecord(out_done[b], c->hs_out);
-    // the previous chunk's photons, now that the next chunks are queued
-    if (e == cudaSuccess && k >= 1) {
+    // (host-read ranges) the previous chunk's photons, now that the next
+    // chunks are queued
+    if (e == cudaSuccess && !mapped && k >= 1) {
       const int pb = (int)((k - 1) % NBUF);
       e = cudaEventSynchronize(comp_done[pb]);
       if (e == cudaSuccess) e = copy_photons(cnt[pb]);
     }
   }
-  if (e == cudaSuccess && K >= 1) {
+  if (e == cudaSuccess && !mapped && K >= 1) {
     const int lb = (int)((K - 1) % NBUF);
     e = cudaEventSynchronize(comp_done[lb]);
     if (e == cudaSuccess) e = copy_photons(cnt[lb]);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->hs_out);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->hs_in);
+  if (e == cudaSuccess && gh && gh->d_n)
+    e = cudaMemcpyAsync(cnt + NBUF, g->d_n, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "qed_lepton_step_host");
-  if (gh && gh->d_n) *gh->d_n = K >= 1 ? (cnt[(K - 1) % NBUF] < gcap ? cnt[(K - 1) % NBUF] : gcap)
-                                       : (cnt[NBUF] < gcap ? cnt[NBUF] : gcap);
+  if (gh && gh->d_n) *gh->d_n = cnt[NBUF] < gcap ? cnt[NBUF] : gcap;
   return QED_OK;
 }
 
