@@ -6,8 +6,10 @@ device (no photons at the start, so its photon stage does nothing): every
 lepton equal bit for bit, the same photons (as a set: chunks append in chunk
 order), the same counters; and the host mirror of the photon species equal to
 the device species it mirrors.  Ragged chunks, a chunk larger than the
-ensemble, both append orders, FP64 and the Method II event generator (its
-per-particle state copied in and out) are covered."""
+ensemble, both append orders, FP64, the Method II event generator (its
+per-particle state copied in and out) and a mirror in pageable memory (which
+the device may not map: then the host reads each chunk's photon count) are
+covered."""
 import numpy as np
 import pytest
 import torch
@@ -38,9 +40,10 @@ def _by_id(h):
     return {k: v[o] for k, v in h.items()}
 
 
-@pytest.mark.parametrize("order,precision,generator,chunk", [
-    (1, 0, 0, 7_001), (1, 0, 0, 1 << 20), (0, 0, 0, 977), (0, 1, 0, 12_345), (0, 0, 1, 9_000)])
-def test_host_step_equals_device_step(api, order, precision, generator, chunk):
+@pytest.mark.parametrize("order,precision,generator,chunk,mirror_pinned", [
+    (1, 0, 0, 7_001, True), (1, 0, 0, 1 << 20, True), (0, 0, 0, 977, True), (0, 1, 0, 12_345, True),
+    (0, 0, 1, 9_000, True), (1, 0, 0, 6_000, False)])
+def test_host_step_equals_device_step(api, order, precision, generator, chunk, mirror_pinned):
     n = 50_001
     f64 = precision == 1
     dt = torch.float64 if f64 else torch.float32
@@ -60,7 +63,8 @@ def test_host_step_equals_device_step(api, order, precision, generator, chunk):
     ctx_h = api.qed_init_tables(api.config(**cfg))
     eh = api.Species.empty(n, -1, dtype=dt, fields=True, od=od, pinned=True).load(**st)
     g2 = api.Species.empty(cap_g, 0, dtype=dt, fields=True)
-    gh = api.Species.empty(cap_g, 0, dtype=dt, fields=True, pinned=True)
+    gh = (api.Species.empty(cap_g, 0, dtype=dt, fields=True, pinned=True) if mirror_pinned
+          else api.Species.empty(cap_g, 0, dtype=dt, fields=True, device="cpu"))
     api.qed_lepton_step_host(ctx_h, eh, g2, gh, F, 4, chunk)
     c = api.qed_read_counters(ctx_h)
     assert eh.n.is_pinned() and int(eh.n[0]) == n
