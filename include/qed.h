@@ -484,6 +484,63 @@ int qed_profile_end_phases(qed_ctx *ctx, double *ms, int64_t *steps);
 int qed_compact_noalloc(const qed_species *s, int precision, uint32_t *d_status,
                         qed_stream_t stream);
 
+/* ---- self-consistent fields: the particle-in-cell loop around the step ----
+ * The paper adds its QED module to a PIC code (introduction) whose field
+ * solver and current deposition it does not describe.  These calls close the
+ * PIC cycle around the step with the standard explicit scheme: Maxwell's
+ * equations on Yee's
+ * staggered grid (K. S. Yee, IEEE Trans. Antennas Propag. 14, 302 (1966)),
+ * leapfrogged in the units above,
+ *     dB/dt = -curl E,      dE/dt = curl B - J,
+ * J in units of e n_c c (n_c = eps0 m omega0^2 / e^2), with the current
+ * deposited by the linear (CIC) shape at each component's staggered position.
+ * The grid is periodic, nx*ny*nz cells, node (i,j,k) at (x0 + i dx, y0 + j dy,
+ * z0 + k dz); every array below is float [nz][ny][nx] (x fastest) holding:
+ *   ex, jx at (i+1/2, j, k)       bx at (i, j+1/2, k+1/2)
+ *   ey, jy at (i, j+1/2, k)       by at (i+1/2, j, k+1/2)
+ *   ez, jz at (i, j, k+1/2)       bz at (i+1/2, j+1/2, k)
+ * nodes: the node grid of qed_fields.GRID (float [nz][ny][nx][8]) that the
+ * particle steps gather from: E and B at the nodes, each the mean of the
+ * component's two (E) or four (B) nearest staggered values.
+ * All pointers are caller-owned device memory, 16-byte aligned.            */
+typedef struct {
+  int nx, ny, nz, pad_;
+  double dx, dy, dz, x0, y0, z0;
+  float *ex, *ey, *ez, *bx, *by, *bz;
+  float *jx, *jy, *jz;
+  float *nodes;
+} qed_yee;
+
+/* Add the current of the first min(*d_count, count of s) particles of s
+ * (d_count: device int64, or NULL for all) to jx, jy, jz: each particle is a
+ * charge s->q * w * weight_unit moving with v = p/gamma, taken at
+ * x - v dt/2 (the middle of the step when x has just been advanced by v dt),
+ * spread with the CIC weights of the staggered J positions and divided by
+ * the cell volume dx dy dz.  weight_unit: real particles per unit of w,
+ * divided by n_c (c/omega0)^3.  Element type of s as for the step
+ * (qed_config.precision); the additions are float atomics, so their order --
+ * and the last bits of J -- vary from run to run.  QED_ERR_ARG for photons
+ * (q = 0) or a bad grid. */
+int qed_pic_deposit(qed_ctx *ctx, const qed_species *s, const qed_yee *y, double weight_unit,
+                    const int64_t *d_count, qed_stream_t stream);
+
+/* advance != 0: one leapfrog step of the fields over the context's dt,
+ *     B <- B - (dt/2) curl E;   E <- E + dt (curl B - J);   B <- B - (dt/2) curl E,
+ * taking E, B from time n to n+1 with J at n+1/2; J is zeroed for the next
+ * deposit.  Then (advance = 0: only) the nodes are written from E and B.
+ * QED_ERR_ARG if dt breaks the Courant limit dt < 1/sqrt(1/dx^2 + 1/dy^2 +
+ * 1/dz^2) or a grid argument is bad. */
+int qed_pic_fields(qed_ctx *ctx, const qed_yee *y, int advance, qed_stream_t stream);
+
+/* One cycle of the loop: qed_step_fused(e, p, g) gathering from y->nodes
+ * (field mode GRID), then the current of the leptons that existed when the
+ * call began (leptons created by this step's pairs are deposited from the
+ * next step on), then qed_pic_fields(advance = 1).  The nodes must hold the
+ * fields of the current time (qed_pic_fields with advance = 0 once at the
+ * start). */
+int qed_pic_step(qed_ctx *ctx, const qed_species *e, const qed_species *p, const qed_species *g,
+                 const qed_yee *y, double weight_unit, int64_t step, qed_stream_t stream);
+
 /* Number of kernel launches this context has issued (for accounting). */
 int64_t qed_launch_count(const qed_ctx *ctx);
 
