@@ -821,6 +821,85 @@ def config_3d_cascade(api, torch, steps=28, seed_n=1 << 24, cap=1 << 28, nx=256,
             "field_fill_bytes_per_step": 32 * nodes, "cpu_baseline": base}
 
 
+def pic_loop_bench(api, torch, nx=128, ppc=8, steps=20, dx=0.25, dt=0.1, cpu_nx=24, cpu_ppc=4):
+    """The self-consistent loop (qed_pic_step): a warm electron plasma at
+    0.05 n_c, thermal momenta 0.1 m c per axis, `ppc` electrons per cell at
+    random positions on a periodic nx^3 Yee grid (dx = 0.25, Dt = 0.1).  Each
+    cycle is the QED step gathering from the node grid, the current deposit
+    and the field leapfrog with the node grid.  The cycles are timed whole,
+    then once more with events between the phases.  Field bytes: 188 B per
+    cell per cycle (B half-step 36, E step 60 with J zeroed, B half-step 36,
+    nodes 56); the deposit reads 28 B and adds 24 float atomics per particle
+    into J arrays that stay in L2."""
+    from paper_1608_06356_gb300 import workloads as W
+    st = W.plasma(nx, nx, nx, dx, ppc=ppc, density=0.05, p_th=0.1, seed=4)
+    st = {k: (v.astype(np.float32) if v.dtype.kind == "f" else v) for k, v in st.items()}
+    n = len(st["x"])
+    ctx = api.qed_init_tables(api.config(dt=dt, seed=2, max_particles=n))
+    e = api.Species.empty(n, -1).load(**st)
+    p = api.Species.empty(0, 1)
+    g = api.Species.empty(1 << 16, 0)
+    y = api.Yee(nx, nx, nx, dx, dx, dx)
+    api.qed_pic_fields(ctx, y, advance=False)
+    for s in range(3):  # warm-up cycles
+        api.qed_pic_step(ctx, e, p, g, y, 1.0, s)
+    api.qed_reset_counters(ctx)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for s in range(3, 3 + steps):
+        api.qed_pic_step(ctx, e, p, g, y, 1.0, s)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    # the same cycle by its parts, with events between them
+    F = y.fields()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    for s in range(steps):
+        k = 3 + steps + s
+        ev[s][0].record()
+        api.qed_step_fused(ctx, e, p, g, F, k)
+        ev[s][1].record()
+        api.qed_pic_deposit(ctx, e, y, 1.0)
+        ev[s][2].record()
+        api.qed_pic_fields(ctx, y, advance=True)
+        ev[s][3].record()
+    torch.cuda.synchronize()
+    ph = [sum(ev[s][i].elapsed_time(ev[s][i + 1]) for s in range(steps)) / steps for i in range(3)]
+    c = api.qed_read_counters(ctx)
+    peak, kind = peaks()
+    cells = nx ** 3
+    field_bytes = 188 * cells
+    base = {}
+    try:
+        import oracle as O
+        from oracle import pic as P
+        O.build()
+        sub = W.plasma(cpu_nx, cpu_nx, cpu_nx, dx, ppc=cpu_ppc, density=0.05, p_th=0.1, seed=4)
+        sub = {k: (v.astype(np.float32).astype(np.float64) if v.dtype.kind == "f" else v) for k, v in sub.items()}
+        cfg = O.make_config(dt=dt, seed=2)
+        oe = O.Species(len(sub["x"]), -1.0).load(**sub)
+        og = O.Species(16, 0.0, with_alive=True)
+        grid = P.Grid(cpu_nx, cpu_nx, cpu_nx, dx, dx, dx)
+        t0 = time.perf_counter()
+        for s in range(2):
+            P.loop_step(cfg, grid, oe, None, og, s)
+        sec = time.perf_counter() - t0
+        base = {"value": 2 * oe.n / sec, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                "sample": f"{cpu_nx}^3 cells x {cpu_ppc} electrons per cell x 2 cycles "
+                          "(oracle step + numpy deposit and Yee step)", "seconds": sec}
+    except Exception as ex:
+        base = {"error": repr(ex)}
+    return {"grid": [nx, nx, nx], "electrons": n, "electrons_per_cell": ppc, "steps_timed": steps,
+            "dt": dt, "dx": dx, "status": run_status(c),
+            "particle_steps_per_s": n / (ms * 1e-3), "ms_per_cycle": ms,
+            "ms_per_phase": {"qed_step": ph[0], "deposit": ph[1], "fields": ph[2]},
+            "fields_roofline": _block_roofline(field_bytes, ph[2], peak, kind),
+            "deposit_atomics_per_s": 24 * n / (ph[1] * 1e-3),
+            "deposit_read_gbs": 28 * n / (ph[1] * 1e-3) / 1e9,
+            "photons": g.count(), "cpu_baseline": base}
+
+
 def oracle_sample_rate(sample_n, steps, seed=0):
     """The FP64 oracle as it stands on `sample_n` electrons of the headline
     ensemble, `steps` steps, each from the same initial state (as the
@@ -990,6 +1069,7 @@ def main():
             extra["config_single_particle_fp64"] = config_single_particle(api, torch)
             extra["config_uniform_field_ensemble"] = config_uniform_ensemble(api, torch)
             extra["config_3d_cascade"] = config_3d_cascade(api, torch)
+            extra["pic_loop"] = pic_loop_bench(api, torch)
         if args.generator_bench:
             extra["event_generators_fig2"] = generator_rates(api, torch)
         if args.cascade_bench:

@@ -537,7 +537,8 @@ int qed_pic_fields(qed_ctx *ctx, const qed_yee *y, int advance, qed_stream_t str
  * call began (leptons created by this step's pairs are deposited from the
  * next step on), then qed_pic_fields(advance = 1).  The nodes must hold the
  * fields of the current time (qed_pic_fields with advance = 0 once at the
- * start). */
+ * start).  e, p and g as for qed_step_fused (e and p leptons, either may have
+ * capacity 0). */
 int qed_pic_step(qed_ctx *ctx, const qed_species *e, const qed_species *p, const qed_species *g,
                  const qed_yee *y, double weight_unit, int64_t step, qed_stream_t stream);
 

@@ -74,6 +74,13 @@ class qed_counters(C.Structure):
                 "status": self.status, "hist": list(self.hist), "deferred": self.deferred}
 
 
+class qed_yee(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("pad_", C.c_int),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double)] + \
+               [(n, C.c_void_p) for n in ("ex", "ey", "ez", "bx", "by", "bz", "jx", "jy", "jz", "nodes")]
+
+
 QED_TUNE_GROUPS, QED_TUNE_MAX_FACTOR = 5, 8
 TUNE_GROUP_NAMES = ("stream", "chains", "order", "photon", "compact")
 QED_SCHED_PARAMS, QED_SCHED_MAX_CANDIDATES = 5, 6
@@ -132,6 +139,10 @@ SIGNATURES = {
     "qed_lepton_step_host": (C.c_int, [_P, C.POINTER(qed_species), C.POINTER(qed_species),
                                        C.POINTER(qed_species), C.POINTER(qed_fields), C.c_int64,
                                        C.c_int64, _P]),
+    "qed_pic_deposit": (C.c_int, [_P, C.POINTER(qed_species), C.POINTER(qed_yee), C.c_double, _P, _P]),
+    "qed_pic_fields": (C.c_int, [_P, C.POINTER(qed_yee), C.c_int, _P]),
+    "qed_pic_step": (C.c_int, [_P, C.POINTER(qed_species), C.POINTER(qed_species), C.POINTER(qed_species),
+                               C.POINTER(qed_yee), C.c_double, C.c_int64, _P]),
     "qed_mlp_load": (C.c_int, [_P, _P, C.c_size_t]),
     "qed_mlp_get": (C.c_int, [_P, _P, C.c_size_t]),
     "qed_mlp_train": (C.c_int, [_P, C.c_int64, C.c_float, C.c_uint64, C.POINTER(C.c_double), _P]),

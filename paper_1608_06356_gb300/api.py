@@ -195,6 +195,54 @@ class Fields:
         return f
 
 
+YEE_ARRAYS = ("ex", "ey", "ez", "bx", "by", "bz", "jx", "jy", "jz")
+
+
+class Yee:
+    """Fields of the PIC loop on a periodic Yee grid (include/qed.h,
+    qed_yee): nine float arrays [nz, ny, nx] at their staggered positions
+    and the node grid [nz, ny, nx, 8] the particle gather reads."""
+
+    def __init__(self, nx, ny, nz, dx, dy, dz, x0=0.0, y0=0.0, z0=0.0, device="cuda"):
+        self.shape = (int(nz), int(ny), int(nx))
+        self.dx, self.dy, self.dz = float(dx), float(dy), float(dz)
+        self.x0, self.y0, self.z0 = float(x0), float(y0), float(z0)
+        for nm in YEE_ARRAYS:
+            setattr(self, nm, torch.zeros(self.shape, dtype=torch.float32, device=device))
+        self.nodes = torch.zeros(self.shape + (8,), dtype=torch.float32, device=device)
+
+    def struct(self) -> B.qed_yee:
+        y = B.qed_yee()
+        y.nz, y.ny, y.nx = self.shape
+        y.dx, y.dy, y.dz, y.x0, y.y0, y.z0 = self.dx, self.dy, self.dz, self.x0, self.y0, self.z0
+        for nm in YEE_ARRAYS + ("nodes",):
+            setattr(y, nm, getattr(self, nm).data_ptr())
+        return y
+
+    def fields(self) -> B.qed_fields:
+        """The node grid as qed_fields (mode GRID)."""
+        return Fields.grid(self.nodes, self.dx, self.dy, self.dz, self.x0, self.y0, self.z0)
+
+
+def qed_pic_deposit(ctx: Context, s: Species, y: Yee, weight_unit: float = 1.0,
+                    d_count: torch.Tensor | None = None, stream=None) -> None:
+    B.check(B.lib().qed_pic_deposit(ctx.handle, C.byref(s.struct()), C.byref(y.struct()),
+                                    float(weight_unit), d_count.data_ptr() if d_count is not None else None,
+                                    _stream(stream)), "qed_pic_deposit")
+
+
+def qed_pic_fields(ctx: Context, y: Yee, advance: bool = True, stream=None) -> None:
+    B.check(B.lib().qed_pic_fields(ctx.handle, C.byref(y.struct()), int(bool(advance)), _stream(stream)),
+            "qed_pic_fields")
+
+
+def qed_pic_step(ctx: Context, e: Species | None, p: Species | None, g: Species, y: Yee,
+                 weight_unit: float, step: int, stream=None) -> None:
+    B.check(B.lib().qed_pic_step(ctx.handle, C.byref(_sp(e)), C.byref(_sp(p)), C.byref(g.struct()),
+                                 C.byref(y.struct()), float(weight_unit), int(step), _stream(stream)),
+            "qed_pic_step")
+
+
 def _sp(s: Species | None) -> B.qed_species:
     if s is None:  # an empty species with a zero count
         z = torch.zeros(1, dtype=torch.int64, device="cuda")

@@ -82,7 +82,7 @@ static void free_ctx(qed_ctx *c) {
   if (!c) return;
   free_host_step(c);
   void *ptrs[] = {c->R64, c->F64, c->Y64, c->P64, c->Yp64, c->R32, c->F32, c->Y32,
-                  c->P32, c->Yp32, c->tile_state, c->sync, c->snap, c->d_counters,
+                  c->P32, c->Yp32, c->tile_state, c->sync, c->snap, c->pic_n, c->d_counters,
                   c->heavy_flags, c->heavy_list, c->heavy_n, c->cls_chunk_cnt,
                   c->cls_chunk_off, c->cls_off, c->sub_cnt, c->sub_gf, c->rec_e,
                   c->rec_k, c->sub_meta, c->fill_meta, c->replay_n, c->stage, c->stage_tag,
@@ -268,6 +268,7 @@ extern "C" int qed_init_tables(const qed_config *cfg, qed_ctx **out, qed_stream_
   if (cudaMalloc(&c->tile_state, sizeof(unsigned long long) * c->max_tiles) != cudaSuccess ||
       cudaMalloc(&c->sync, sizeof(unsigned int) * 4) != cudaSuccess ||
       cudaMalloc(&c->snap, sizeof(int64_t) * 4) != cudaSuccess ||
+      cudaMalloc(&c->pic_n, sizeof(int64_t) * 2) != cudaSuccess ||
       cudaMalloc(&c->d_counters, sizeof(qed_counters)) != cudaSuccess ||
       cudaMalloc(&c->heavy_flags, (size_t)c->heavy_slots + 4096) != cudaSuccess ||
       cudaMalloc(&c->heavy_list, sizeof(int) * (size_t)c->heavy_slots) != cudaSuccess ||

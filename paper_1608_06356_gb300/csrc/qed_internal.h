@@ -22,6 +22,7 @@ struct qed_ctx {
   unsigned int *sync;  // [0] tile counter, [1] done counter, [2] epoch
   int64_t max_tiles;
   int64_t *snap;       // [4] counts snapshotted at the start of a fused step
+  int64_t *pic_n;      // [2] lepton counts at the start of a qed_pic_step
   int64_t heavy_slots;   // block-tile slots of both lepton species
   uint8_t *heavy_flags;  // [heavy_slots] streaming-pass class flags
   int *heavy_list;       // [heavy_slots] ordered deferred slots

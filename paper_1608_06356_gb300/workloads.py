@@ -94,3 +94,24 @@ def batched_runs(n_runs=256, seed=0, lo=1e3, hi=1e6, chi_lo=0.01, chi_hi=10.0):
 def uniform_words(n, seed=0):
     """Uniform 32-bit words (inputs to the inverse-CDF parity checks)."""
     return np.random.default_rng(seed).integers(0, 2**32, size=n, dtype=np.uint64).astype(np.uint32)
+
+
+def plasma(nx, ny, nz, dx, ppc=1, density=0.01, p_th=0.0, drift=(0.0, 0.0, 0.0), seed=0,
+           lattice=False, id0=0):
+    """Electrons filling a periodic box of nx*ny*nz cubic cells of side dx at
+    `density` (units of the critical density) with weights density dx^3 / ppc:
+    ppc per cell, at uniform random positions (lattice=True: one at each cell
+    centre), momenta normal with deviation p_th per axis plus `drift`."""
+    rng = np.random.default_rng(seed)
+    cells = nx * ny * nz
+    if lattice:
+        assert ppc == 1
+        k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        pos = [((a + 0.5) * dx).ravel() for a in (i, j, k)]
+    else:
+        box = (nx * dx, ny * dx, nz * dx)
+        pos = [rng.uniform(0.0, L, cells * ppc) for L in box]
+    n = cells * ppc
+    p = rng.normal(0.0, 1.0, (3, n)) * p_th + np.asarray(drift, dtype=np.float64)[:, None]
+    return dict(x=pos[0], y=pos[1], z=pos[2], px=p[0], py=p[1], pz=p[2],
+                w=np.full(n, density * dx ** 3 / ppc), id=np.arange(id0, id0 + n, dtype=np.uint64))

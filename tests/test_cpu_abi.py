@@ -54,6 +54,8 @@ def test_struct_layouts_match_c(qlib, tmp_path):
                  offsetof(qed_fields, grid), offsetof(qed_counters, hist));
           printf("%zu %zu %zu %zu\\n", sizeof(qed_tuning), offsetof(qed_tuning, sched),
                  offsetof(qed_tuning, ms_per_step), offsetof(qed_tuning, sched_ms));
+          printf("%zu %zu %zu %zu\\n", sizeof(qed_yee), offsetof(qed_yee, dx),
+                 offsetof(qed_yee, ex), offsetof(qed_yee, nodes));
           return 0;
         }"""))
     exe = tmp_path / "sz"
@@ -64,8 +66,10 @@ def test_struct_layouts_match_c(qlib, tmp_path):
                                          C.sizeof(B.qed_fields), C.sizeof(B.qed_counters)]
     assert [int(v) for v in out[4:8]] == [B.qed_config.seed.offset, B.qed_species.d_n.offset,
                                           B.qed_fields.grid.offset, B.qed_counters.hist.offset]
-    assert [int(v) for v in out[8:]] == [C.sizeof(B.qed_tuning), B.qed_tuning.sched.offset,
-                                         B.qed_tuning.ms_per_step.offset, B.qed_tuning.sched_ms.offset]
+    assert [int(v) for v in out[8:12]] == [C.sizeof(B.qed_tuning), B.qed_tuning.sched.offset,
+                                           B.qed_tuning.ms_per_step.offset, B.qed_tuning.sched_ms.offset]
+    assert [int(v) for v in out[12:]] == [C.sizeof(B.qed_yee), B.qed_yee.dx.offset, B.qed_yee.ex.offset,
+                                          B.qed_yee.nodes.offset]
 
 
 def test_config_defaults_and_strerror(qlib):
@@ -118,6 +122,9 @@ def test_entry_points_reject_a_null_context(qlib):
     assert lib.qed_compact(None, None, None) == -1
     assert lib.qed_profile_end_phases(None, None, None) == -1
     assert lib.qed_test_wait_expiry(None, None) == -1
+    assert lib.qed_pic_fields(None, None, 0, None) == -1
+    assert lib.qed_pic_deposit(None, None, None, 1.0, None, None) == -1
+    assert lib.qed_pic_step(None, None, None, None, None, 1.0, 0, None) == -1
 
 
 def test_missing_library_fails_loudly(qlib, monkeypatch, tmp_path):
