@@ -352,6 +352,7 @@ def e2e_arm(api, torch, ctx, H, F, host, steps, step0):
     return {"value": n * steps / wall, "unit": UNIT,
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h // steps, "steps": steps,
             "ms_per_step": 1e3 * wall / steps, "ms_each_step": [round(1e3 * t, 2) for t in times],
+            "ms_median_step": 1e3 * float(np.median(times)) if times else None,
             "chunks": E2E_CHUNKS,
             "note": "ensemble in pinned host memory; every step streams the 64M electrons "
                     "(60 B each) through qed_lepton_step_host in chunks, copies their positions "
@@ -821,18 +822,23 @@ def config_3d_cascade(api, torch, steps=28, seed_n=1 << 24, cap=1 << 28, nx=256,
             "field_fill_bytes_per_step": 32 * nodes, "cpu_baseline": base}
 
 
-def pic_loop_bench(api, torch, nx=128, ppc=8, steps=20, dx=0.25, dt=0.1, cpu_nx=24, cpu_ppc=4):
+def pic_loop_bench(api, torch, nx=256, ppc=1, steps=20, dx=0.25, dt=0.1, cpu_nx=24, cpu_ppc=4,
+                   cell_order=True):
     """The self-consistent loop (qed_pic_step): a warm electron plasma at
     0.05 n_c, thermal momenta 0.1 m c per axis, `ppc` electrons per cell at
-    random positions on a periodic nx^3 Yee grid (dx = 0.25, Dt = 0.1).  Each
-    cycle is the QED step gathering from the node grid, the current deposit
-    and the field leapfrog with the node grid.  The cycles are timed whole,
-    then once more with events between the phases.  Field bytes: 188 B per
-    cell per cycle (B half-step 36, E step 60 with J zeroed, B half-step 36,
-    nodes 56); the deposit reads 28 B and adds 24 float atomics per particle
-    into J arrays that stay in L2."""
+    random positions on a periodic nx^3 Yee grid (dx = 0.25, Dt = 0.1); at
+    256^3 the field arrays (1.1 GB) and the particles are larger than L2.
+    Each cycle is the QED step gathering from the node grid, the current
+    deposit and the field leapfrog with the node grid.  The cycles are timed
+    whole, then once more with events between the phases.  Field bytes: 188 B
+    per cell per cycle (B half-step 36, E step 60 with J zeroed, B half-step
+    36, nodes 56); the deposit reads 28 B per particle and adds its 24 CIC
+    contributions (about 15 atomic operations) into J.  cell_order: the
+    particles stored by cell (as a PIC code's periodic sort keeps them), else
+    in random order, where the gather and the deposit touch a random cell per
+    particle."""
     from paper_1608_06356_gb300 import workloads as W
-    st = W.plasma(nx, nx, nx, dx, ppc=ppc, density=0.05, p_th=0.1, seed=4)
+    st = W.plasma(nx, nx, nx, dx, ppc=ppc, density=0.05, p_th=0.1, seed=4, cell_order=cell_order)
     st = {k: (v.astype(np.float32) if v.dtype.kind == "f" else v) for k, v in st.items()}
     n = len(st["x"])
     ctx = api.qed_init_tables(api.config(dt=dt, seed=2, max_particles=n))
@@ -872,6 +878,8 @@ def pic_loop_bench(api, torch, nx=128, ppc=8, steps=20, dx=0.25, dt=0.1, cpu_nx=
     field_bytes = 188 * cells
     base = {}
     try:
+        if cpu_nx <= 0:
+            raise RuntimeError("no CPU baseline for this variant (see the cell-ordered block)")
         import oracle as O
         from oracle import pic as P
         O.build()
@@ -891,11 +899,12 @@ def pic_loop_bench(api, torch, nx=128, ppc=8, steps=20, dx=0.25, dt=0.1, cpu_nx=
     except Exception as ex:
         base = {"error": repr(ex)}
     return {"grid": [nx, nx, nx], "electrons": n, "electrons_per_cell": ppc, "steps_timed": steps,
+            "particle_order": "by cell" if cell_order else "random",
             "dt": dt, "dx": dx, "status": run_status(c),
             "particle_steps_per_s": n / (ms * 1e-3), "ms_per_cycle": ms,
             "ms_per_phase": {"qed_step": ph[0], "deposit": ph[1], "fields": ph[2]},
             "fields_roofline": _block_roofline(field_bytes, ph[2], peak, kind),
-            "deposit_atomics_per_s": 24 * n / (ph[1] * 1e-3),
+            "deposit_contributions_per_s": 24 * n / (ph[1] * 1e-3),
             "deposit_read_gbs": 28 * n / (ph[1] * 1e-3) / 1e9,
             "photons": g.count(), "cpu_baseline": base}
 
@@ -966,6 +975,7 @@ def main():
     ap.add_argument("--generator-bench", type=int, default=1)
     ap.add_argument("--cascade-bench", type=int, default=1)
     ap.add_argument("--spectra-bench", type=int, default=1)
+    ap.add_argument("--pic-bench", type=int, default=1)
     ap.add_argument("--append-order", choices=["any", "ordered"], default="any",
                     help="lepton step of the headline arms: single pass (any) or the ordered path")
     args = ap.parse_args()
@@ -1069,7 +1079,13 @@ def main():
             extra["config_single_particle_fp64"] = config_single_particle(api, torch)
             extra["config_uniform_field_ensemble"] = config_uniform_ensemble(api, torch)
             extra["config_3d_cascade"] = config_3d_cascade(api, torch)
-            extra["pic_loop"] = pic_loop_bench(api, torch)
+        if args.pic_bench:
+            try:
+                extra["pic_loop"] = pic_loop_bench(api, torch)
+                extra["pic_loop_random_order"] = pic_loop_bench(api, torch, cell_order=False,
+                                                                cpu_nx=0)
+            except Exception as ex:  # report, do not hide the headline
+                extra["pic_loop"] = {"error": repr(ex)}
         if args.generator_bench:
             extra["event_generators_fig2"] = generator_rates(api, torch)
         if args.cascade_bench:

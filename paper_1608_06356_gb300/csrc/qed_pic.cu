@@ -17,9 +17,11 @@
 // neighbours coming from planes that L2 still holds.  One step is four
 // passes -- B half-step, E step (which zeroes J behind it), B half-step, node
 // grid -- because each needs its neighbours' results of the one before.  The
-// deposit is one thread per particle, grid-stride over a persistent grid,
-// 24 float atomics per particle (8 CIC weights x 3 components at their
-// staggered positions), reduced in L2.
+// deposit is one thread per particle, grid-stride over a persistent grid:
+// 8 CIC weights x 3 components at their staggered positions, reduced in L2
+// by atomics -- the two x-neighbours of each stencil row by one 16-byte
+// vector atomic where they share an aligned group of four floats (3 rows
+// in 4), so about 15 atomic operations per particle instead of 24.
 #include <cmath>
 #include <cstdio>
 
@@ -145,6 +147,26 @@ template <class Real> struct DepArgs {
   qed_counters *cnt;
 };
 
+// The two x-neighbours a0, a1 of one row of the stencil: one 16-byte vector
+// atomic (the other two lanes add zero) when both lie in one aligned group of
+// four floats inside the array, else a scalar atomic each (a row wrapping
+// around the periodic boundary, a pair across a group, or nx = 1, where
+// a1 == a0).
+__device__ __forceinline__ void add_pair(float *J, int64_t ncell, int64_t a0, int64_t a1, float v0,
+                                         float v1) {
+  const int64_t g = a0 & ~(int64_t)3;
+  const int l = (int)(a0 & 3);
+  if (a1 == a0 + 1 && l != 3 && g + 3 < ncell) {
+    const float4 v = l == 0 ? make_float4(v0, v1, 0.f, 0.f)
+                   : l == 1 ? make_float4(0.f, v0, v1, 0.f)
+                            : make_float4(0.f, 0.f, v0, v1);
+    atomicAdd(reinterpret_cast<float4 *>(J + g), v);
+  } else {
+    atomicAdd(J + a0, v0);
+    atomicAdd(J + a1, v1);
+  }
+}
+
 // CIC spread of `amount` at reduced coordinates (fx, fy, fz) (cells from the
 // origin of the component's staggered lattice).
 template <class Real>
@@ -159,17 +181,15 @@ __device__ __forceinline__ void spread(float *J, const DepArgs<Real> &A, Real fx
   const int64_t i1 = i0 + 1 == A.nx ? 0 : i0 + 1;
   const int64_t j1 = j0 + 1 == A.ny ? 0 : j0 + 1;
   const int64_t k1 = k0 + 1 == A.nz ? 0 : k0 + 1;
-  const int64_t nx = A.nx, plane = (int64_t)A.nx * A.ny;
+  const int64_t nx = A.nx, plane = (int64_t)A.nx * A.ny, ncell = plane * A.nz;
 #pragma unroll
   for (int dk = 0; dk < 2; ++dk)
 #pragma unroll
-    for (int dj = 0; dj < 2; ++dj)
-#pragma unroll
-      for (int di = 0; di < 2; ++di) {
-        const Real wgt = (di ? wx : (Real)1 - wx) * (dj ? wy : (Real)1 - wy) * (dk ? wz : (Real)1 - wz);
-        const int64_t cell = (dk ? k1 : k0) * plane + (dj ? j1 : j0) * nx + (di ? i1 : i0);
-        atomicAdd(J + cell, (float)(amount * wgt));
-      }
+    for (int dj = 0; dj < 2; ++dj) {
+      const Real wr = amount * (dj ? wy : (Real)1 - wy) * (dk ? wz : (Real)1 - wz);
+      const int64_t row = (dk ? k1 : k0) * plane + (dj ? j1 : j0) * nx;
+      add_pair(J, ncell, row + i0, row + i1, (float)(wr * ((Real)1 - wx)), (float)(wr * wx));
+    }
 }
 
 template <class Real>

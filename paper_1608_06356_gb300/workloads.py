@@ -97,11 +97,13 @@ def uniform_words(n, seed=0):
 
 
 def plasma(nx, ny, nz, dx, ppc=1, density=0.01, p_th=0.0, drift=(0.0, 0.0, 0.0), seed=0,
-           lattice=False, id0=0):
+           lattice=False, id0=0, cell_order=False):
     """Electrons filling a periodic box of nx*ny*nz cubic cells of side dx at
     `density` (units of the critical density) with weights density dx^3 / ppc:
     ppc per cell, at uniform random positions (lattice=True: one at each cell
-    centre), momenta normal with deviation p_th per axis plus `drift`."""
+    centre), momenta normal with deviation p_th per axis plus `drift`.
+    cell_order=True stores them by cell (z, then y, then x), the order a PIC
+    code's periodic particle sort keeps; ids follow the storage order."""
     rng = np.random.default_rng(seed)
     cells = nx * ny * nz
     if lattice:
@@ -112,6 +114,10 @@ def plasma(nx, ny, nz, dx, ppc=1, density=0.01, p_th=0.0, drift=(0.0, 0.0, 0.0),
         box = (nx * dx, ny * dx, nz * dx)
         pos = [rng.uniform(0.0, L, cells * ppc) for L in box]
     n = cells * ppc
+    if cell_order and not lattice:
+        cell = [np.floor(pos[a] / dx).astype(np.int64) for a in range(3)]
+        o = np.argsort((cell[2] * ny + cell[1]) * nx + cell[0], kind="stable")
+        pos = [q[o] for q in pos]
     p = rng.normal(0.0, 1.0, (3, n)) * p_th + np.asarray(drift, dtype=np.float64)[:, None]
     return dict(x=pos[0], y=pos[1], z=pos[2], px=p[0], py=p[1], pz=p[2],
                 w=np.full(n, density * dx ** 3 / ppc), id=np.arange(id0, id0 + n, dtype=np.uint64))
