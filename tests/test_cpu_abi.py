@@ -112,6 +112,27 @@ def test_workload_generators_are_seeded():
     assert gam.min() >= 100 * (1 - 1e-12) and gam.max() <= 1e4 * (1 + 1e-12)
 
 
+def test_plasma_generator():
+    from paper_1608_06356_gb300 import workloads as W
+    a = W.plasma(6, 5, 4, 0.5, ppc=3, density=0.02, p_th=0.1, seed=2)
+    b = W.plasma(6, 5, 4, 0.5, ppc=3, density=0.02, p_th=0.1, seed=2)
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k])
+    n = 6 * 5 * 4 * 3
+    assert len(a["x"]) == n and np.all(a["w"] == 0.02 * 0.5 ** 3 / 3)
+    for c, L in (("x", 3.0), ("y", 2.5), ("z", 2.0)):
+        assert a[c].min() >= 0 and a[c].max() < L
+    # stored by cell: the same particles, cell indices non-decreasing (z, then y, then x)
+    s = W.plasma(6, 5, 4, 0.5, ppc=3, density=0.02, p_th=0.1, seed=2, cell_order=True)
+    cell = lambda d: ((np.floor(d["z"] / 0.5) * 5 + np.floor(d["y"] / 0.5)) * 6 + np.floor(d["x"] / 0.5))
+    assert np.all(np.diff(cell(s)) >= 0)
+    np.testing.assert_array_equal(np.sort(s["x"]), np.sort(a["x"]))
+    # a lattice: one at each cell centre
+    lat = W.plasma(4, 3, 2, 1.0, lattice=True, drift=(0.1, 0, 0))
+    np.testing.assert_array_equal(np.unique(lat["x"]), [0.5, 1.5, 2.5, 3.5])
+    assert np.all(lat["px"] == 0.1) and np.all(lat["py"] == 0)
+
+
 def test_entry_points_reject_a_null_context(qlib):
     lib = qlib.lib()
     bits, dropped = C.c_uint32(7), C.c_int64(7)
